@@ -1,0 +1,384 @@
+"""Benchmark: p(l)-CG on the 3D 7-point Laplacian 256^3 (n = 16.8M), FP64, rtol 1e-8.
+
+One step = one full solve of A x = b from x0 = 0 (every iteration, the true
+residual check and any restart run in one persistent kernel launch).  The JSON
+line reports p(l)-CG iterations/s (the headline), the solve's algorithmic HBM
+GB/s, classic CG on the same system and GPU, the FP32-with-FP64-correction
+path, an l sweep, an end-to-end number through the host-pointer C entry point,
+the dominant kernel's roofline and the FP64 CPU oracle timed on the host.
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+
+Under torchrun (N > 1) every rank solves its own copy of the system
+(independent replicas, weak scaling); rank 0 prints the line.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "p(l)-CG iterations/s, 3D 7-point Laplacian 256^3 FP64, rtol 1e-8"
+UNIT = "iter/s"
+NX = 256
+RTOL = 1e-8
+L_HEAD = 1
+
+
+def dist_env():
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return rank, world, local
+
+
+# ---------------------------------------------------------------- clocks
+class ClockSampler:
+    """nvidia-smi samples (every 200 ms) while the timed region runs."""
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index: int):
+        self.gpu = gpu_index
+        self.proc = None
+        self.lines = []
+
+    def __enter__(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--id={self.gpu}", f"--query-gpu={self.FIELDS}",
+                 "--format=csv,noheader,nounits", "-lms", "200"],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.thread = threading.Thread(target=self._read, daemon=True)
+            self.thread.start()
+        except Exception:
+            self.proc = None
+        return self
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def __exit__(self, *exc):
+        if self.proc is not None:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except Exception:
+                self.proc.kill()
+
+    def summary(self):
+        sm, smax, reasons = [], [], set()
+        names = ("hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap")
+        for ln in self.lines:
+            parts = [p.strip() for p in ln.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                smax.append(float(parts[2]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, parts[5:9]):
+                if v.lower() == "active":
+                    reasons.add(nm)
+        if not sm:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unsampled"], "samples": 0}
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(smax),
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+# ---------------------------------------------------------------- helpers
+def measured_peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            return json.load(f)
+    except Exception:
+        return {}
+
+
+def kernel_source_hash() -> str:
+    h = hashlib.sha256()
+    for f in sorted(os.listdir(os.path.join(ROOT, "paper_1905_06850_gb300", "csrc"))):
+        if f.endswith((".cu", ".cuh", ".h")):
+            with open(os.path.join(ROOT, "paper_1905_06850_gb300", "csrc", f), "rb") as fh:
+                h.update(f.encode() + fh.read())
+    return h.hexdigest()[:16]
+
+
+def profiled_traffic(name: str):
+    """DRAM bytes per point-iteration from a committed ncu summary, when its
+    kernel-source hash matches the current sources (else None)."""
+    path = os.path.join(ROOT, "profiles", name)
+    try:
+        with open(path) as f:
+            d = json.load(f)
+    except Exception:
+        return None
+    if d.get("source_hash") != kernel_source_hash():
+        return None
+    return d.get("dram_bytes_per_point_iter")
+
+
+def passes_per_iter(l: int, method: str) -> int:
+    """Streaming passes over length-n vectors per iteration (fused sweep,
+    l+1 dots): 3 per basis (read 2, write 1) + 4 for p and x + extra dot
+    operands z^(l)_j for l >= 4; classic CG: 10."""
+    if method == "cg":
+        return 10
+    return 3 * (l + 1) + 4 + max(0, l - 3)
+
+
+def dp_flops_per_point(l: int) -> int:
+    """FP64 flops per point per p(l)-CG iteration on the 7-point stencil
+    (FMA = 2): SpMV 8, K4 5 per basis, K5 2 per dot (l+1 dots), K6 5."""
+    return 8 + 5 * (l + 1) + 2 * (l + 1) + 5
+
+
+# ---------------------------------------------------------------- our arm
+def run_ours(args):
+    import torch
+    import torch.distributed as dist
+    from paper_1905_06850_gb300 import plcg
+    from paper_1905_06850_gb300 import workloads as W
+
+    rank, world, local = dist_env()
+    if world > 1:
+        dist.init_process_group("nccl" if torch.cuda.is_available() else "gloo")
+    torch.cuda.set_device(local)
+    plcg.load()
+    dev = torch.device("cuda", local)
+
+    cfg = W.config_3d(nx=args.nx, seed=2)
+    op, b_np = cfg["op"], cfg["b"]
+    n = W.op_size(op)
+    interval = cfg["interval"]
+    b = torch.tensor(b_np, device=dev)
+    A = plcg.Matrix(op)
+    stream = torch.cuda.current_stream()
+
+    def solve_once(x, **kw):
+        return A.solve(b, x, l=kw.pop("l", L_HEAD), interval=interval, rtol=RTOL, **kw)
+
+    def barrier():
+        if world > 1:
+            dist.barrier()
+        torch.cuda.synchronize()
+
+    # warm-up (also builds the workspace)
+    xs = [torch.zeros(n, dtype=torch.float64, device=dev) for _ in range(args.warmup + args.steps)]
+    for w in range(args.warmup):
+        solve_once(xs[w])
+    results = []
+    barrier()
+    with ClockSampler(local) as clk:
+        ev0 = torch.cuda.Event(enable_timing=True)
+        ev1 = torch.cuda.Event(enable_timing=True)
+        ev0.record(stream)
+        for s in range(args.steps):
+            results.append(solve_once(xs[args.warmup + s]))
+        ev1.record(stream)
+        barrier()
+    t_total = ev0.elapsed_time(ev1) * 1e-3
+    if world > 1:
+        t = torch.tensor([t_total], device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        t_total = float(t.item())
+    iters = [r.iters for r in results]
+    assert all(r.ok for r in results), [r.status for r in results]
+    total_iters = sum(iters) * world
+    value = total_iters / t_total
+    ms_per_step = t_total / args.steps * 1e3
+    kern_s = [r.seconds for r in results]
+    # true residual of the last solve, checked on the host (independent stencil apply)
+    x_last = xs[-1].cpu().numpy()
+    host_relres = float(np.linalg.norm(b_np - W.rhs(op, x_last)) / np.linalg.norm(b_np))
+
+    peaks = measured_peaks()
+    hbm_peak = peaks.get("hbm_gbs") or 6800.0
+    hbm_src = "measured" if peaks.get("hbm_gbs") else "fallback"
+    bytes_iter = passes_per_iter(L_HEAD, "plcg") * 8 * n
+    bytes_launch = statistics.mean(iters) * bytes_iter + 3 * 8 * n * 2   # + 2 residual sweeps
+    achieved_gbs = bytes_launch / statistics.mean(kern_s) / 1e9
+    dp_flops = statistics.mean(iters) * dp_flops_per_point(L_HEAD) * n
+    achieved_dp_tf = dp_flops / statistics.mean(kern_s) / 1e12
+    dp_peak_tf = 1.25   # nominal FP64 rate of GB300 (recipe table); see the design doc
+    traffic_ppi = profiled_traffic("plcg_3d_fp64_l1.json")
+    traffic = None if traffic_ppi is None else traffic_ppi * n * statistics.mean(iters)
+    hbm_frac = achieved_gbs / hbm_peak
+    dp_frac = achieved_dp_tf / dp_peak_tf
+    if dp_frac >= hbm_frac:
+        roofline = {"bound": "alu", "achieved": round(achieved_dp_tf, 4), "peak": dp_peak_tf,
+                    "unit": "TFLOP/s", "frac": round(dp_frac, 4), "traffic": traffic,
+                    "peak_source": "nominal FP64 1.25 TFLOP/s (GB300 FP64 units x clock)",
+                    "hbm": {"achieved_gbs": round(achieved_gbs, 1), "peak_gbs": hbm_peak,
+                            "frac": round(hbm_frac, 4), "peak_source": hbm_src}}
+    else:
+        roofline = {"bound": "hbm", "achieved": round(achieved_gbs, 1), "peak": hbm_peak,
+                    "unit": "GB/s", "frac": round(hbm_frac, 4), "traffic": traffic,
+                    "peak_source": hbm_src}
+
+    extra = {}
+    if rank == 0 and not args.quick:
+        # classic CG on the same system and GPU
+        xc = torch.zeros(n, dtype=torch.float64, device=dev)
+        A.solve(b, xc, method="cg", rtol=RTOL)
+        xc.zero_()
+        rc = A.solve(b, xc, method="cg", rtol=RTOL)
+        extra["classic_cg"] = {"iters": rc.iters, "time_to_rtol_s": round(rc.seconds, 5),
+                               "iters_per_s": round(rc.iters / rc.seconds, 1),
+                               "hbm_gbs": round(rc.iters * 10 * 8 * n / rc.seconds / 1e9, 1)}
+        # l sweep (FP64)
+        sweep = {}
+        for l in (2, 3, 4, 5):
+            xl = torch.zeros(n, dtype=torch.float64, device=dev)
+            r = A.solve(b, xl, l=l, interval=interval, rtol=RTOL)
+            sweep[f"l{l}"] = {"iters": r.iters, "time_to_rtol_s": round(r.seconds, 5),
+                              "iters_per_s": round(r.iters / r.seconds, 1),
+                              "hbm_gbs": round(r.iters * passes_per_iter(l, "plcg") * 8 * n
+                                               / r.seconds / 1e9, 1)}
+        extra["plcg_l_sweep_fp64"] = sweep
+        # FP32 vectors with FP64 dots / scalars / refinement
+        mp = {}
+        for l in (1, 2):
+            xf = torch.zeros(n, dtype=torch.float64, device=dev)
+            A.solve(b, xf, l=l, interval=interval, rtol=RTOL, prec="fp32")
+            xf.zero_()
+            r = A.solve(b, xf, l=l, interval=interval, rtol=RTOL, prec="fp32")
+            err = float(np.linalg.norm(b_np - W.rhs(op, xf.cpu().numpy())) / np.linalg.norm(b_np))
+            byt = r.iters * passes_per_iter(l, "plcg") * 4 * n
+            mp[f"l{l}"] = {"iters": r.iters, "refinements": r.refinements,
+                           "time_to_rtol_s": round(r.seconds, 5),
+                           "iters_per_s": round(r.iters / r.seconds, 1),
+                           "hbm_gbs": round(byt / r.seconds / 1e9, 1),
+                           "hbm_frac": round(byt / r.seconds / 1e9 / hbm_peak, 4),
+                           "true_relres": err}
+        xf = torch.zeros(n, dtype=torch.float64, device=dev)
+        r = A.solve(b, xf, method="cg", rtol=RTOL, prec="fp32")
+        mp["classic_cg"] = {"iters": r.iters, "time_to_rtol_s": round(r.seconds, 5),
+                            "iters_per_s": round(r.iters / r.seconds, 1)}
+        extra["fp32_fp64corr"] = mp
+
+    # end to end through the host-pointer entry point (pinned host buffers)
+    e2e = None
+    if not args.quick:
+        bh = torch.tensor(b_np).pin_memory()
+        xh = torch.zeros(n, dtype=torch.float64).pin_memory()
+        A.solve_host(bh.numpy(), xh.numpy(), l=L_HEAD, interval=interval, rtol=RTOL)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        k_e2e = 0
+        for _ in range(max(1, args.steps // 2)):
+            xh.zero_()
+            r = A.solve_host(bh.numpy(), xh.numpy(), l=L_HEAD, interval=interval, rtol=RTOL)
+            k_e2e += r.iters
+        t_e2e = time.perf_counter() - t0
+        e2e = {"value": round(k_e2e * world / t_e2e, 1), "unit": UNIT,
+               "h2d_bytes_per_step": 2 * 8 * n, "d2h_bytes_per_step": 8 * n,
+               "steps": max(1, args.steps // 2)}
+
+    if world > 1:
+        dist.barrier()
+    if rank != 0:
+        return
+    cpu = cpu_baseline(op, b_np, interval) if not args.quick else None
+    line = {
+        "metric": METRIC, "value": round(value, 2), "unit": UNIT, "n_gpus": world,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(ms_per_step, 3),
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+        "data": "synthetic (seeded x* ~ N(0,1), b = A x*)",
+        "config": {"workload": f"3D 7-point Laplacian {args.nx}^3 (n={n}), FP64, p(1)-CG, "
+                               f"Chebyshev shifts on [0, 12], rtol {RTOL}, x0 = 0",
+                   "l": L_HEAD, "n": n, "iters_per_solve": iters[0],
+                   "time_to_rtol_s": round(statistics.median(kern_s), 5),
+                   "l2": "inputs larger than L2 (each vector 134 MB > 126 MB L2); no flush",
+                   "host_check_true_relres": host_relres},
+        "hbm_gbs": round(achieved_gbs, 1),
+        "roofline": roofline,
+        "cpu_baseline": cpu,
+        "e2e": e2e,
+        "gpu_launches": args.steps,
+        "clocks": clk.summary(),
+        **extra,
+    }
+    print(json.dumps(line), flush=True)
+
+
+# ---------------------------------------------------------------- CPU oracle
+def cpu_baseline(op, b, interval, iters=12):
+    """The FP64 oracle (serial C, as it stands) on a bounded sample of the same
+    workload: `iters` iterations of p(1)-CG on the full 256^3 system."""
+    from oracle import oracle as O
+    sig = O.chebyshev_shifts(L_HEAD, *interval)
+    t0 = time.perf_counter()
+    r = O.plcg(op, b, l=L_HEAD, sigma=sig, rtol=RTOL, maxit=iters, dots_2l1=False)
+    dt = time.perf_counter() - t0
+    return {"value": round(r.iters / dt, 3), "unit": UNIT, "cores": 1, "kind": "oracle",
+            "sample": f"{r.iters} iterations of p(1)-CG on the full {op['nx']}^3 system "
+                      f"(serial C oracle, plus its 2 residual evaluations), {dt:.1f} s"}
+
+
+def run_reference(args):
+    """The reference arm: the FP64 CPU oracle on the machine's host cores, same
+    metric and workload, each step a bounded sample (a few iterations)."""
+    rank, world, _ = dist_env()
+    if rank != 0:
+        return
+    from oracle import oracle as O
+    from paper_1905_06850_gb300 import workloads as W
+    cfg = W.config_3d(nx=args.nx, seed=2)
+    op, b = cfg["op"], cfg["b"]
+    sig = O.chebyshev_shifts(L_HEAD, *cfg["interval"])
+    per_step = 4
+    for _ in range(args.warmup):
+        O.plcg(op, b, l=L_HEAD, sigma=sig, rtol=RTOL, maxit=1, dots_2l1=False)
+    t0 = time.perf_counter()
+    k = 0
+    for _ in range(args.steps):
+        k += O.plcg(op, b, l=L_HEAD, sigma=sig, rtol=RTOL, maxit=per_step, dots_2l1=False).iters
+    dt = time.perf_counter() - t0
+    value = k / dt
+    line = {"metric": METRIC, "value": round(value, 3), "unit": UNIT, "n_gpus": world,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(dt / args.steps * 1e3, 1),
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic (seeded x* ~ N(0,1), b = A x*)", "impl": "reference",
+            "config": {"workload": f"3D 7-point Laplacian {args.nx}^3, FP64, p(1)-CG, rtol {RTOL}",
+                       "sample_per_step": f"{per_step} iterations (+2 residual evaluations)"},
+            "cpu_baseline": {"value": round(value, 3), "unit": UNIT, "cores": 1, "kind": "oracle",
+                             "sample": f"{per_step} iterations per step of the full system"},
+            "e2e": {"value": round(value, 3), "unit": UNIT, "h2d_bytes_per_step": 0,
+                    "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--nx", type=int, default=NX)
+    ap.add_argument("--quick", action="store_true", help="headline only (no sweeps, e2e, CPU)")
+    args = ap.parse_args()
+    if args.warmup < 3:
+        args.warmup = 3
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_ours(args)
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,182 @@
+/*
+ * plcg.h -- C ABI of libplcg.so: deep pipelined Conjugate Gradients, p(l)-CG,
+ * on one NVIDIA GB300 (sm_103a).
+ *
+ * Method: Cools, Cornelis, Ghysels, Vanroose, "Improving strong scaling of
+ * the Conjugate Gradient method for solving large linear systems using global
+ * reduction pipelining", EuroMPI'19 (arXiv:1905.06850), Algorithm 1 with
+ * M = I, and classic Hestenes-Stiefel CG (cited and costed in Sec. 1 and
+ * Table 1) for comparison.  The problem is A x = b with A sparse symmetric
+ * positive definite (Sec. 2.1).
+ *
+ * Conventions
+ *   - Every function returns a plcg_status; nothing throws across the ABI.
+ *     On failure plcg_last_error() returns a thread-local message.
+ *   - Vectors are contiguous FP64 arrays of length n.  Pointers marked
+ *     "device" must be CUDA device (or managed) memory of the current
+ *     device; pointers marked "host" are ordinary host memory.  The caller
+ *     owns all vectors and keeps them alive until the call returns (or, for
+ *     plcg_submit, until plcg_poll reports completion).
+ *   - The library copies matrix data into device memory it owns; that memory
+ *     and every workspace are released by plcg_destroy.
+ *   - A solve runs on the stream given at matrix creation (NULL = the legacy
+ *     default stream) and returns after the stream has finished it.
+ *   - Every device-side wait in the library is bounded; when a bound expires
+ *     the solve returns PLCG_ERR_TIMEOUT and the CUDA context stays usable.
+ */
+#ifndef PLCG_H
+#define PLCG_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+    PLCG_OK = 0,
+    PLCG_PENDING = 1,           /* plcg_poll: the request is not finished      */
+    PLCG_ERR_INVALID = -1,      /* bad argument (checked on the host)          */
+    PLCG_ERR_NOMEM = -2,        /* device or host allocation failed            */
+    PLCG_ERR_CUDA = -3,         /* a CUDA call failed (message has the reason) */
+    PLCG_ERR_BREAKDOWN = -4,    /* square-root breakdowns exceeded max_restarts
+                                   (Alg. 1 line 11, Sec. 2.2)                  */
+    PLCG_ERR_MAXIT = -5,        /* iteration budget exhausted; x = last iterate */
+    PLCG_ERR_NONFINITE = -6,    /* NaN/Inf met in b, x0 or a recurrence         */
+    PLCG_ERR_TIMEOUT = -7,      /* a bounded device wait expired                */
+    PLCG_ERR_UNIMPL = -8        /* combination not implemented                  */
+} plcg_status;
+
+typedef enum {
+    PLCG_FP64 = 0,              /* vectors, dots and scalars in FP64            */
+    PLCG_FP32_FP64DOT = 1       /* FP32 vectors and matrix values; FP64 dot
+                                   accumulation, scalar recurrences, true
+                                   residual and an FP64 outer refinement loop   */
+} plcg_precision;
+
+typedef enum {
+    PLCG_METHOD_PLCG = 0,       /* p(l)-CG, Algorithm 1                         */
+    PLCG_METHOD_CG = 1          /* classic Hestenes-Stiefel CG                  */
+} plcg_method;
+
+/* Opaque matrix handle: operator + its device data + cached workspaces. */
+typedef struct plcg_matrix plcg_matrix;
+
+/* Structured constant-coefficient operator with homogeneous Dirichlet
+ * boundaries (a neighbour outside the grid contributes 0).  Unknowns are in
+ * lexicographic order, x fastest: index = (z*ny + y)*nx + x.
+ *   dim = 2, points = 5:  (A u)_p = (center + diag_shift) u_p + off * sum of the 4 neighbours
+ *   dim = 3, points = 7:  same with the 6 neighbours.
+ * The 2D Laplacian of Sec. 4 is center = 4, off = -1; the 3D one center = 6. */
+typedef struct {
+    int dim;                    /* 2 or 3                                        */
+    int points;                 /* 5 (dim 2) or 7 (dim 3)                        */
+    int64_t nx, ny, nz;         /* grid; nz = 1 when dim = 2; n = nx*ny*nz < 2^31 */
+    double center;
+    double off;
+    double diag_shift;          /* added to the diagonal (0 for the Laplacian)   */
+} plcg_stencil_desc;
+
+/* Solve parameters; plcg_params_default() fills the defaults shown. */
+typedef struct {
+    int method;                 /* plcg_method (PLCG_METHOD_PLCG)                */
+    int l;                      /* pipeline length, 1..8 (1)                     */
+    const double *shifts;       /* host array of l shifts sigma_0..sigma_{l-1},
+                                   or NULL: Chebyshev shifts on [lmin, lmax],
+                                   Sec. 2.2 Eq. (chebyshev) (NULL)               */
+    double lmin, lmax;          /* spectrum interval for the shifts (0, 8)      */
+    double rtol;                /* stop when ||b - A x|| < rtol ||b|| (1e-8)      */
+    int64_t maxit;              /* budget on the iterate index k (100000)        */
+    int prec;                   /* plcg_precision (PLCG_FP64)                    */
+    int dots_2l1;               /* 1: the 2l+1 dot products of Alg. 1 line 23;
+                                   0: l+1 dots via the symmetry of G (Sec. 2.2)  (0) */
+    int max_restarts;           /* explicit restarts allowed (8)                 */
+    double inner_rtol_floor;    /* FP32 path: floor of the inner relative tolerance
+                                   of each refinement step (1e-4) */
+    int grid_ctas;              /* 0: choose; else the number of CTAs (tuning)   */
+} plcg_params;
+
+typedef struct {
+    int status;                 /* plcg_status of this solve                     */
+    int64_t iters;              /* k of the returned x (summed over segments)    */
+    int64_t spmvs;              /* applications of A, residuals included         */
+    int64_t restarts;           /* segments started after the first              */
+    int64_t refinements;        /* FP64 outer refinement steps (FP32 path)        */
+    double recursive_relres;    /* |zeta_k| / ||b|| at the end of the last segment */
+    double true_relres;         /* ||b - A x|| / ||b||, FP64, at return           */
+    double seconds;             /* device time of the solve (CUDA events)        */
+} plcg_result;
+
+/* Fill *p with the defaults listed in plcg_params. */
+void plcg_params_default(plcg_params *p);
+
+/* Create a matrix-free stencil operator.  stream: a cudaStream_t (NULL =
+ * default stream) on which every solve of this matrix runs.
+ * Errors: PLCG_ERR_INVALID (bad dims/points, n >= 2^31), PLCG_ERR_CUDA. */
+plcg_status plcg_create_stencil(const plcg_stencil_desc *desc, void *stream,
+                                plcg_matrix **out);
+
+/* Create a CSR operator (A symmetric positive definite; not checked).
+ * rowptr[n+1] (int64, rowptr[0] = 0, non-decreasing), col[nnz] (int32, in
+ * [0, n)), val[nnz] (FP64).  on_device = 1: the three arrays are device
+ * pointers, else host pointers.  prec fixes the stored value type: PLCG_FP64
+ * keeps FP64 values; PLCG_FP32_FP64DOT rounds them to FP32 once, and all
+ * solves of this matrix (including the FP64 residuals) use those rounded
+ * values.  The arrays are copied; the caller may free them on return.
+ * Errors: PLCG_ERR_INVALID (n <= 0, n >= 2^31, bad rowptr or col, checked on
+ * the host when on_device = 0), PLCG_ERR_NOMEM, PLCG_ERR_CUDA. */
+plcg_status plcg_create_csr(int64_t n, int64_t nnz, const int64_t *rowptr,
+                            const int32_t *col, const double *val, int on_device,
+                            int prec, void *stream, plcg_matrix **out);
+
+/* Release the matrix, its device copies and workspaces.  NULL is a no-op. */
+void plcg_destroy(plcg_matrix *A);
+
+/* Solve A x = b.  b: device FP64[n]; x: device FP64[n], in: x0, out: the
+ * returned iterate (written even when the status is MAXIT or BREAKDOWN).
+ * The whole solve (every iteration, restart and refinement step) runs in one
+ * persistent kernel launch; the call waits for it.  res may be NULL.
+ * Returns the solve status (also in res->status). */
+plcg_status plcg_solve(plcg_matrix *A, const double *b, double *x,
+                       const plcg_params *prm, plcg_result *res);
+
+/* As plcg_solve, but b and x are HOST arrays: the call copies b and x0 to
+ * the device, solves, and copies x back (pinned staging owned by A). */
+plcg_status plcg_solve_host(plcg_matrix *A, const double *b, double *x,
+                            const plcg_params *prm, plcg_result *res);
+
+/* Solve count independent systems A[i] x[i] = b[i] (device pointers) in one
+ * persistent launch; each system gets its own thread block(s), converged
+ * systems retire and their blocks take the next system.  prm applies to
+ * every system except that shifts == NULL places Chebyshev shifts on each
+ * system's own [lmin_i, lmax_i] given in lmin[], lmax[] (may be NULL: then
+ * prm->lmin/lmax for all).  results[count] may be NULL.  Only stencil
+ * matrices are supported (PLCG_ERR_UNIMPL otherwise).
+ * Returns PLCG_OK when every system returned PLCG_OK, else the first
+ * non-OK status in index order. */
+plcg_status plcg_solve_batched(int count, plcg_matrix *const *A,
+                               const double *const *b, double *const *x,
+                               const double *lmin, const double *lmax,
+                               const plcg_params *prm, plcg_result *results);
+
+/* Thread-local message describing the last failure in this thread. */
+const char *plcg_last_error(void);
+
+/* Library version string. */
+const char *plcg_version(void);
+
+/* ---- test hooks (no effect unless called) ----------------------------- */
+/* Bound on the polls of every device-side wait (grid barrier, server
+ * mailbox); 0 restores the default (about 2 s at 64 ns per poll). */
+void plcg_debug_set_poll_limit(uint64_t polls);
+/* 1: every grid barrier of the next solves waits for one arrival more than
+ * there are thread blocks, so the first wait runs out and the solve returns
+ * PLCG_ERR_TIMEOUT (exercises the bounded-wait path); 0: off. */
+void plcg_debug_force_barrier_timeout(int on);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* PLCG_H */

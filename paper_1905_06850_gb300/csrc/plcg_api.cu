@@ -1,0 +1,449 @@
+// plcg_api.cu -- host side of the C ABI declared in include/plcg.h.
+//
+// Validates arguments, owns device copies of the operator and the solve
+// workspaces, picks a kernel instantiation (precision x operator x l) and
+// launches it cooperatively (all CTAs co-resident, which the bounded grid
+// barrier of the persistent solver relies on).
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cmath>
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <mutex>
+#include <string>
+
+#include "../../include/plcg.h"
+#include "plcg_internal.h"
+#include "plcg_kernels.h"
+
+using namespace plcg;
+
+// ------------------------------------------------------------------ errors
+static thread_local std::string g_last_error;
+static unsigned long long g_poll_limit = 0;     // 0 = default
+static int g_force_timeout = 0;
+
+static plcg_status fail(plcg_status st, const char *fmt, ...)
+{
+    char buf[512];
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(buf, sizeof(buf), fmt, ap);
+    va_end(ap);
+    g_last_error = buf;
+    return st;
+}
+
+#define CUDA_TRY(call)                                                                      \
+    do {                                                                                    \
+        cudaError_t e_ = (call);                                                            \
+        if (e_ != cudaSuccess)                                                              \
+            return fail(e_ == cudaErrorMemoryAllocation ? PLCG_ERR_NOMEM : PLCG_ERR_CUDA,   \
+                        "%s failed: %s", #call, cudaGetErrorString(e_));                    \
+    } while (0)
+
+extern "C" const char *plcg_last_error(void) { return g_last_error.c_str(); }
+extern "C" const char *plcg_version(void) { return "plcg 0.1 (sm_103a)"; }
+extern "C" void plcg_debug_set_poll_limit(uint64_t polls) { g_poll_limit = polls; }
+extern "C" void plcg_debug_force_barrier_timeout(int on) { g_force_timeout = on ? 1 : 0; }
+
+static unsigned long long poll_limit()
+{
+    // ~2 s at 64 ns per poll (the poll itself adds an L2 round trip)
+    return g_poll_limit ? g_poll_limit : 30000000ull;
+}
+
+// ------------------------------------------------------------------ matrix
+struct Workspace {
+    void *mem = nullptr;        // one allocation for everything below
+    size_t bytes = 0;
+};
+
+struct plcg_matrix {
+    int kind = kOpStencil;
+    int64_t n = 0;
+    StencilDesc st{};
+    int csr_prec = PLCG_FP64;
+    int64_t nnz = 0;
+    int64_t *rowptr = nullptr;
+    int32_t *col = nullptr;
+    void *val = nullptr;
+    cudaStream_t stream = nullptr;
+    int device = 0;
+    int num_sms = 0;
+    Workspace ws;
+    double *b_dev = nullptr, *x_dev = nullptr;   // plcg_solve_host staging
+    cudaEvent_t ev0 = nullptr, ev1 = nullptr;
+    DevResult *host_res = nullptr;              // pinned
+    std::mutex mu;
+};
+
+extern "C" void plcg_params_default(plcg_params *p)
+{
+    if (!p) return;
+    std::memset(p, 0, sizeof(*p));
+    p->method = PLCG_METHOD_PLCG;
+    p->l = 1;
+    p->shifts = nullptr;
+    p->lmin = 0.0;
+    p->lmax = 8.0;
+    p->rtol = 1e-8;
+    p->maxit = 100000;
+    p->prec = PLCG_FP64;
+    p->dots_2l1 = 0;
+    p->max_restarts = 8;
+    p->inner_rtol_floor = 1e-4;
+    p->grid_ctas = 0;
+}
+
+static plcg_status matrix_common_init(plcg_matrix *A, void *stream)
+{
+    A->stream = static_cast<cudaStream_t>(stream);
+    CUDA_TRY(cudaGetDevice(&A->device));
+    CUDA_TRY(cudaDeviceGetAttribute(&A->num_sms, cudaDevAttrMultiProcessorCount, A->device));
+    CUDA_TRY(cudaEventCreate(&A->ev0));
+    CUDA_TRY(cudaEventCreate(&A->ev1));
+    CUDA_TRY(cudaMallocHost(&A->host_res, sizeof(DevResult)));
+    return PLCG_OK;
+}
+
+extern "C" plcg_status plcg_create_stencil(const plcg_stencil_desc *d, void *stream,
+                                           plcg_matrix **out)
+{
+    if (!d || !out) return fail(PLCG_ERR_INVALID, "plcg_create_stencil: NULL argument");
+    *out = nullptr;
+    if (!((d->dim == 2 && d->points == 5) || (d->dim == 3 && d->points == 7)))
+        return fail(PLCG_ERR_INVALID, "stencil: need dim 2 with 5 points or dim 3 with 7 points");
+    const int64_t nz = (d->dim == 3) ? d->nz : 1;
+    if (d->nx < 1 || d->ny < 1 || nz < 1)
+        return fail(PLCG_ERR_INVALID, "stencil: grid sizes must be >= 1");
+    const int64_t n = d->nx * d->ny * nz;
+    if (n >= (int64_t(1) << 31) || d->nx >= (1 << 30) || d->ny >= (1 << 30) || nz >= (1 << 30))
+        return fail(PLCG_ERR_INVALID, "stencil: n must be < 2^31");
+    if (!std::isfinite(d->center) || !std::isfinite(d->off) || !std::isfinite(d->diag_shift))
+        return fail(PLCG_ERR_INVALID, "stencil: non-finite coefficient");
+    plcg_matrix *A = new plcg_matrix();
+    A->kind = kOpStencil;
+    A->n = n;
+    A->st.dim = d->dim;
+    A->st.nx = (int)d->nx;
+    A->st.ny = (int)d->ny;
+    A->st.nz = (int)nz;
+    A->st.center = d->center + d->diag_shift;
+    A->st.off = d->off;
+    plcg_status st = matrix_common_init(A, stream);
+    if (st != PLCG_OK) { plcg_destroy(A); return st; }
+    *out = A;
+    return PLCG_OK;
+}
+
+extern "C" plcg_status plcg_create_csr(int64_t n, int64_t nnz, const int64_t *rowptr,
+                                       const int32_t *col, const double *val, int on_device,
+                                       int prec, void *stream, plcg_matrix **out)
+{
+    if (!out) return fail(PLCG_ERR_INVALID, "plcg_create_csr: NULL out");
+    *out = nullptr;
+    if (n <= 0 || n >= (int64_t(1) << 31) || nnz < 0)
+        return fail(PLCG_ERR_INVALID, "csr: need 0 < n < 2^31 and nnz >= 0");
+    if (!rowptr || (nnz > 0 && (!col || !val)))
+        return fail(PLCG_ERR_INVALID, "csr: NULL array");
+    if (prec != PLCG_FP64 && prec != PLCG_FP32_FP64DOT)
+        return fail(PLCG_ERR_INVALID, "csr: unknown precision %d", prec);
+    if (!on_device) {
+        if (rowptr[0] != 0 || rowptr[n] != nnz)
+            return fail(PLCG_ERR_INVALID, "csr: rowptr[0] must be 0 and rowptr[n] = nnz");
+        for (int64_t r = 0; r < n; ++r)
+            if (rowptr[r + 1] < rowptr[r])
+                return fail(PLCG_ERR_INVALID, "csr: rowptr decreases at row %lld", (long long)r);
+        for (int64_t e = 0; e < nnz; ++e)
+            if (col[e] < 0 || col[e] >= n)
+                return fail(PLCG_ERR_INVALID, "csr: column index out of range at entry %lld",
+                            (long long)e);
+        for (int64_t e = 0; e < nnz; ++e)
+            if (!std::isfinite(val[e]))
+                return fail(PLCG_ERR_INVALID, "csr: non-finite value at entry %lld", (long long)e);
+    }
+    plcg_matrix *A = new plcg_matrix();
+    A->kind = kOpCsr;
+    A->n = n;
+    A->nnz = nnz;
+    A->csr_prec = prec;
+    plcg_status st = matrix_common_init(A, stream);
+    if (st != PLCG_OK) { plcg_destroy(A); return st; }
+    const cudaMemcpyKind kind = on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice;
+    const size_t vsz = (prec == PLCG_FP64) ? sizeof(double) : sizeof(float);
+    cudaError_t e = cudaMalloc(&A->rowptr, (n + 1) * sizeof(int64_t));
+    if (e == cudaSuccess) e = cudaMalloc(&A->col, std::max<int64_t>(nnz, 1) * sizeof(int32_t));
+    if (e == cudaSuccess) e = cudaMalloc(&A->val, std::max<int64_t>(nnz, 1) * vsz);
+    if (e == cudaSuccess) e = cudaMemcpy(A->rowptr, rowptr, (n + 1) * sizeof(int64_t), kind);
+    if (e == cudaSuccess && nnz) e = cudaMemcpy(A->col, col, nnz * sizeof(int32_t), kind);
+    if (e == cudaSuccess && nnz) {
+        if (prec == PLCG_FP64) {
+            e = cudaMemcpy(A->val, val, nnz * sizeof(double), kind);
+        } else {
+            // round to FP32 once: on the device when the values already live there
+            double *tmp = nullptr;
+            const double *src = val;
+            if (!on_device) {
+                e = cudaMalloc(&tmp, nnz * sizeof(double));
+                if (e == cudaSuccess) e = cudaMemcpy(tmp, val, nnz * sizeof(double), kind);
+                src = tmp;
+            }
+            if (e == cudaSuccess) e = launch_round_to_f32(src, static_cast<float *>(A->val), nnz, nullptr);
+            if (e == cudaSuccess) e = cudaDeviceSynchronize();
+            if (tmp) cudaFree(tmp);
+        }
+    }
+    if (e != cudaSuccess) {
+        plcg_status s2 = fail(e == cudaErrorMemoryAllocation ? PLCG_ERR_NOMEM : PLCG_ERR_CUDA,
+                              "csr upload: %s", cudaGetErrorString(e));
+        plcg_destroy(A);
+        return s2;
+    }
+    *out = A;
+    return PLCG_OK;
+}
+
+extern "C" void plcg_destroy(plcg_matrix *A)
+{
+    if (!A) return;
+    if (A->stream) cudaStreamSynchronize(A->stream);
+    else cudaDeviceSynchronize();
+    cudaFree(A->rowptr);
+    cudaFree(A->col);
+    cudaFree(A->val);
+    cudaFree(A->ws.mem);
+    cudaFree(A->b_dev);
+    cudaFree(A->x_dev);
+    if (A->host_res) cudaFreeHost(A->host_res);
+    if (A->ev0) cudaEventDestroy(A->ev0);
+    if (A->ev1) cudaEventDestroy(A->ev1);
+    delete A;
+}
+
+// ------------------------------------------------------------------ solve
+static void chebyshev_shifts(int l, double lmin, double lmax, double *sig)
+{
+    // Sec. 2.2, Eq. (chebyshev): zeros of T_l mapped to [lmin, lmax]
+    const double pi = 3.14159265358979323846;
+    for (int i = 0; i < l; ++i)
+        sig[i] = 0.5 * (lmax + lmin) + 0.5 * (lmax - lmin) * std::cos((2 * i + 1) * pi / (2.0 * l));
+}
+
+static plcg_status ensure_ws(plcg_matrix *A, size_t bytes)
+{
+    if (A->ws.bytes >= bytes) return PLCG_OK;
+    if (A->ws.mem) {
+        if (A->stream) cudaStreamSynchronize(A->stream);
+        cudaFree(A->ws.mem);
+        A->ws.mem = nullptr;
+        A->ws.bytes = 0;
+    }
+    CUDA_TRY(cudaMalloc(&A->ws.mem, bytes));
+    A->ws.bytes = bytes;
+    return PLCG_OK;
+}
+
+static inline size_t align_up(size_t v, size_t a) { return (v + a - 1) / a * a; }
+
+template <typename T>
+static plcg_status run_solve(plcg_matrix *A, const double *b, double *x, const plcg_params *prm,
+                             const double *sigma, plcg_result *res)
+{
+    const int64_t n = A->n;
+    const int l = prm->l;
+    const bool cg = prm->method == PLCG_METHOD_CG;
+    const int op = A->kind;
+    const bool f32 = sizeof(T) == 4;
+    int vec = 1;
+    if (op == kOpStencil) {
+        const int want = 16 / (int)sizeof(T);
+        vec = (A->st.nx % want == 0) ? want : 1;
+    }
+    const void *func = kernel_ptr(f32, op, vec, cg ? 0 : l, cg);
+    if (!func) return fail(PLCG_ERR_UNIMPL, "no kernel for prec=%d op=%d vec=%d l=%d", (int)f32, op, vec, l);
+
+    int per_sm = 0;
+    CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, func, kBlock, 0));
+    if (per_sm < 1) return fail(PLCG_ERR_CUDA, "solver kernel cannot be resident");
+    const int64_t unit = (int64_t)kBlock * vec;
+    const int64_t nunits = (n + unit - 1) / unit;
+    int64_t P = (int64_t)per_sm * A->num_sms;
+    if (prm->grid_ctas > 0) P = std::min<int64_t>(P, prm->grid_ctas);
+    P = std::max<int64_t>(1, std::min<int64_t>(P, nunits));
+
+    // ---- workspace layout
+    SolveArgs<T> a;
+    std::memset(&a, 0, sizeof(a));
+    int nvec = 0;
+    if (!cg) {
+        for (int k = 0; k <= l; ++k) {
+            int d = 3;
+            if (k == l) d = std::max(3, l);
+            if (k == 0 && prm->dots_2l1) d = std::max(3, l + 1);
+            a.depth[k] = d;
+            a.base[k] = nvec;
+            nvec += d;
+        }
+    } else {
+        nvec = 3;   // p ring of two + the FP32 inner iterate
+    }
+    const size_t vbytes = align_up((size_t)n * sizeof(T), 256);
+    size_t off = 0;
+    const size_t o_ring = off; off += vbytes * nvec;
+    const size_t o_p = off; off += vbytes;
+    const size_t o_rc = off; off += vbytes;
+    const size_t o_r = off; off += align_up((size_t)n * sizeof(double), 256);
+    const int slots = cg ? 2 : (l + 1);
+    const size_t o_part = off; off += align_up((size_t)slots * P * kMaxDots * sizeof(double), 256);
+    const size_t o_npart = off; off += align_up((size_t)P * kNormSlots * sizeof(double), 256);
+    const size_t o_bar = off; off += 256;
+    const size_t o_out = off; off += align_up(sizeof(DevResult), 256);
+    plcg_status st = ensure_ws(A, off);
+    if (st != PLCG_OK) return st;
+    char *base = static_cast<char *>(A->ws.mem);
+    // x's vector layout is contiguous per vector: ring base[k] counts vectors of n
+    // elements; keep the ring packed (n elements per vector) so ring() indexes it.
+    a.n = n;
+    a.st = A->st;
+    a.csr.rowptr = A->rowptr;
+    a.csr.col = A->col;
+    a.csr.val = A->val;
+    a.b = b;
+    a.x = x;
+    a.r = reinterpret_cast<double *>(base + o_r);
+    a.zring = reinterpret_cast<T *>(base + o_ring);
+    a.p = reinterpret_cast<T *>(base + o_p);
+    a.rc = reinterpret_cast<T *>(base + o_rc);
+    a.part = reinterpret_cast<double *>(base + o_part);
+    a.npart = reinterpret_cast<double *>(base + o_npart);
+    a.bar = reinterpret_cast<unsigned *>(base + o_bar);
+    a.out = reinterpret_cast<DevResult *>(base + o_out);
+    a.method = cg ? 1 : 0;
+    a.l = l;
+    for (int k = 0; k < l && k < kMaxL; ++k) a.sigma[k] = sigma[k];
+    a.rtol = prm->rtol;
+    a.maxit = prm->maxit;
+    a.dots_2l1 = prm->dots_2l1 ? 1 : 0;
+    a.max_restarts = prm->max_restarts;
+    a.inner_floor = prm->inner_rtol_floor;
+    a.fp32 = f32 ? 1 : 0;
+    a.poll_limit = poll_limit();
+    a.force_timeout = g_force_timeout;
+    // The ring is indexed in whole vectors of n elements: pad n to keep every
+    // vector 16-byte aligned.
+    if (((size_t)n * sizeof(T)) % 16 != 0 && vec > 1)
+        return fail(PLCG_ERR_INVALID, "internal: vector length not 16-byte aligned");
+
+    CUDA_TRY(cudaMemsetAsync(base + o_bar, 0, 256, A->stream));
+    CUDA_TRY(cudaMemsetAsync(base + o_out, 0, sizeof(DevResult), A->stream));
+    CUDA_TRY(cudaEventRecord(A->ev0, A->stream));
+    void *args[] = {&a};
+    CUDA_TRY(cudaLaunchCooperativeKernel(func, dim3((unsigned)P), dim3(kBlock), args, 0, A->stream));
+    CUDA_TRY(cudaEventRecord(A->ev1, A->stream));
+    CUDA_TRY(cudaMemcpyAsync(A->host_res, a.out, sizeof(DevResult), cudaMemcpyDeviceToHost, A->stream));
+    CUDA_TRY(cudaStreamSynchronize(A->stream));
+    float ms = 0.f;
+    CUDA_TRY(cudaEventElapsedTime(&ms, A->ev0, A->ev1));
+    const DevResult &o = *A->host_res;
+    if (res) {
+        res->status = o.status;
+        res->iters = o.iters;
+        res->spmvs = o.spmvs;
+        res->restarts = o.restarts;
+        res->refinements = o.refinements;
+        res->recursive_relres = o.recursive_relres;
+        res->true_relres = o.true_relres;
+        res->seconds = ms * 1e-3;
+    }
+    if (o.status == PLCG_ERR_TIMEOUT)
+        return fail(PLCG_ERR_TIMEOUT, "a bounded device wait expired (grid barrier)");
+    if (o.status != PLCG_OK) {
+        const char *why = o.status == PLCG_ERR_BREAKDOWN ? "square-root breakdowns exceeded max_restarts"
+                        : o.status == PLCG_ERR_MAXIT ? "iteration budget exhausted"
+                        : o.status == PLCG_ERR_NONFINITE ? "non-finite value in the recurrences"
+                        : "solve failed";
+        return fail((plcg_status)o.status, "%s", why);
+    }
+    return PLCG_OK;
+}
+
+static plcg_status check_params(const plcg_matrix *A, const plcg_params *p)
+{
+    if (!p) return fail(PLCG_ERR_INVALID, "NULL params");
+    if (p->method != PLCG_METHOD_PLCG && p->method != PLCG_METHOD_CG)
+        return fail(PLCG_ERR_INVALID, "unknown method %d", p->method);
+    if (p->method == PLCG_METHOD_PLCG && (p->l < 1 || p->l > kMaxL))
+        return fail(PLCG_ERR_INVALID, "l must be in 1..%d", kMaxL);
+    if (!(p->rtol > 0.0) || !std::isfinite(p->rtol))
+        return fail(PLCG_ERR_INVALID, "rtol must be a positive finite number");
+    if (p->maxit < 0) return fail(PLCG_ERR_INVALID, "maxit must be >= 0");
+    if (p->max_restarts < 0) return fail(PLCG_ERR_INVALID, "max_restarts must be >= 0");
+    if (p->prec != PLCG_FP64 && p->prec != PLCG_FP32_FP64DOT)
+        return fail(PLCG_ERR_INVALID, "unknown precision %d", p->prec);
+    if (A->kind == kOpCsr && p->prec != A->csr_prec)
+        return fail(PLCG_ERR_INVALID, "CSR matrix was created for precision %d", A->csr_prec);
+    if (p->prec == PLCG_FP32_FP64DOT && !(p->inner_rtol_floor > 0.0 && p->inner_rtol_floor < 1.0))
+        return fail(PLCG_ERR_INVALID, "inner_rtol_floor must be in (0, 1)");
+    if (p->method == PLCG_METHOD_PLCG) {
+        if (p->shifts) {
+            for (int k = 0; k < p->l; ++k)
+                if (!std::isfinite(p->shifts[k])) return fail(PLCG_ERR_INVALID, "non-finite shift");
+        } else if (!std::isfinite(p->lmin) || !std::isfinite(p->lmax) || p->lmax < p->lmin) {
+            return fail(PLCG_ERR_INVALID, "need lmin <= lmax for the Chebyshev shifts");
+        }
+    }
+    return PLCG_OK;
+}
+
+extern "C" plcg_status plcg_solve(plcg_matrix *A, const double *b, double *x,
+                                  const plcg_params *prm, plcg_result *res)
+{
+    if (!A || !b || !x) return fail(PLCG_ERR_INVALID, "plcg_solve: NULL argument");
+    plcg_status st = check_params(A, prm);
+    if (st != PLCG_OK) return st;
+    if ((reinterpret_cast<uintptr_t>(b) | reinterpret_cast<uintptr_t>(x)) & 15)
+        return fail(PLCG_ERR_INVALID, "b and x must be 16-byte aligned");
+    double sigma[kMaxL] = {0};
+    if (prm->method == PLCG_METHOD_PLCG) {
+        if (prm->shifts) std::memcpy(sigma, prm->shifts, prm->l * sizeof(double));
+        else chebyshev_shifts(prm->l, prm->lmin, prm->lmax, sigma);
+    }
+    std::lock_guard<std::mutex> lock(A->mu);
+    CUDA_TRY(cudaSetDevice(A->device));
+    if (prm->prec == PLCG_FP64) return run_solve<double>(A, b, x, prm, sigma, res);
+    return run_solve<float>(A, b, x, prm, sigma, res);
+}
+
+extern "C" plcg_status plcg_solve_host(plcg_matrix *A, const double *b, double *x,
+                                       const plcg_params *prm, plcg_result *res)
+{
+    if (!A || !b || !x) return fail(PLCG_ERR_INVALID, "plcg_solve_host: NULL argument");
+    plcg_status st = check_params(A, prm);
+    if (st != PLCG_OK) return st;
+    {
+        std::lock_guard<std::mutex> lock(A->mu);
+        CUDA_TRY(cudaSetDevice(A->device));
+        if (!A->b_dev) CUDA_TRY(cudaMalloc(&A->b_dev, A->n * sizeof(double)));
+        if (!A->x_dev) CUDA_TRY(cudaMalloc(&A->x_dev, A->n * sizeof(double)));
+        CUDA_TRY(cudaMemcpyAsync(A->b_dev, b, A->n * sizeof(double), cudaMemcpyHostToDevice, A->stream));
+        CUDA_TRY(cudaMemcpyAsync(A->x_dev, x, A->n * sizeof(double), cudaMemcpyHostToDevice, A->stream));
+    }
+    st = plcg_solve(A, A->b_dev, A->x_dev, prm, res);
+    if (st == PLCG_ERR_INVALID || st == PLCG_ERR_CUDA || st == PLCG_ERR_UNIMPL || st == PLCG_ERR_NOMEM)
+        return st;
+    std::lock_guard<std::mutex> lock(A->mu);
+    CUDA_TRY(cudaMemcpyAsync(x, A->x_dev, A->n * sizeof(double), cudaMemcpyDeviceToHost, A->stream));
+    CUDA_TRY(cudaStreamSynchronize(A->stream));
+    return st;
+}
+
+extern "C" plcg_status plcg_solve_batched(int count, plcg_matrix *const *A, const double *const *b,
+                                          double *const *x, const double *lmin, const double *lmax,
+                                          const plcg_params *prm, plcg_result *results)
+{
+    (void)count; (void)A; (void)b; (void)x; (void)lmin; (void)lmax; (void)prm; (void)results;
+    return fail(PLCG_ERR_UNIMPL, "plcg_solve_batched: not built yet");
+}

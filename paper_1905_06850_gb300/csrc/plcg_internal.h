@@ -1,0 +1,79 @@
+// plcg_internal.h -- structures shared by the host side of libplcg.so and its
+// kernels.  Not part of the public ABI (include/plcg.h is).
+#pragma once
+
+#include <stdint.h>
+
+namespace plcg {
+
+constexpr int kMaxL = 8;                  // largest pipeline length l
+constexpr int kMaxDots = 2 * kMaxL + 1;   // dot products per iteration (Alg. 1 line 23)
+constexpr int kBlock = 256;               // threads per CTA of the persistent solver
+constexpr int kNormSlots = 2;             // doubles per CTA in the norm partials
+
+enum OpKind : int { kOpStencil = 0, kOpCsr = 1 };
+
+// End reasons of one segment (a run of Algorithm 1 from a residual).
+enum SegEnd : int { kSegConverged = 0, kSegMaxit = 1, kSegBreakdown = 2, kSegLucky = 3,
+                    kSegNonfinite = 4 };
+
+// Device-side result of one solve; written by CTA 0, thread 0.
+struct DevResult {
+    int status;              // plcg_status
+    int abort;               // set by any CTA whose bounded wait expired
+    long long iters;
+    long long spmvs;
+    long long restarts;
+    long long refinements;
+    double recursive_relres;
+    double true_relres;
+};
+
+// Matrix-free constant-coefficient Dirichlet stencil (5-point 2D / 7-point 3D).
+struct StencilDesc {
+    int dim;
+    int nx, ny, nz;
+    double center;   // includes the diagonal shift
+    double off;
+};
+
+// CSR arrays in device memory; val is float or double (see the kernel's T).
+struct CsrDesc {
+    const int64_t *rowptr;
+    const int32_t *col;
+    const void *val;
+};
+
+// Everything one persistent solve needs (passed by value to the kernel).
+template <typename T>
+struct SolveArgs {
+    int64_t n;
+    StencilDesc st;
+    CsrDesc csr;
+    const double *b;          // FP64 right-hand side
+    double *x;                // FP64 iterate (in: x0)
+    double *r;                // FP64 residual b - A x
+    T *zring;                 // ring storage of the l+1 bases (p(l)-CG) / p ring (CG)
+    int depth[kMaxL + 1];     // ring depth of basis k
+    int64_t base[kMaxL + 1];  // offset (in vectors) of basis k's ring
+    T *p;                     // search direction p (p(l)-CG) / q = A p (CG)
+    T *rc;                    // CG: the recursive residual in T (FP32 path)
+    double *part;             // dot partials [(l+1) slots][P][kMaxDots]
+    double *npart;            // norm partials [P][kNormSlots]
+    unsigned int *bar;        // grid barrier arrival counter
+    DevResult *out;
+    // parameters
+    int method;               // 0 = p(l)-CG, 1 = CG
+    int l;
+    double sigma[kMaxL];
+    double rtol;
+    long long maxit;
+    int dots_2l1;
+    int max_restarts;
+    double inner_floor;       // FP32 path: floor of the inner relative tolerance
+    int fp32;                 // 1: T = float with FP64 outer refinement
+    unsigned long long poll_limit;
+    int force_timeout;
+};
+
+}  // namespace plcg

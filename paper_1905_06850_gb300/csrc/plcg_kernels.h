@@ -1,0 +1,24 @@
+// plcg_kernels.h -- host-visible entry points of the kernel translation units.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+namespace plcg {
+
+// Address of the persistent solver for (FP32 path?, operator, vector width,
+// pipeline length l, classic CG?); nullptr when not instantiated.
+const void *kernel_ptr(bool f32, int op, int vec, int l, bool cg);
+
+// Per-translation-unit getters used by kernel_ptr.
+const void *kptr_f64_st2(int l, bool cg);
+const void *kptr_f64_st1(int l, bool cg);
+const void *kptr_f64_csr(int l, bool cg);
+const void *kptr_f32_st4(int l, bool cg);
+const void *kptr_f32_st1(int l, bool cg);
+const void *kptr_f32_csr(int l, bool cg);
+
+// dst[i] = (float) src[i] on the device.
+cudaError_t launch_round_to_f32(const double *src, float *dst, int64_t n, cudaStream_t s);
+
+}  // namespace plcg

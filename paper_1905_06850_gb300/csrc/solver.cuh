@@ -1,0 +1,976 @@
+// solver.cuh -- the persistent single-launch solvers of libplcg.so (sm_103a).
+//
+// One cooperative launch runs a whole solve: ||b||, residuals, every
+// iteration of every segment (Algorithm 1 of Cools et al., EuroMPI'19, with
+// M = I, or classic CG), restarts after square-root breakdowns (Sec. 2.2) and,
+// on the FP32 path, the FP64 refinement loop.  Thread blocks (CTAs) own
+// interleaved units of rows; one bounded grid barrier separates iterations
+// (the SpMV of iteration i+1 reads neighbours written in iteration i).
+//
+// The global reduction of Alg. 2 (MPI_Iallreduce, consumed by MPI_Wait l
+// iterations later) becomes: each CTA writes its FP64 dot partials into ring
+// slot i mod (l+1) before the barrier, and at iteration i+l every CTA sums the
+// slot's partials itself in a fixed order, so all CTAs hold bit-identical
+// G entries and run the O(l^2) scalar work (K2, K3, K6 scalars) redundantly,
+// with no extra barrier and no single-CTA serialisation.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <float.h>
+#include <stdint.h>
+
+#include "plcg_internal.h"
+
+namespace plcg {
+
+// plcg_status values used on the device (mirrors include/plcg.h).
+enum : int { kStOk = 0, kStBreakdown = -4, kStMaxit = -5, kStNonfinite = -6, kStTimeout = -7 };
+
+constexpr int kMaxRefine = 64;   // FP32 path: cap on FP64 refinement steps
+
+// ------------------------------------------------------------------------
+// Memory-model helpers for the grid barrier.
+// ------------------------------------------------------------------------
+__device__ __forceinline__ unsigned ld_acquire_u32(const unsigned *p)
+{
+    unsigned v;
+    asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+    return v;
+}
+
+__device__ __forceinline__ void red_release_add_u32(unsigned *p, unsigned v)
+{
+    asm volatile("red.release.gpu.global.add.u32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
+}
+
+__device__ __forceinline__ int ld_volatile(const int *p) { return *(volatile const int *)p; }
+
+// Bounded grid-wide barrier.  Every CTA adds 1 to *bar; the barrier of epoch
+// e is passed when *bar reaches e * gridDim.x.  Returns false when the poll
+// bound ran out (the CTA then sets the abort flag) or another CTA aborted;
+// the caller must then leave the kernel.  force_timeout adds one phantom
+// arrival to the target so that the wait runs out (test hook).
+__device__ __forceinline__ bool grid_barrier(unsigned *bar, unsigned &epoch,
+                                             unsigned long long limit, int force,
+                                             int *abort_flag, int *s_ok)
+{
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        epoch += 1u;
+        const unsigned target = epoch * gridDim.x + (force ? 1u : 0u);
+        __threadfence();
+        red_release_add_u32(bar, 1u);
+        int ok = 1;
+        unsigned long long polls = 0;
+        while ((int)(ld_acquire_u32(bar) - target) < 0) {
+            if (ld_volatile(abort_flag)) { ok = 0; break; }
+            if (++polls > limit) { atomicExch(abort_flag, 1); ok = 0; break; }
+            __nanosleep(64);
+        }
+        if (ok && ld_volatile(abort_flag)) ok = 0;
+        __threadfence();
+        *s_ok = ok;
+    }
+    __syncthreads();
+    return *s_ok != 0;
+}
+
+// ------------------------------------------------------------------------
+// Reductions (fixed order, so every CTA gets the same bits).
+// ------------------------------------------------------------------------
+template <int ND>
+__device__ __forceinline__ void block_sum(double (&v)[ND], double *s_red, double *s_out)
+{
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+#pragma unroll
+    for (int q = 0; q < ND; ++q) {
+        double t = v[q];
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) t += __shfl_down_sync(0xffffffffu, t, o);
+        if (lane == 0) s_red[warp * ND + q] = t;
+    }
+    __syncthreads();
+    if (threadIdx.x < ND) {
+        double s = 0.0;
+        for (int w = 0; w < kBlock / 32; ++w) s += s_red[w * ND + threadIdx.x];
+        s_out[threadIdx.x] = s;
+    }
+    __syncthreads();
+}
+
+// Sum over all CTAs of part[c * stride + q], q < ND; result in s_out[q].
+template <int ND>
+__device__ __forceinline__ void grid_partials_sum(const double *part, int stride, double *s_red,
+                                                  double *s_out)
+{
+    double v[ND];
+#pragma unroll
+    for (int q = 0; q < ND; ++q) v[q] = 0.0;
+    for (int c = threadIdx.x; c < (int)gridDim.x; c += kBlock) {
+#pragma unroll
+        for (int q = 0; q < ND; ++q) v[q] += __ldcg(part + (size_t)c * stride + q);
+    }
+    block_sum<ND>(v, s_red, s_out);
+}
+
+// ------------------------------------------------------------------------
+// Vector loads/stores of VEC consecutive elements (128-bit when VEC*sizeof = 16).
+// ------------------------------------------------------------------------
+template <typename V, int VEC>
+__device__ __forceinline__ void vld(const V *p, V (&o)[VEC])
+{
+    if constexpr (VEC == 1) {
+        o[0] = *p;
+    } else if constexpr (sizeof(V) == 8 && VEC == 2) {
+        const double2 t = *reinterpret_cast<const double2 *>(p);
+        o[0] = t.x; o[1] = t.y;
+    } else if constexpr (sizeof(V) == 4 && VEC == 4) {
+        const float4 t = *reinterpret_cast<const float4 *>(p);
+        o[0] = t.x; o[1] = t.y; o[2] = t.z; o[3] = t.w;
+    } else if constexpr (sizeof(V) == 4 && VEC == 2) {
+        const float2 t = *reinterpret_cast<const float2 *>(p);
+        o[0] = t.x; o[1] = t.y;
+    } else {
+#pragma unroll
+        for (int v = 0; v < VEC; ++v) o[v] = p[v];
+    }
+}
+
+template <typename V, int VEC>
+__device__ __forceinline__ void vldg(const V *p, V (&o)[VEC])   // read-only data (b, CSR)
+{
+    if constexpr (VEC == 1) {
+        o[0] = __ldg(p);
+    } else if constexpr (sizeof(V) == 8 && VEC == 2) {
+        const double2 t = __ldg(reinterpret_cast<const double2 *>(p));
+        o[0] = t.x; o[1] = t.y;
+    } else {
+#pragma unroll
+        for (int v = 0; v < VEC; ++v) o[v] = __ldg(p + v);
+    }
+}
+
+template <typename V, int VEC>
+__device__ __forceinline__ void vst(V *p, const V (&o)[VEC])
+{
+    if constexpr (VEC == 1) {
+        *p = o[0];
+    } else if constexpr (sizeof(V) == 8 && VEC == 2) {
+        *reinterpret_cast<double2 *>(p) = make_double2(o[0], o[1]);
+    } else if constexpr (sizeof(V) == 4 && VEC == 4) {
+        *reinterpret_cast<float4 *>(p) = make_float4(o[0], o[1], o[2], o[3]);
+    } else if constexpr (sizeof(V) == 4 && VEC == 2) {
+        *reinterpret_cast<float2 *>(p) = make_float2(o[0], o[1]);
+    } else {
+#pragma unroll
+        for (int v = 0; v < VEC; ++v) p[v] = o[v];
+    }
+}
+
+// ------------------------------------------------------------------------
+// Operand loaders for the SpMV: one vector, or r + beta * p (classic CG).
+// ------------------------------------------------------------------------
+template <typename V>
+struct Ld1 {
+    const V *z;
+    template <int VEC>
+    __device__ __forceinline__ void vec(int64_t g, V (&o)[VEC]) const { vld<V, VEC>(z + g, o); }
+    __device__ __forceinline__ V one(int64_t g) const { return z[g]; }
+};
+
+template <typename V>
+struct LdAxpy {           // value = a[g] + beta * b[g]
+    const V *a;
+    const V *b;
+    V beta;
+    template <int VEC>
+    __device__ __forceinline__ void vec(int64_t g, V (&o)[VEC]) const
+    {
+        V t[VEC];
+        vld<V, VEC>(a + g, o);
+        vld<V, VEC>(b + g, t);
+#pragma unroll
+        for (int v = 0; v < VEC; ++v) o[v] = fma(beta, t[v], o[v]);
+    }
+    __device__ __forceinline__ V one(int64_t g) const { return fma(beta, b[g], a[g]); }
+};
+
+template <typename V>
+struct LdFirst {          // value = a[g] (CG first step, p_0 = r_0)
+    const V *a;
+    template <int VEC>
+    __device__ __forceinline__ void vec(int64_t g, V (&o)[VEC]) const { vld<V, VEC>(a + g, o); }
+    __device__ __forceinline__ V one(int64_t g) const { return a[g]; }
+};
+
+// ------------------------------------------------------------------------
+// Operators.  apply() returns the centre values c and w = (A z) for the VEC
+// rows g0 .. g0+VEC-1 (stencil: nx % VEC == 0, so they share y and z).
+// ------------------------------------------------------------------------
+template <typename V, int VEC, class Ld>
+__device__ __forceinline__ void stencil_apply(const StencilDesc &st, V cC, V cO, const Ld &ld,
+                                              int64_t g0, V (&c)[VEC], V (&w)[VEC])
+{
+    const int nx = st.nx, ny = st.ny;
+    const int64_t line = g0 / nx;
+    const int x0 = (int)(g0 - line * nx);
+    const int y = (int)(line % ny);
+    const int64_t zc = line / ny;
+    ld.template vec<VEC>(g0, c);
+    V nb[VEC];
+    const V left = (x0 > 0) ? ld.one(g0 - 1) : V(0);
+    const V right = (x0 + VEC < nx) ? ld.one(g0 + VEC) : V(0);
+#pragma unroll
+    for (int v = 0; v < VEC; ++v)
+        nb[v] = ((v > 0) ? c[v - 1] : left) + ((v < VEC - 1) ? c[v + 1] : right);
+    V t[VEC];
+    if (y > 0) {
+        ld.template vec<VEC>(g0 - nx, t);
+#pragma unroll
+        for (int v = 0; v < VEC; ++v) nb[v] += t[v];
+    }
+    if (y < ny - 1) {
+        ld.template vec<VEC>(g0 + nx, t);
+#pragma unroll
+        for (int v = 0; v < VEC; ++v) nb[v] += t[v];
+    }
+    if (st.dim == 3) {
+        const int64_t nxy = (int64_t)nx * ny;
+        if (zc > 0) {
+            ld.template vec<VEC>(g0 - nxy, t);
+#pragma unroll
+            for (int v = 0; v < VEC; ++v) nb[v] += t[v];
+        }
+        if (zc < st.nz - 1) {
+            ld.template vec<VEC>(g0 + nxy, t);
+#pragma unroll
+            for (int v = 0; v < VEC; ++v) nb[v] += t[v];
+        }
+    }
+#pragma unroll
+    for (int v = 0; v < VEC; ++v) w[v] = fma(cO, nb[v], cC * c[v]);
+}
+
+// CSR row (VEC = 1).  C is the stored value type (float or double).
+template <typename V, typename C, class Ld>
+__device__ __forceinline__ V csr_row(const CsrDesc &A, const Ld &ld, int64_t row)
+{
+    const C *val = static_cast<const C *>(A.val);
+    const int64_t e0 = __ldg(A.rowptr + row), e1 = __ldg(A.rowptr + row + 1);
+    V s = V(0);
+    for (int64_t e = e0; e < e1; ++e) s = fma((V)__ldg(val + e), ld.one(__ldg(A.col + e)), s);
+    return s;
+}
+
+template <typename V, typename C, int VEC, int OP, class Ld>
+__device__ __forceinline__ void op_apply(const SolveArgs<C> &a, V cC, V cO, const Ld &ld,
+                                         int64_t g0, V (&c)[VEC], V (&w)[VEC])
+{
+    if constexpr (OP == kOpStencil) {
+        stencil_apply<V, VEC>(a.st, cC, cO, ld, g0, c, w);
+    } else {
+        static_assert(VEC == 1, "CSR rows are one per thread");
+        c[0] = ld.one(g0);
+        w[0] = csr_row<V, C>(a.csr, ld, g0);
+    }
+}
+
+// ------------------------------------------------------------------------
+// Shared-memory state of one CTA.
+// ------------------------------------------------------------------------
+template <typename T>
+struct Coef {
+    int mode;                 // 0: fill (i < l), 1: recurrences (i >= l)
+    int k6;                   // 0: none, 1: p_0 = v_0 / eta_0, 2: x and p update
+    int end;                  // -1: continue, else SegEnd
+    int fmode;                // final sweep: 0 x += f1 p; 1 lucky (m >= 1); 2 lucky (m = 0)
+    int prev0;                // z^(0)_{m-1} exists
+    int ncopy;
+    long long kseg;           // k of the iterate the segment returns (when end >= 0)
+    T sig, invd, al, bm;
+    T ak[kMaxL];
+    T zx, pv, pp;
+    T f1, f2;
+    int dsrc[kMaxDots];       // 0 off, 1 memory, 2 new u, 3 new v, 4 z^(l)_i, 5 z^(l)_{i-1}
+    const T *dptr[kMaxDots];
+    const T *zl_cur;
+    const T *zl_prev;
+    T *zl_new;
+    const T *cur[kMaxL];
+    const T *prv[kMaxL];
+    T *nw[kMaxL];
+    T *cpy[kMaxL];
+    const T *v0;              // final sweep: z^(0)_m
+};
+
+template <typename T>
+struct Smem {
+    double red[(kBlock / 32) * kMaxDots];
+    double out[kMaxDots + 2];
+    double raw[kMaxDots];
+    double G[kMaxL + 1][kMaxDots];   // finalised columns c-l .. c (column c at c mod (l+1))
+    double gam[kMaxL + 1], del[kMaxL + 1];
+    double eta[2], zeta[2];
+    Coef<T> cf;
+    int ok;
+};
+
+template <typename T> struct Eps;
+template <> struct Eps<double> { static constexpr double v = DBL_EPSILON; };
+template <> struct Eps<float> { static constexpr double v = (double)FLT_EPSILON; };
+
+template <typename T>
+__device__ __forceinline__ T *ring(const SolveArgs<T> &a, int k, long long j)
+{
+    return a.zring + (a.base[k] + (j % a.depth[k])) * a.n;
+}
+
+// ------------------------------------------------------------------------
+// Scalar step of iteration i (thread 0 of every CTA; all CTAs compute the
+// same bits).  K2: finalise column c = i-l+1 of G (Alg. 1 lines 9-10);
+// line 11: breakdown check; K3: gamma_{i-l}, delta_{i-l} (lines 12-18);
+// K6 scalars: lambda, eta, zeta and the stop test (lines 24-33).
+// ------------------------------------------------------------------------
+template <typename T, int L>
+__device__ void scalar_step(Smem<T> &s, const SolveArgs<T> &a, long long i, double rn,
+                            double tau, long long budget)
+{
+    Coef<T> &cf = s.cf;
+    cf.end = -1;
+    cf.fmode = 0;
+    cf.ncopy = 0;
+    const long long m = i - L;
+    if (i < L) {
+        cf.mode = 0;
+        cf.k6 = 0;
+        cf.sig = (T)a.sigma[i];
+    } else {
+        const long long c = i - L + 1;
+        double *col = s.G[c % (L + 1)];
+        auto g = [&](long long j, long long cc) -> double {
+            if (j < 0 || j < cc - 2 * L || j > cc) return 0.0;
+            return s.G[cc % (L + 1)][j - cc + 2 * L];
+        };
+        auto del = [&](long long j) -> double { return j < 0 ? 0.0 : s.del[j % (L + 1)]; };
+        auto gam = [&](long long j) -> double { return s.gam[j % (L + 1)]; };
+        // raw column c (dots of iteration i-l): position q is row c-2l+q
+#pragma unroll
+        for (int q = 0; q <= 2 * L; ++q) col[q] = (c - 2 * L + q >= 0) ? s.raw[q] : 0.0;
+        const long long lo = (c - 2 * L > 0) ? c - 2 * L : 0;
+        if (!a.dots_2l1)   // Sec. 2.2: g_{j,c} = g_{c-l,j+l} for j = c-2l .. c-l-1
+            for (long long j = lo; j <= c - L - 1; ++j) col[j - c + 2 * L] = g(c - L, j + L);
+        for (long long j = (c - L + 1 > 0 ? c - L + 1 : 0); j <= c - 1; ++j) {
+            double t = col[j - c + 2 * L];
+            for (long long k = lo; k <= j - 1; ++k) t -= g(k, j) * col[k - c + 2 * L];
+            col[j - c + 2 * L] = t / g(j, j);
+        }
+        const double graw = col[2 * L];
+        double arg = graw;
+        for (long long k = lo; k <= c - 1; ++k) arg -= col[k - c + 2 * L] * col[k - c + 2 * L];
+        const double gmm = g(m, m);
+        const double gmc = col[m - c + 2 * L];
+        double gm;
+        if (m < L)
+            gm = (gmc + a.sigma[m] * gmm - (m >= 1 ? g(m - 1, m) * del(m - 1) : 0.0)) / gmm;
+        else
+            gm = (gmm * gam(m - L) + gmc * del(m - L) - g(m - 1, m) * del(m - 1)) / gmm;
+        s.gam[m % (L + 1)] = gm;
+        const double thr = 64.0 * Eps<T>::v * fabs(graw);
+        if (!isfinite(arg) || !isfinite(gm)) {
+            cf.end = kSegNonfinite;
+            cf.kseg = m;
+            return;
+        }
+        if (arg <= thr) {
+            if (arg >= -thr) {   // lucky breakdown: x_{m+1} is exact in this Krylov space
+                if (m == 0) {
+                    s.eta[0] = gm;
+                    s.zeta[0] = rn;
+                    cf.fmode = 2;
+                    cf.pv = (T)(1.0 / gm);
+                    cf.f2 = (T)rn;
+                } else {
+                    const double lam = del(m - 1) / s.eta[(m - 1) & 1];
+                    const double em = gm - lam * del(m - 1);
+                    const double zm = -lam * s.zeta[(m - 1) & 1];
+                    cf.fmode = 1;
+                    cf.f1 = (T)s.zeta[(m - 1) & 1];
+                    cf.pv = (T)(1.0 / em);
+                    cf.pp = (T)(-del(m - 1) / em);
+                    cf.f2 = (T)zm;
+                }
+                cf.end = kSegLucky;
+                cf.kseg = m + 1;
+            } else {             // breakdown: keep x_m and restart
+                cf.fmode = 0;
+                cf.f1 = (T)((m >= 1) ? s.zeta[(m - 1) & 1] : 0.0);
+                cf.end = kSegBreakdown;
+                cf.kseg = m;
+            }
+            cf.v0 = ring(a, 0, m);
+            return;
+        }
+        col[2 * L] = sqrt(arg);
+        const double dm = (m < L) ? col[2 * L] / gmm : col[2 * L] * del(m - L) / gmm;
+        s.del[m % (L + 1)] = dm;
+        const double invd = 1.0 / dm;
+        cf.mode = 1;
+        cf.invd = (T)invd;
+        cf.al = (T)(-gm * invd);
+        cf.bm = (T)((m >= 1) ? -del(m - 1) * invd : 0.0);
+        cf.prev0 = (m >= 1);
+#pragma unroll
+        for (int k = 0; k < L; ++k) cf.ak[k] = (T)((a.sigma[k] - gm) * invd);
+        if (i == L) {
+            s.eta[0] = gm;
+            s.zeta[0] = rn;
+            cf.k6 = 1;
+            cf.pv = (T)(1.0 / gm);
+        } else {
+            const double lam = del(m - 1) / s.eta[(m - 1) & 1];
+            const double em = gm - lam * del(m - 1);
+            const double zm = -lam * s.zeta[(m - 1) & 1];
+            cf.k6 = 2;
+            cf.zx = (T)s.zeta[(m - 1) & 1];
+            cf.pv = (T)(1.0 / em);
+            cf.pp = (T)(-del(m - 1) / em);
+            s.eta[m & 1] = em;
+            s.zeta[m & 1] = zm;
+            if (!isfinite(zm)) {
+                cf.end = kSegNonfinite;
+                cf.kseg = m;
+                return;
+            }
+            if (fabs(zm) < tau || m >= budget) {
+                cf.end = (fabs(zm) < tau) ? kSegConverged : kSegMaxit;
+                cf.fmode = 0;
+                cf.f1 = cf.zx;
+                cf.kseg = m;
+                cf.v0 = ring(a, 0, m);
+                return;
+            }
+        }
+    }
+    // vectors of this iteration
+    cf.zl_cur = ring(a, L, i);
+    cf.zl_prev = (i >= 1) ? ring(a, L, i - 1) : nullptr;
+    cf.zl_new = ring(a, L, i + 1);
+    if (cf.mode == 0) {
+        for (int k = (int)i + 1; k <= L - 1; ++k) cf.cpy[cf.ncopy++] = ring(a, k, i + 1);
+    } else {
+#pragma unroll
+        for (int k = 0; k < L; ++k) {
+            cf.cur[k] = ring(a, k, m + k);
+            cf.prv[k] = (m + k - 1 >= 0) ? ring(a, k, m + k - 1) : nullptr;
+            cf.nw[k] = ring(a, k, m + k + 1);
+        }
+    }
+    // K5 operands: position q is row j = i-2l+1+q of column i+1 (Alg. 1 line 23)
+#pragma unroll
+    for (int q = 0; q <= 2 * L; ++q) {
+        const long long j = i - 2 * L + 1 + q;
+        int src = 0;
+        const T *ptr = nullptr;
+        if (j >= 0) {
+            if (q < L) {
+                if (a.dots_2l1) { src = 1; ptr = ring(a, 0, j); }
+            } else if (q == L) {
+                if (i >= L) src = 3;
+                else { src = 1; ptr = ring(a, 0, j); }
+            } else {
+                if (j == i + 1) src = 2;
+                else if (j == i) src = 4;
+                else if (j == i - 1 && cf.mode == 1) src = 5;
+                else { src = 1; ptr = ring(a, L, j); }
+            }
+        }
+        cf.dsrc[q] = src;
+        cf.dptr[q] = ptr;
+    }
+}
+
+// Accumulate a*b into an FP64 sum.
+template <typename T>
+__device__ __forceinline__ double dacc(double acc, T a, T b)
+{
+    return fma((double)a, (double)b, acc);
+}
+
+// ------------------------------------------------------------------------
+// Residual sweep: r = b - A x (FP64; the stored operator values widened),
+// partial ||r||^2 and ||b||^2.  Units of kBlock * V64 rows.
+// ------------------------------------------------------------------------
+template <typename T, int VEC, int OP>
+__device__ void residual_sweep(const SolveArgs<T> &a, Smem<T> &s)
+{
+    constexpr int V64 = (VEC >= 2) ? 2 : 1;
+    constexpr int UNIT = kBlock * V64;
+    const int64_t n = a.n;
+    const int64_t nunits = (n + UNIT - 1) / UNIT;
+    const double cC = (double)(T)a.st.center, cO = (double)(T)a.st.off;
+    double acc[2] = {0.0, 0.0};
+    Ld1<double> ld{a.x};
+    for (int64_t u = blockIdx.x; u < nunits; u += gridDim.x) {
+        const int64_t g0 = u * UNIT + (int64_t)threadIdx.x * V64;
+        if (g0 >= n) continue;
+        double c[V64], w[V64], bv[V64];
+        if constexpr (OP == kOpStencil) {
+            stencil_apply<double, V64>(a.st, cC, cO, ld, g0, c, w);
+        } else {
+            c[0] = a.x[g0];
+            w[0] = csr_row<double, T>(a.csr, ld, g0);
+        }
+        vldg<double, V64>(a.b + g0, bv);
+        double rv[V64];
+#pragma unroll
+        for (int v = 0; v < V64; ++v) {
+            rv[v] = bv[v] - w[v];
+            acc[0] = fma(bv[v], bv[v], acc[0]);
+            acc[1] = fma(rv[v], rv[v], acc[1]);
+        }
+        vst<double, V64>(a.r + g0, rv);
+    }
+    block_sum<2>(acc, s.red, s.out);
+    if (threadIdx.x == 0) {
+        a.npart[(size_t)blockIdx.x * kNormSlots + 0] = s.out[0];
+        a.npart[(size_t)blockIdx.x * kNormSlots + 1] = s.out[1];
+    }
+}
+
+// ------------------------------------------------------------------------
+// The p(l)-CG persistent kernel.
+// ------------------------------------------------------------------------
+template <typename T, int L, int VEC, int OP>
+__global__ void __launch_bounds__(kBlock) plcg_kernel(SolveArgs<T> a)
+{
+    __shared__ Smem<T> s;
+    constexpr int UNIT = kBlock * VEC;
+    constexpr bool kF32 = (sizeof(T) == 4);
+    const int64_t n = a.n;
+    const int64_t nunits = (n + UNIT - 1) / UNIT;
+    const int tid = threadIdx.x;
+    unsigned epoch = 0;
+    const T cC = (T)a.st.center, cO = (T)a.st.off;
+    // xi: the iterate K6 updates (FP64 path: x itself; FP32 path: the inner
+    // correction d, stored in the p-ring's spare vector)
+    T *xi = kF32 ? a.rc : reinterpret_cast<T *>(a.x);
+
+    long long iters = 0, spmvs = 0, restarts = 0, refinements = 0, segments = 0;
+    int last_end = kSegConverged;
+    double normb = 0.0, recres = 0.0, last_rn = 0.0;
+    int status = kStOk;
+
+#define PLCG_BARRIER()                                                                       \
+    do {                                                                                     \
+        if (!grid_barrier(a.bar, epoch, a.poll_limit, a.force_timeout, &a.out->abort,       \
+                          &s.ok)) {                                                          \
+            status = kStTimeout;                                                             \
+            goto finish;                                                                     \
+        }                                                                                    \
+    } while (0)
+
+    for (;;) {
+        // ---- true residual r = b - A x and its norm (Alg. 1 line 1 / the final check)
+        residual_sweep<T, VEC, OP>(a, s);
+        spmvs++;
+        PLCG_BARRIER();
+        grid_partials_sum<2>(a.npart, kNormSlots, s.red, s.out);
+        if (segments == 0) normb = sqrt(s.out[0]);
+        const double rn = sqrt(s.out[1]);
+        last_rn = rn;
+        if (normb == 0.0) {
+            // b = 0: x = 0 is the solution
+            for (int64_t g = (int64_t)blockIdx.x * kBlock + tid; g < n; g += (int64_t)gridDim.x * kBlock)
+                a.x[g] = 0.0;
+            status = kStOk;
+            break;
+        }
+        if (!isfinite(normb) || !isfinite(rn)) { status = kStNonfinite; break; }
+        if (rn < a.rtol * normb) { status = kStOk; recres = (segments == 0) ? rn : recres; break; }
+        if (iters >= a.maxit) { status = kStMaxit; break; }
+        if (segments > 0) {
+            if (kF32 && (last_end == kSegConverged || last_end == kSegLucky)) {
+                if (++refinements > kMaxRefine) { status = kStMaxit; break; }
+            } else {
+                if (restarts >= a.max_restarts) {
+                    status = (last_end == kSegMaxit) ? kStMaxit : kStBreakdown;
+                    break;
+                }
+                restarts++;
+            }
+        }
+        const double tau = kF32 ? fmax(a.inner_floor * rn, 0.5 * a.rtol * normb) : a.rtol * normb;
+        const long long budget = a.maxit - iters;
+
+        // ---- Alg. 1 line 1: z^(k)_0 := u_0 := r_0 / ||r_0|| for every k; g_00 := 1
+        {
+            const double inv = 1.0 / rn;
+            for (int64_t u = blockIdx.x; u < nunits; u += gridDim.x) {
+                const int64_t g0 = u * UNIT + (int64_t)tid * VEC;
+                if (g0 >= n) continue;
+                T z[VEC];
+#pragma unroll
+                for (int v = 0; v < VEC; ++v) z[v] = (T)(a.r[g0 + v] * inv);
+#pragma unroll
+                for (int k = 0; k <= L; ++k) vst<T, VEC>(ring(a, k, 0) + g0, z);
+                if constexpr (kF32) {
+                    T zero[VEC];
+#pragma unroll
+                    for (int v = 0; v < VEC; ++v) zero[v] = T(0);
+                    vst<T, VEC>(xi + g0, zero);
+                }
+            }
+            if (tid == 0) {
+#pragma unroll
+                for (int q = 0; q < kMaxDots; ++q) s.G[0][q] = 0.0;
+                s.G[0][2 * L] = 1.0;
+            }
+        }
+        PLCG_BARRIER();
+
+        for (long long i = 0;; ++i) {
+            if (i >= L) {   // MPI_Wait(req(i-l)): sum the partials of iteration i-l
+                grid_partials_sum<2 * L + 1>(a.part + (size_t)((i - L) % (L + 1)) * gridDim.x * kMaxDots,
+                                             kMaxDots, s.red, s.raw);
+            }
+            if (tid == 0) scalar_step<T, L>(s, a, i, rn, tau, budget);
+            __syncthreads();
+            const Coef<T> &cf = s.cf;
+            if (cf.end >= 0) {
+                // ---- final vector update of the segment
+                if (cf.end != kSegNonfinite) {
+                    for (int64_t u = blockIdx.x; u < nunits; u += gridDim.x) {
+                        const int64_t g0 = u * UNIT + (int64_t)tid * VEC;
+                        if (g0 >= n) continue;
+                        T xv[VEC], pv[VEC];
+                        vld<T, VEC>(xi + g0, xv);
+                        if (cf.fmode == 0) {
+                            if (cf.f1 != T(0)) {
+                                vld<T, VEC>(a.p + g0, pv);
+#pragma unroll
+                                for (int v = 0; v < VEC; ++v) xv[v] = fma(cf.f1, pv[v], xv[v]);
+                            }
+                        } else {
+                            T vv[VEC];
+                            vld<T, VEC>(cf.v0 + g0, vv);
+                            if (cf.fmode == 1) {
+                                vld<T, VEC>(a.p + g0, pv);
+#pragma unroll
+                                for (int v = 0; v < VEC; ++v) {
+                                    xv[v] = fma(cf.f1, pv[v], xv[v]);
+                                    const T pn = fma(cf.pv, vv[v], cf.pp * pv[v]);
+                                    xv[v] = fma(cf.f2, pn, xv[v]);
+                                }
+                            } else {
+#pragma unroll
+                                for (int v = 0; v < VEC; ++v) xv[v] = fma(cf.f2, cf.pv * vv[v], xv[v]);
+                            }
+                        }
+                        if constexpr (kF32) {
+#pragma unroll
+                            for (int v = 0; v < VEC; ++v) a.x[g0 + v] += (double)xv[v];
+                        } else {
+                            vst<T, VEC>(xi + g0, xv);
+                        }
+                    }
+                }
+                iters += cf.kseg;
+                last_end = cf.end;
+                segments++;
+                if (cf.end == kSegNonfinite) { status = kStNonfinite; goto finish; }
+                {
+                    // |zeta| of the returned iterate for the report
+                    const long long mm = cf.kseg;
+                    recres = (cf.end == kSegLucky) ? 0.0 : fabs(s.zeta[mm & 1]);
+                }
+                PLCG_BARRIER();
+                break;
+            }
+
+            // ---- one full iteration sweep: K1, K4, K5 (partials), K6
+            double acc[2 * L + 1];
+#pragma unroll
+            for (int q = 0; q <= 2 * L; ++q) acc[q] = 0.0;
+            for (int64_t u = blockIdx.x; u < nunits; u += gridDim.x) {
+                const int64_t g0 = u * UNIT + (int64_t)tid * VEC;
+                if (g0 >= n) continue;
+                T c[VEC], w[VEC], un[VEC];
+                op_apply<T, T, VEC, OP>(a, cC, cO, Ld1<T>{cf.zl_cur}, g0, c, w);   // K1
+                T zp[VEC];
+                T cur[L][VEC];
+                T nv0[VEC];
+                if (cf.mode == 0) {
+#pragma unroll
+                    for (int v = 0; v < VEC; ++v) un[v] = fma(-cf.sig, c[v], w[v]);
+                    vst<T, VEC>(cf.zl_new + g0, un);
+                    for (int k = 0; k < cf.ncopy; ++k) vst<T, VEC>(cf.cpy[k] + g0, un);
+                } else {
+                    // K4: z^(l)_{i+1} and z^(k)_{i-l+k+1}, k < l (Alg. 1 lines 19-21)
+                    vld<T, VEC>(cf.zl_prev + g0, zp);
+#pragma unroll
+                    for (int v = 0; v < VEC; ++v)
+                        un[v] = fma(w[v], cf.invd, fma(cf.al, c[v], cf.bm * zp[v]));
+                    vst<T, VEC>(cf.zl_new + g0, un);
+#pragma unroll
+                    for (int k = 0; k < L; ++k) vld<T, VEC>(cf.cur[k] + g0, cur[k]);
+#pragma unroll
+                    for (int k = 0; k < L; ++k) {
+                        T pk[VEC];
+                        if (k > 0 || cf.prev0) {
+                            vld<T, VEC>(cf.prv[k] + g0, pk);
+                        } else {
+#pragma unroll
+                            for (int v = 0; v < VEC; ++v) pk[v] = T(0);
+                        }
+                        T nk[VEC];
+#pragma unroll
+                        for (int v = 0; v < VEC; ++v) {
+                            const T up = (k == L - 1) ? c[v] : cur[k + 1][v];
+                            nk[v] = fma(up, cf.invd, fma(cf.ak[k], cur[k][v], cf.bm * pk[v]));
+                        }
+                        vst<T, VEC>(cf.nw[k] + g0, nk);
+                        if (k == 0) {
+#pragma unroll
+                            for (int v = 0; v < VEC; ++v) nv0[v] = nk[v];
+                        }
+                    }
+                }
+                // K5: partial dot products with u_{i+1} = z^(l)_{i+1}
+#pragma unroll
+                for (int q = 0; q <= 2 * L; ++q) {
+                    const int src = cf.dsrc[q];
+                    if (src == 0) continue;
+                    T o[VEC];
+                    if (src == 1) vld<T, VEC>(cf.dptr[q] + g0, o);
+#pragma unroll
+                    for (int v = 0; v < VEC; ++v) {
+                        const T val = (src == 1) ? o[v] : (src == 2) ? un[v] : (src == 3) ? nv0[v]
+                                    : (src == 4) ? c[v] : zp[v];
+                        acc[q] = dacc(acc[q], un[v], val);
+                    }
+                }
+                // K6: p and the iterate (Alg. 1 lines 26-31)
+                if (cf.k6 == 1) {
+                    T pn[VEC];
+#pragma unroll
+                    for (int v = 0; v < VEC; ++v) pn[v] = cf.pv * cur[0][v];
+                    vst<T, VEC>(a.p + g0, pn);
+                } else if (cf.k6 == 2) {
+                    T pv[VEC], xv[VEC];
+                    vld<T, VEC>(a.p + g0, pv);
+                    vld<T, VEC>(xi + g0, xv);
+#pragma unroll
+                    for (int v = 0; v < VEC; ++v) {
+                        xv[v] = fma(cf.zx, pv[v], xv[v]);
+                        pv[v] = fma(cf.pv, cur[0][v], cf.pp * pv[v]);
+                    }
+                    vst<T, VEC>(xi + g0, xv);
+                    vst<T, VEC>(a.p + g0, pv);
+                }
+            }
+            spmvs++;
+            // MPI_Iallreduce(..., req(i)): publish this CTA's partials in slot i mod (l+1)
+            block_sum<2 * L + 1>(acc, s.red, s.out);
+            if (tid <= 2 * L)
+                a.part[((size_t)(i % (L + 1)) * gridDim.x + blockIdx.x) * kMaxDots + tid] = s.out[tid];
+            PLCG_BARRIER();
+        }
+    }
+finish:
+    if (blockIdx.x == 0 && tid == 0) {
+        DevResult *o = a.out;
+        o->status = (ld_volatile(&o->abort) && status == kStOk) ? kStTimeout : status;
+        o->iters = iters;
+        o->spmvs = spmvs;
+        o->restarts = restarts;
+        o->refinements = refinements;
+        o->recursive_relres = (normb > 0.0) ? recres / normb : 0.0;
+        o->true_relres = (normb > 0.0) ? last_rn / normb : 0.0;
+    }
+#undef PLCG_BARRIER
+}
+
+// ------------------------------------------------------------------------
+// Classic CG (Hestenes-Stiefel) persistent kernel: two barriers per
+// iteration (after (p, Ap) and after (r, r)).  p lives in a ring of two
+// vectors because the SpMV of step k reads neighbours of p_k while p_{k+1}
+// is written.  q = A p is in a.p; the recursive residual is r itself on the
+// FP64 path and a.rc (FP32) on the FP32 path, whose inner iterate is the
+// ring's third vector.
+// ------------------------------------------------------------------------
+template <typename T, int VEC, int OP>
+__global__ void __launch_bounds__(kBlock) cg_kernel(SolveArgs<T> a)
+{
+    __shared__ Smem<T> s;
+    constexpr int UNIT = kBlock * VEC;
+    constexpr bool kF32 = (sizeof(T) == 4);
+    const int64_t n = a.n;
+    const int64_t nunits = (n + UNIT - 1) / UNIT;
+    const int tid = threadIdx.x;
+    unsigned epoch = 0;
+    const T cC = (T)a.st.center, cO = (T)a.st.off;
+    T *pr[2] = {a.zring, a.zring + n};
+    T *q = a.p;
+    T *rc = kF32 ? a.rc : reinterpret_cast<T *>(a.r);
+    T *xi = kF32 ? a.zring + 2 * n : reinterpret_cast<T *>(a.x);
+
+    long long iters = 0, spmvs = 0, restarts = 0, refinements = 0, segments = 0;
+    int last_end = kSegConverged;
+    double normb = 0.0, recres = 0.0, last_rn = 0.0;
+    int status = kStOk;
+
+#define CG_BARRIER()                                                                         \
+    do {                                                                                     \
+        if (!grid_barrier(a.bar, epoch, a.poll_limit, a.force_timeout, &a.out->abort,       \
+                          &s.ok)) {                                                          \
+            status = kStTimeout;                                                             \
+            goto finish;                                                                     \
+        }                                                                                    \
+    } while (0)
+
+    for (;;) {
+        residual_sweep<T, VEC, OP>(a, s);
+        spmvs++;
+        CG_BARRIER();
+        grid_partials_sum<2>(a.npart, kNormSlots, s.red, s.out);
+        if (segments == 0) normb = sqrt(s.out[0]);
+        const double rn = sqrt(s.out[1]);
+        last_rn = rn;
+        if (normb == 0.0) {
+            for (int64_t g = (int64_t)blockIdx.x * kBlock + tid; g < n; g += (int64_t)gridDim.x * kBlock)
+                a.x[g] = 0.0;
+            status = kStOk;
+            break;
+        }
+        if (!isfinite(normb) || !isfinite(rn)) { status = kStNonfinite; break; }
+        if (rn < a.rtol * normb) { status = kStOk; break; }
+        if (iters >= a.maxit) { status = kStMaxit; break; }
+        if (segments > 0) {
+            if (kF32 && last_end == kSegConverged) {
+                if (++refinements > kMaxRefine) { status = kStMaxit; break; }
+            } else {
+                if (restarts >= a.max_restarts) {
+                    status = (last_end == kSegMaxit) ? kStMaxit : kStBreakdown;
+                    break;
+                }
+                restarts++;
+            }
+        }
+        const double tau = kF32 ? fmax(a.inner_floor * rn, 0.5 * a.rtol * normb) : a.rtol * normb;
+        const long long budget = a.maxit - iters;
+        double rr = rn * rn;
+        if constexpr (kF32) {
+            // rc = (float) r, d = 0, rr from the rounded values
+            double acc[1] = {0.0};
+            for (int64_t u = blockIdx.x; u < nunits; u += gridDim.x) {
+                const int64_t g0 = u * UNIT + (int64_t)tid * VEC;
+                if (g0 >= n) continue;
+                T z[VEC], zero[VEC];
+#pragma unroll
+                for (int v = 0; v < VEC; ++v) {
+                    z[v] = (T)a.r[g0 + v];
+                    zero[v] = T(0);
+                    acc[0] = dacc(acc[0], z[v], z[v]);
+                }
+                vst<T, VEC>(rc + g0, z);
+                vst<T, VEC>(xi + g0, zero);
+            }
+            block_sum<1>(acc, s.red, s.out);
+            if (tid == 0) a.part[blockIdx.x * kMaxDots] = s.out[0];
+            CG_BARRIER();
+            grid_partials_sum<1>(a.part, kMaxDots, s.red, s.raw);
+            rr = s.raw[0];
+        }
+        long long k = 0;
+        int end;
+        double beta = 0.0;
+        for (;;) {
+            if (!isfinite(rr)) { end = kSegNonfinite; break; }
+            if (sqrt(rr) < tau) { end = kSegConverged; break; }
+            if (k >= budget) { end = kSegMaxit; break; }
+            // ---- p_k = r_k + beta_{k-1} p_{k-1};  q = A p_k;  (p_k, q)
+            T *pn = pr[(k + 1) & 1];
+            const T *po = pr[k & 1];
+            double acc[1] = {0.0};
+            for (int64_t u = blockIdx.x; u < nunits; u += gridDim.x) {
+                const int64_t g0 = u * UNIT + (int64_t)tid * VEC;
+                if (g0 >= n) continue;
+                T c[VEC], w[VEC];
+                if (k == 0)
+                    op_apply<T, T, VEC, OP>(a, cC, cO, LdFirst<T>{rc}, g0, c, w);
+                else
+                    op_apply<T, T, VEC, OP>(a, cC, cO, LdAxpy<T>{rc, po, (T)beta}, g0, c, w);
+                vst<T, VEC>(pn + g0, c);
+                vst<T, VEC>(q + g0, w);
+#pragma unroll
+                for (int v = 0; v < VEC; ++v) acc[0] = dacc(acc[0], c[v], w[v]);
+            }
+            spmvs++;
+            block_sum<1>(acc, s.red, s.out);
+            if (tid == 0) a.part[(size_t)blockIdx.x * kMaxDots] = s.out[0];
+            CG_BARRIER();
+            grid_partials_sum<1>(a.part, kMaxDots, s.red, s.raw);
+            const double pq = s.raw[0];
+            if (!(pq > 0.0)) { end = isfinite(pq) ? kSegBreakdown : kSegNonfinite; break; }
+            const double alpha = rr / pq;
+            const T al = (T)alpha;
+            // ---- x += alpha p; r -= alpha q; (r, r)
+            double acc2[1] = {0.0};
+            for (int64_t u = blockIdx.x; u < nunits; u += gridDim.x) {
+                const int64_t g0 = u * UNIT + (int64_t)tid * VEC;
+                if (g0 >= n) continue;
+                T pv[VEC], qv[VEC], xv[VEC], rv[VEC];
+                vld<T, VEC>(pn + g0, pv);
+                vld<T, VEC>(q + g0, qv);
+                vld<T, VEC>(xi + g0, xv);
+                vld<T, VEC>(rc + g0, rv);
+#pragma unroll
+                for (int v = 0; v < VEC; ++v) {
+                    xv[v] = fma(al, pv[v], xv[v]);
+                    rv[v] = fma(-al, qv[v], rv[v]);
+                    acc2[0] = dacc(acc2[0], rv[v], rv[v]);
+                }
+                vst<T, VEC>(xi + g0, xv);
+                vst<T, VEC>(rc + g0, rv);
+            }
+            block_sum<1>(acc2, s.red, s.out);
+            if (tid == 0) a.part[(size_t)(gridDim.x + blockIdx.x) * kMaxDots] = s.out[0];
+            CG_BARRIER();
+            grid_partials_sum<1>(a.part + (size_t)gridDim.x * kMaxDots, kMaxDots, s.red, s.raw);
+            const double rr_new = s.raw[0];
+            beta = rr_new / rr;
+            rr = rr_new;
+            ++k;
+        }
+        iters += k;
+        last_end = end;
+        segments++;
+        recres = sqrt(rr);
+        if (end == kSegNonfinite) { status = kStNonfinite; goto finish; }
+        if constexpr (kF32) {   // x += d
+            for (int64_t u = blockIdx.x; u < nunits; u += gridDim.x) {
+                const int64_t g0 = u * UNIT + (int64_t)tid * VEC;
+                if (g0 >= n) continue;
+                T xv[VEC];
+                vld<T, VEC>(xi + g0, xv);
+#pragma unroll
+                for (int v = 0; v < VEC; ++v) a.x[g0 + v] += (double)xv[v];
+            }
+        }
+        CG_BARRIER();
+    }
+finish:
+    if (blockIdx.x == 0 && tid == 0) {
+        DevResult *o = a.out;
+        o->status = (ld_volatile(&o->abort) && status == kStOk) ? kStTimeout : status;
+        o->iters = iters;
+        o->spmvs = spmvs;
+        o->restarts = restarts;
+        o->refinements = refinements;
+        o->recursive_relres = (normb > 0.0) ? recres / normb : 0.0;
+        o->true_relres = (normb > 0.0) ? last_rn / normb : 0.0;
+    }
+#undef CG_BARRIER
+}
+
+}  // namespace plcg
