@@ -160,6 +160,28 @@ plcg_status plcg_solve_batched(int count, plcg_matrix *const *A,
                                const double *lmin, const double *lmax,
                                const plcg_params *prm, plcg_result *results);
 
+/* Stencil solve that allocates nothing, for callers that may not allocate
+ * device memory while they solve (a fixed memory budget or pre-reserved
+ * pool, a real-time loop that must stay out of the allocator, a plugin
+ * handed a stream but no allocator).  The paper has no counterpart: this is
+ * a deployment variant of plcg_solve for stencil operators.
+ *   desc, prm, res: as for plcg_create_stencil / plcg_solve (res may be
+ *   NULL; res->seconds is 0).  b, x: device FP64[n], 16-byte aligned, owned
+ *   by the caller (x in: x0, out: the solution).  stream: cudaStream_t.
+ * The solver's scratch is one fixed __device__ array of 32 MiB inside the
+ * library, held by every GPU that loads it until the process exits; a solve
+ * whose scratch would not fit (roughly n > 400k for FP64 l = 1) returns
+ * PLCG_ERR_INVALID and names both sizes.  The call performs no cudaMalloc,
+ * cudaFree or other allocation.  Its first call on a device looks up that
+ * array's device address (cudaGetSymbolAddress), so make the first call on
+ * each device before any stream capture.  All calls share the one array,
+ * which keeps the previous call's contents (the parts that must start at
+ * zero are cleared by each call); calls whose kernels overlap on the GPU
+ * race with each other.  Returns the solve status like plcg_solve. */
+plcg_status plcg_solve_stencil_noalloc(const plcg_stencil_desc *desc, const double *b,
+                                       double *x, const plcg_params *prm,
+                                       plcg_result *res, void *stream);
+
 /* Thread-local message describing the last failure in this thread. */
 const char *plcg_last_error(void);
 

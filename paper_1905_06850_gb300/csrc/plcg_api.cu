@@ -45,6 +45,7 @@ static plcg_status fail(plcg_status st, const char *fmt, ...)
     } while (0)
 
 extern "C" const char *plcg_last_error(void) { return g_last_error.c_str(); }
+void plcg::set_last_error(const std::string &msg) { g_last_error = msg; }
 extern "C" const char *plcg_version(void) { return "plcg 0.1 (sm_103a)"; }
 extern "C" void plcg_debug_set_poll_limit(uint64_t polls) { g_poll_limit = polls; }
 extern "C" void plcg_debug_force_barrier_timeout(int on) { g_force_timeout = on ? 1 : 0; }

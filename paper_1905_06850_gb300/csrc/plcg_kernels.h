@@ -4,6 +4,8 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include <string>
+
 namespace plcg {
 
 // Address of the persistent solver for (FP32 path?, operator, vector width,
@@ -17,6 +19,9 @@ const void *kptr_f64_csr(int l, bool cg);
 const void *kptr_f32_st4(int l, bool cg);
 const void *kptr_f32_st1(int l, bool cg);
 const void *kptr_f32_csr(int l, bool cg);
+
+// Sets the thread-local message returned by plcg_last_error().
+void set_last_error(const std::string &msg);
 
 // dst[i] = (float) src[i] on the device.
 cudaError_t launch_round_to_f32(const double *src, float *dst, int64_t n, cudaStream_t s);

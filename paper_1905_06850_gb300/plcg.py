@@ -73,6 +73,8 @@ SIGNATURES = {
     "plcg_solve_host": (C.c_int, [_VP, _VP, _VP, C.POINTER(plcg_params), C.POINTER(plcg_result)]),
     "plcg_solve_batched": (C.c_int, [C.c_int, _VP, _VP, _VP, _VP, _VP, C.POINTER(plcg_params),
                                      _VP]),
+    "plcg_solve_stencil_noalloc": (C.c_int, [C.POINTER(plcg_stencil_desc), _VP, _VP,
+                                             C.POINTER(plcg_params), C.POINTER(plcg_result), _VP]),
     "plcg_last_error": (C.c_char_p, []),
     "plcg_version": (C.c_char_p, []),
     "plcg_debug_set_poll_limit": (None, [C.c_uint64]),
