@@ -207,9 +207,11 @@ struct LdFirst {          // value = a[g] (CG first step, p_0 = r_0)
 // Operators.  apply() returns the centre values c and w = (A z) for the VEC
 // rows g0 .. g0+VEC-1 (stencil: nx % VEC == 0, so they share y and z).
 // ------------------------------------------------------------------------
+// Centre values c and neighbour sums nb of the VEC rows g0 .. g0+VEC-1, so
+// that (A z)_g = center * c + off * nb.
 template <typename V, int VEC, class Ld>
-__device__ __forceinline__ void stencil_apply(const StencilDesc &st, V cC, V cO, const Ld &ld,
-                                              int64_t g0, V (&c)[VEC], V (&w)[VEC])
+__device__ __forceinline__ void stencil_parts(const StencilDesc &st, const Ld &ld, int64_t g0,
+                                              V (&c)[VEC], V (&nb)[VEC])
 {
     const int nx = st.nx, ny = st.ny;
     const int64_t line = g0 / nx;
@@ -217,7 +219,6 @@ __device__ __forceinline__ void stencil_apply(const StencilDesc &st, V cC, V cO,
     const int y = (int)(line % ny);
     const int64_t zc = line / ny;
     ld.template vec<VEC>(g0, c);
-    V nb[VEC];
     const V left = (x0 > 0) ? ld.one(g0 - 1) : V(0);
     const V right = (x0 + VEC < nx) ? ld.one(g0 + VEC) : V(0);
 #pragma unroll
@@ -247,6 +248,14 @@ __device__ __forceinline__ void stencil_apply(const StencilDesc &st, V cC, V cO,
             for (int v = 0; v < VEC; ++v) nb[v] += t[v];
         }
     }
+}
+
+template <typename V, int VEC, class Ld>
+__device__ __forceinline__ void stencil_apply(const StencilDesc &st, V cC, V cO, const Ld &ld,
+                                              int64_t g0, V (&c)[VEC], V (&w)[VEC])
+{
+    V nb[VEC];
+    stencil_parts<V, VEC>(st, ld, g0, c, nb);
 #pragma unroll
     for (int v = 0; v < VEC; ++v) w[v] = fma(cO, nb[v], cC * c[v]);
 }
@@ -260,6 +269,20 @@ __device__ __forceinline__ V csr_row(const CsrDesc &A, const Ld &ld, int64_t row
     V s = V(0);
     for (int64_t e = e0; e < e1; ++e) s = fma((V)__ldg(val + e), ld.one(__ldg(A.col + e)), s);
     return s;
+}
+
+// (c, nb) with (A z)_g = kc * c + kn * nb: stencil (center, off), CSR (0, 1).
+template <typename V, typename C, int VEC, int OP, class Ld>
+__device__ __forceinline__ void op_parts(const SolveArgs<C> &a, const Ld &ld, int64_t g0,
+                                         V (&c)[VEC], V (&nb)[VEC])
+{
+    if constexpr (OP == kOpStencil) {
+        stencil_parts<V, VEC>(a.st, ld, g0, c, nb);
+    } else {
+        static_assert(VEC == 1, "CSR rows are one per thread");
+        c[0] = ld.one(g0);
+        nb[0] = csr_row<V, C>(a.csr, ld, g0);
+    }
 }
 
 template <typename V, typename C, int VEC, int OP, class Ld>
@@ -489,11 +512,37 @@ __device__ void scalar_step(Smem<T> &s, const SolveArgs<T> &a, long long i, doub
     }
 }
 
-// Accumulate a*b into an FP64 sum.
-template <typename T>
-__device__ __forceinline__ double dacc(double acc, T a, T b)
+// acc + sum_v a[v] b[v] with FP64 accumulation.  FP64: one FMA per term.
+// FP32 vectors: the VEC products of a group are summed exactly up to
+// O(eps^2) with error-free transformations -- Dekker's TwoProduct via FMA
+// (p + e = a*b exactly) and Knuth's TwoSum (s + e = a + b exactly), the
+// building blocks of Ogita, Rump & Oishi, "Accurate sum and dot product",
+// SIAM J. Sci. Comput. 26(6), 2005 -- and the group sum (s, t) is then
+// added to the FP64 accumulator.  This keeps per-point FP64 work (which runs
+// at a fraction of the FP32 rate on GB300) to two conversions and two adds per
+// group instead of three FP64 operations per term.
+template <typename T, int VEC>
+__device__ __forceinline__ double group_dot(const T (&a)[VEC], const T (&b)[VEC], double acc)
 {
-    return fma((double)a, (double)b, acc);
+    if constexpr (sizeof(T) == 8 || VEC == 1) {
+#pragma unroll
+        for (int v = 0; v < VEC; ++v) acc = fma((double)a[v], (double)b[v], acc);
+        return acc;
+    } else {
+        float s = __fmul_rn(a[0], b[0]);
+        float t = __fmaf_rn(a[0], b[0], -s);
+#pragma unroll
+        for (int v = 1; v < VEC; ++v) {
+            const float h = __fmul_rn(a[v], b[v]);
+            const float lo = __fmaf_rn(a[v], b[v], -h);
+            const float s2 = __fadd_rn(s, h);
+            const float bb = __fsub_rn(s2, s);
+            const float e = __fadd_rn(__fsub_rn(s, __fsub_rn(s2, bb)), __fsub_rn(h, bb));
+            s = s2;
+            t = __fadd_rn(t, __fadd_rn(e, lo));
+        }
+        return (acc + (double)s) + (double)t;
+    }
 }
 
 // ------------------------------------------------------------------------
@@ -541,7 +590,7 @@ __device__ void residual_sweep(const SolveArgs<T> &a, Smem<T> &s)
 // The p(l)-CG persistent kernel.
 // ------------------------------------------------------------------------
 template <typename T, int L, int VEC, int OP>
-__global__ void __launch_bounds__(kBlock) plcg_kernel(SolveArgs<T> a)
+__global__ void __launch_bounds__(kBlock, (L <= 2 ? 3 : 2)) plcg_kernel(SolveArgs<T> a)
 {
     __shared__ Smem<T> s;
     constexpr int UNIT = kBlock * VEC;
@@ -551,6 +600,8 @@ __global__ void __launch_bounds__(kBlock) plcg_kernel(SolveArgs<T> a)
     const int tid = threadIdx.x;
     unsigned epoch = 0;
     const T cC = (T)a.st.center, cO = (T)a.st.off;
+    // (A z)_g = kc * c + kn * nb (see op_parts)
+    const T kc = (OP == kOpStencil) ? cC : T(0), kn = (OP == kOpStencil) ? cO : T(1);
     // xi: the iterate K6 updates (FP64 path: x itself; FP32 path: the inner
     // correction d, stored in the p-ring's spare vector)
     T *xi = kF32 ? a.rc : reinterpret_cast<T *>(a.x);
@@ -694,22 +745,26 @@ __global__ void __launch_bounds__(kBlock) plcg_kernel(SolveArgs<T> a)
             for (int64_t u = blockIdx.x; u < nunits; u += gridDim.x) {
                 const int64_t g0 = u * UNIT + (int64_t)tid * VEC;
                 if (g0 >= n) continue;
-                T c[VEC], w[VEC], un[VEC];
-                op_apply<T, T, VEC, OP>(a, cC, cO, Ld1<T>{cf.zl_cur}, g0, c, w);   // K1
+                // K1: A z^(l)_i = kc * c + kn * nb, folded into the z^(l) update
+                T c[VEC], nb[VEC], un[VEC];
+                op_parts<T, T, VEC, OP>(a, Ld1<T>{cf.zl_cur}, g0, c, nb);
                 T zp[VEC];
                 T cur[L][VEC];
                 T nv0[VEC];
                 if (cf.mode == 0) {
+                    // u_{i+1} = A z^(l)_i - sigma_i z^(l)_i
 #pragma unroll
-                    for (int v = 0; v < VEC; ++v) un[v] = fma(-cf.sig, c[v], w[v]);
+                    for (int v = 0; v < VEC; ++v) un[v] = fma(kc - cf.sig, c[v], kn * nb[v]);
                     vst<T, VEC>(cf.zl_new + g0, un);
                     for (int k = 0; k < cf.ncopy; ++k) vst<T, VEC>(cf.cpy[k] + g0, un);
                 } else {
-                    // K4: z^(l)_{i+1} and z^(k)_{i-l+k+1}, k < l (Alg. 1 lines 19-21)
+                    // K4: z^(l)_{i+1} = (A z^(l)_i - gamma z^(l)_i - delta' z^(l)_{i-1}) / delta
+                    // and z^(k)_{i-l+k+1}, k < l (Alg. 1 lines 19-21)
                     vld<T, VEC>(cf.zl_prev + g0, zp);
+                    const T uc = fma(kc, cf.invd, cf.al), un_nb = kn * cf.invd;
 #pragma unroll
                     for (int v = 0; v < VEC; ++v)
-                        un[v] = fma(w[v], cf.invd, fma(cf.al, c[v], cf.bm * zp[v]));
+                        un[v] = fma(uc, c[v], fma(un_nb, nb[v], cf.bm * zp[v]));
                     vst<T, VEC>(cf.zl_new + g0, un);
 #pragma unroll
                     for (int k = 0; k < L; ++k) vld<T, VEC>(cf.cur[k] + g0, cur[k]);
@@ -741,13 +796,14 @@ __global__ void __launch_bounds__(kBlock) plcg_kernel(SolveArgs<T> a)
                     const int src = cf.dsrc[q];
                     if (src == 0) continue;
                     T o[VEC];
-                    if (src == 1) vld<T, VEC>(cf.dptr[q] + g0, o);
+                    if (src == 1) {
+                        vld<T, VEC>(cf.dptr[q] + g0, o);
+                    } else {
 #pragma unroll
-                    for (int v = 0; v < VEC; ++v) {
-                        const T val = (src == 1) ? o[v] : (src == 2) ? un[v] : (src == 3) ? nv0[v]
-                                    : (src == 4) ? c[v] : zp[v];
-                        acc[q] = dacc(acc[q], un[v], val);
+                        for (int v = 0; v < VEC; ++v)
+                            o[v] = (src == 2) ? un[v] : (src == 3) ? nv0[v] : (src == 4) ? c[v] : zp[v];
                     }
+                    acc[q] = group_dot<T, VEC>(un, o, acc[q]);
                 }
                 // K6: p and the iterate (Alg. 1 lines 26-31)
                 if (cf.k6 == 1) {
@@ -799,7 +855,7 @@ finish:
 // ring's third vector.
 // ------------------------------------------------------------------------
 template <typename T, int VEC, int OP>
-__global__ void __launch_bounds__(kBlock) cg_kernel(SolveArgs<T> a)
+__global__ void __launch_bounds__(kBlock, 3) cg_kernel(SolveArgs<T> a)
 {
     __shared__ Smem<T> s;
     constexpr int UNIT = kBlock * VEC;
@@ -870,8 +926,8 @@ __global__ void __launch_bounds__(kBlock) cg_kernel(SolveArgs<T> a)
                 for (int v = 0; v < VEC; ++v) {
                     z[v] = (T)a.r[g0 + v];
                     zero[v] = T(0);
-                    acc[0] = dacc(acc[0], z[v], z[v]);
                 }
+                acc[0] = group_dot<T, VEC>(z, z, acc[0]);
                 vst<T, VEC>(rc + g0, z);
                 vst<T, VEC>(xi + g0, zero);
             }
@@ -902,8 +958,7 @@ __global__ void __launch_bounds__(kBlock) cg_kernel(SolveArgs<T> a)
                     op_apply<T, T, VEC, OP>(a, cC, cO, LdAxpy<T>{rc, po, (T)beta}, g0, c, w);
                 vst<T, VEC>(pn + g0, c);
                 vst<T, VEC>(q + g0, w);
-#pragma unroll
-                for (int v = 0; v < VEC; ++v) acc[0] = dacc(acc[0], c[v], w[v]);
+                acc[0] = group_dot<T, VEC>(c, w, acc[0]);
             }
             spmvs++;
             block_sum<1>(acc, s.red, s.out);
@@ -928,8 +983,8 @@ __global__ void __launch_bounds__(kBlock) cg_kernel(SolveArgs<T> a)
                 for (int v = 0; v < VEC; ++v) {
                     xv[v] = fma(al, pv[v], xv[v]);
                     rv[v] = fma(-al, qv[v], rv[v]);
-                    acc2[0] = dacc(acc2[0], rv[v], rv[v]);
                 }
+                acc2[0] = group_dot<T, VEC>(rv, rv, acc2[0]);
                 vst<T, VEC>(xi + g0, xv);
                 vst<T, VEC>(rc + g0, rv);
             }
