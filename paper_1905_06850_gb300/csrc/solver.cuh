@@ -545,6 +545,47 @@ __device__ __forceinline__ double group_dot(const T (&a)[VEC], const T (&b)[VEC]
     }
 }
 
+// Per-thread accumulator of one dot product over the units a thread sweeps.
+// FP64 vectors: one FMA per term into the FP64 sum.  FP32 vectors: the
+// compensated dot product Dot2 of Ogita, Rump & Oishi (2005) -- TwoProduct
+// per term, TwoSum into a running FP32 pair (s, t) -- flushed into the FP64
+// sum every kFlushUnits units, so the running pair never covers more than
+// kFlushUnits * VEC terms (error O(eps_32^2) relative to the sum of |terms|
+// per flush) and the FP64 pipe sees two conversions and two adds per flush.
+constexpr int kFlushUnits = 4;
+
+template <typename T, int VEC>
+struct DotAcc {
+    double acc = 0.0;
+    float s = 0.f, t = 0.f;
+    __device__ __forceinline__ void add(const T (&x)[VEC], const T (&y)[VEC])
+    {
+        if constexpr (sizeof(T) == 8) {
+#pragma unroll
+            for (int v = 0; v < VEC; ++v) acc = fma(x[v], y[v], acc);
+        } else {
+#pragma unroll
+            for (int v = 0; v < VEC; ++v) {
+                const float h = __fmul_rn(x[v], y[v]);
+                const float lo = __fmaf_rn(x[v], y[v], -h);
+                const float s2 = __fadd_rn(s, h);
+                const float bb = __fsub_rn(s2, s);
+                const float e = __fadd_rn(__fsub_rn(s, __fsub_rn(s2, bb)), __fsub_rn(h, bb));
+                s = s2;
+                t = __fadd_rn(t, __fadd_rn(e, lo));
+            }
+        }
+    }
+    __device__ __forceinline__ void flush()
+    {
+        if constexpr (sizeof(T) == 4) {
+            acc = (acc + (double)s) + (double)t;
+            s = 0.f;
+            t = 0.f;
+        }
+    }
+};
+
 // ------------------------------------------------------------------------
 // Residual sweep: r = b - A x (FP64; the stored operator values widened),
 // partial ||r||^2 and ||b||^2.  Units of kBlock * V64 rows.
@@ -590,7 +631,7 @@ __device__ void residual_sweep(const SolveArgs<T> &a, Smem<T> &s)
 // The p(l)-CG persistent kernel.
 // ------------------------------------------------------------------------
 template <typename T, int L, int VEC, int OP>
-__global__ void __launch_bounds__(kBlock, (L <= 2 ? 3 : 2)) plcg_kernel(SolveArgs<T> a)
+__global__ void __launch_bounds__(kBlock, (sizeof(T) == 4 && L <= 2) ? 3 : 2) plcg_kernel(SolveArgs<T> a)
 {
     __shared__ Smem<T> s;
     constexpr int UNIT = kBlock * VEC;
@@ -738,59 +779,82 @@ __global__ void __launch_bounds__(kBlock, (L <= 2 ? 3 : 2)) plcg_kernel(SolveArg
                 break;
             }
 
-            // ---- one full iteration sweep: K1, K4, K5 (partials), K6
-            double acc[2 * L + 1];
-#pragma unroll
-            for (int q = 0; q <= 2 * L; ++q) acc[q] = 0.0;
+            // ---- one full iteration sweep: K1, K4, K5 (partials), K6.  Each unit
+            // issues every load before any store (the vectors are distinct, but
+            // the compiler cannot know), so its HBM reads overlap in flight.
+            DotAcc<T, VEC> dac[2 * L + 1];
+            int since_flush = 0;
             for (int64_t u = blockIdx.x; u < nunits; u += gridDim.x) {
                 const int64_t g0 = u * UNIT + (int64_t)tid * VEC;
                 if (g0 >= n) continue;
-                // K1: A z^(l)_i = kc * c + kn * nb, folded into the z^(l) update
-                T c[VEC], nb[VEC], un[VEC];
-                op_parts<T, T, VEC, OP>(a, Ld1<T>{cf.zl_cur}, g0, c, nb);
-                T zp[VEC];
-                T cur[L][VEC];
-                T nv0[VEC];
-                if (cf.mode == 0) {
-                    // u_{i+1} = A z^(l)_i - sigma_i z^(l)_i
+                const bool rec = cf.mode == 1;
+                // -- loads
+                T c[VEC], nb[VEC];
+                op_parts<T, T, VEC, OP>(a, Ld1<T>{cf.zl_cur}, g0, c, nb);   // K1 operands
+                T zp[VEC], cur[L][VEC], pk[L][VEC], pv[VEC], xv[VEC];
 #pragma unroll
-                    for (int v = 0; v < VEC; ++v) un[v] = fma(kc - cf.sig, c[v], kn * nb[v]);
-                    vst<T, VEC>(cf.zl_new + g0, un);
-                    for (int k = 0; k < cf.ncopy; ++k) vst<T, VEC>(cf.cpy[k] + g0, un);
-                } else {
-                    // K4: z^(l)_{i+1} = (A z^(l)_i - gamma z^(l)_i - delta' z^(l)_{i-1}) / delta
-                    // and z^(k)_{i-l+k+1}, k < l (Alg. 1 lines 19-21)
+                for (int v = 0; v < VEC; ++v) zp[v] = T(0);
+                if (rec) {
                     vld<T, VEC>(cf.zl_prev + g0, zp);
-                    const T uc = fma(kc, cf.invd, cf.al), un_nb = kn * cf.invd;
-#pragma unroll
-                    for (int v = 0; v < VEC; ++v)
-                        un[v] = fma(uc, c[v], fma(un_nb, nb[v], cf.bm * zp[v]));
-                    vst<T, VEC>(cf.zl_new + g0, un);
 #pragma unroll
                     for (int k = 0; k < L; ++k) vld<T, VEC>(cf.cur[k] + g0, cur[k]);
 #pragma unroll
                     for (int k = 0; k < L; ++k) {
-                        T pk[VEC];
                         if (k > 0 || cf.prev0) {
-                            vld<T, VEC>(cf.prv[k] + g0, pk);
+                            vld<T, VEC>(cf.prv[k] + g0, pk[k]);
                         } else {
 #pragma unroll
-                            for (int v = 0; v < VEC; ++v) pk[v] = T(0);
-                        }
-                        T nk[VEC];
-#pragma unroll
-                        for (int v = 0; v < VEC; ++v) {
-                            const T up = (k == L - 1) ? c[v] : cur[k + 1][v];
-                            nk[v] = fma(up, cf.invd, fma(cf.ak[k], cur[k][v], cf.bm * pk[v]));
-                        }
-                        vst<T, VEC>(cf.nw[k] + g0, nk);
-                        if (k == 0) {
-#pragma unroll
-                            for (int v = 0; v < VEC; ++v) nv0[v] = nk[v];
+                            for (int v = 0; v < VEC; ++v) pk[k][v] = T(0);
                         }
                     }
                 }
-                // K5: partial dot products with u_{i+1} = z^(l)_{i+1}
+                if (cf.k6 == 2) {
+                    vld<T, VEC>(a.p + g0, pv);
+                    vld<T, VEC>(xi + g0, xv);
+                }
+                // -- compute
+                T un[VEC], nw[L][VEC];
+                if (!rec) {
+                    // u_{i+1} = A z^(l)_i - sigma_i z^(l)_i
+#pragma unroll
+                    for (int v = 0; v < VEC; ++v) un[v] = fma(kc - cf.sig, c[v], kn * nb[v]);
+                } else {
+                    // K4: z^(l)_{i+1} = (A z^(l)_i - gamma z^(l)_i - delta' z^(l)_{i-1}) / delta
+                    // and z^(k)_{i-l+k+1}, k < l (Alg. 1 lines 19-21)
+                    const T uc = fma(kc, cf.invd, cf.al), un_nb = kn * cf.invd;
+#pragma unroll
+                    for (int v = 0; v < VEC; ++v)
+                        un[v] = fma(uc, c[v], fma(un_nb, nb[v], cf.bm * zp[v]));
+#pragma unroll
+                    for (int k = 0; k < L; ++k)
+#pragma unroll
+                        for (int v = 0; v < VEC; ++v) {
+                            const T up = (k == L - 1) ? c[v] : cur[k + 1][v];
+                            nw[k][v] = fma(up, cf.invd, fma(cf.ak[k], cur[k][v], cf.bm * pk[k][v]));
+                        }
+                }
+                // K6: p and the iterate (Alg. 1 lines 26-31)
+                if (cf.k6 == 1) {
+#pragma unroll
+                    for (int v = 0; v < VEC; ++v) pv[v] = cf.pv * cur[0][v];
+                } else if (cf.k6 == 2) {
+#pragma unroll
+                    for (int v = 0; v < VEC; ++v) {
+                        xv[v] = fma(cf.zx, pv[v], xv[v]);
+                        pv[v] = fma(cf.pv, cur[0][v], cf.pp * pv[v]);
+                    }
+                }
+                // -- stores
+                vst<T, VEC>(cf.zl_new + g0, un);
+                if (!rec) {
+                    for (int k = 0; k < cf.ncopy; ++k) vst<T, VEC>(cf.cpy[k] + g0, un);
+                } else {
+#pragma unroll
+                    for (int k = 0; k < L; ++k) vst<T, VEC>(cf.nw[k] + g0, nw[k]);
+                }
+                if (cf.k6 >= 1) vst<T, VEC>(a.p + g0, pv);
+                if (cf.k6 == 2) vst<T, VEC>(xi + g0, xv);
+                // -- K5: partial dot products with u_{i+1} = z^(l)_{i+1}
 #pragma unroll
                 for (int q = 0; q <= 2 * L; ++q) {
                     const int src = cf.dsrc[q];
@@ -801,28 +865,21 @@ __global__ void __launch_bounds__(kBlock, (L <= 2 ? 3 : 2)) plcg_kernel(SolveArg
                     } else {
 #pragma unroll
                         for (int v = 0; v < VEC; ++v)
-                            o[v] = (src == 2) ? un[v] : (src == 3) ? nv0[v] : (src == 4) ? c[v] : zp[v];
+                            o[v] = (src == 2) ? un[v] : (src == 3) ? nw[0][v] : (src == 4) ? c[v] : zp[v];
                     }
-                    acc[q] = group_dot<T, VEC>(un, o, acc[q]);
+                    dac[q].add(un, o);
                 }
-                // K6: p and the iterate (Alg. 1 lines 26-31)
-                if (cf.k6 == 1) {
-                    T pn[VEC];
+                if (++since_flush == kFlushUnits) {
 #pragma unroll
-                    for (int v = 0; v < VEC; ++v) pn[v] = cf.pv * cur[0][v];
-                    vst<T, VEC>(a.p + g0, pn);
-                } else if (cf.k6 == 2) {
-                    T pv[VEC], xv[VEC];
-                    vld<T, VEC>(a.p + g0, pv);
-                    vld<T, VEC>(xi + g0, xv);
-#pragma unroll
-                    for (int v = 0; v < VEC; ++v) {
-                        xv[v] = fma(cf.zx, pv[v], xv[v]);
-                        pv[v] = fma(cf.pv, cur[0][v], cf.pp * pv[v]);
-                    }
-                    vst<T, VEC>(xi + g0, xv);
-                    vst<T, VEC>(a.p + g0, pv);
+                    for (int q = 0; q <= 2 * L; ++q) dac[q].flush();
+                    since_flush = 0;
                 }
+            }
+            double acc[2 * L + 1];
+#pragma unroll
+            for (int q = 0; q <= 2 * L; ++q) {
+                dac[q].flush();
+                acc[q] = dac[q].acc;
             }
             spmvs++;
             // MPI_Iallreduce(..., req(i)): publish this CTA's partials in slot i mod (l+1)
