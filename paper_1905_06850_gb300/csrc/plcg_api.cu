@@ -13,6 +13,7 @@
 #include <cstring>
 #include <mutex>
 #include <string>
+#include <vector>
 
 #include "../../include/plcg.h"
 #include "plcg_internal.h"
@@ -441,10 +442,180 @@ extern "C" plcg_status plcg_solve_host(plcg_matrix *A, const double *b, double *
     return st;
 }
 
+// ------------------------------------------------------------------ batched
+namespace {
+
+// Device buffers of batched solves, per device, grown on demand and kept
+// until the process exits.
+struct BatchCtx {
+    std::mutex mu;
+    char *mem = nullptr;
+    size_t bytes = 0;
+    cudaEvent_t ev0 = nullptr, ev1 = nullptr;
+};
+BatchCtx g_batch[64];
+
+}  // namespace
+
+template <typename T>
+static plcg_status run_batched(int count, plcg_matrix *const *A, const double *const *b,
+                               double *const *x, const double *lmin, const double *lmax,
+                               const plcg_params *prm, plcg_result *results)
+{
+    const bool f32 = sizeof(T) == 4;
+    const bool cg = prm->method == PLCG_METHOD_CG;
+    const int l = cg ? 1 : prm->l;
+    const void *func = batched_kernel_ptr(f32, l);
+    if (!func) return fail(PLCG_ERR_UNIMPL, "plcg_solve_batched: l must be 1..4");
+    cudaStream_t stream = A[0]->stream;
+    int dev = A[0]->device;
+    if (dev < 0 || dev >= 64) return fail(PLCG_ERR_INVALID, "device ordinal too large");
+    BatchCtx &ctx = g_batch[dev];
+    std::lock_guard<std::mutex> lock(ctx.mu);
+
+    // host descriptors; work list by decreasing size (longest first)
+    std::vector<BatchSys> sys(count);
+    std::vector<int> order(count);
+    int64_t nmax = 0;
+    for (int i = 0; i < count; ++i) {
+        const plcg_matrix *M = A[i];
+        BatchSys &y = sys[i];
+        y.dim = M->st.dim;
+        y.nx = M->st.nx;
+        y.ny = M->st.ny;
+        y.nz = M->st.nz;
+        y.center = M->st.center;
+        y.off = M->st.off;
+        y.b = b[i];
+        y.x = x[i];
+        y.out = nullptr;
+        std::memset(y.sigma, 0, sizeof(y.sigma));
+        if (!cg) {
+            if (prm->shifts) {
+                for (int k = 0; k < l; ++k) y.sigma[k] = prm->shifts[k];
+            } else {
+                const double lo = lmin ? lmin[i] : prm->lmin, hi = lmax ? lmax[i] : prm->lmax;
+                if (!std::isfinite(lo) || !std::isfinite(hi) || hi < lo)
+                    return fail(PLCG_ERR_INVALID, "system %d: need lmin <= lmax", i);
+                chebyshev_shifts(l, lo, hi, y.sigma);
+            }
+        }
+        order[i] = i;
+        nmax = std::max<int64_t>(nmax, M->n);
+    }
+    std::stable_sort(order.begin(), order.end(),
+                     [&](int p, int q) { return A[p]->n > A[q]->n; });
+
+    // ring layout (as for a single solve)
+    SolveArgs<T> proto;
+    std::memset(&proto, 0, sizeof(proto));
+    int nvec = 0;
+    if (!cg) {
+        for (int k = 0; k <= l; ++k) {
+            int d = 3;
+            if (k == l) d = std::max(3, l);
+            if (k == 0 && prm->dots_2l1) d = std::max(3, l + 1);
+            proto.depth[k] = d;
+            proto.base[k] = nvec;
+            nvec += d;
+        }
+    } else {
+        nvec = 3;
+    }
+    proto.method = cg ? 1 : 0;
+    proto.l = l;
+    proto.rtol = prm->rtol;
+    proto.maxit = prm->maxit;
+    proto.dots_2l1 = prm->dots_2l1 ? 1 : 0;
+    proto.max_restarts = prm->max_restarts;
+    proto.inner_floor = prm->inner_rtol_floor;
+    proto.fp32 = f32 ? 1 : 0;
+    proto.poll_limit = poll_limit();
+
+    int per_sm = 0;
+    CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, func, kBlock, 0));
+    if (per_sm < 1) return fail(PLCG_ERR_CUDA, "batched kernel cannot be resident");
+    const int P = (int)std::max<int64_t>(1, std::min<int64_t>(count, (int64_t)per_sm * A[0]->num_sms));
+    const size_t ws_stride =
+        align_up(align_up((size_t)(nvec + 2) * nmax * sizeof(T), 256) + (size_t)nmax * sizeof(double), 256);
+    size_t off = 0;
+    const size_t o_sys = off; off += align_up(sizeof(BatchSys) * count, 256);
+    const size_t o_order = off; off += align_up(sizeof(int) * count, 256);
+    const size_t o_res = off; off += align_up(sizeof(DevResult) * count, 256);
+    const size_t o_ctr = off; off += 256;
+    const size_t o_ws = off; off += ws_stride * P;
+    if (ctx.bytes < off) {
+        if (ctx.mem) { cudaStreamSynchronize(stream); cudaFree(ctx.mem); ctx.mem = nullptr; ctx.bytes = 0; }
+        CUDA_TRY(cudaMalloc(&ctx.mem, off));
+        ctx.bytes = off;
+    }
+    if (!ctx.ev0) {
+        CUDA_TRY(cudaEventCreate(&ctx.ev0));
+        CUDA_TRY(cudaEventCreate(&ctx.ev1));
+    }
+    DevResult *dres = reinterpret_cast<DevResult *>(ctx.mem + o_res);
+    for (int i = 0; i < count; ++i) sys[i].out = dres + i;
+    CUDA_TRY(cudaMemcpyAsync(ctx.mem + o_sys, sys.data(), sizeof(BatchSys) * count,
+                             cudaMemcpyHostToDevice, stream));
+    CUDA_TRY(cudaMemcpyAsync(ctx.mem + o_order, order.data(), sizeof(int) * count,
+                             cudaMemcpyHostToDevice, stream));
+    CUDA_TRY(cudaMemsetAsync(ctx.mem + o_res, 0, sizeof(DevResult) * count, stream));
+    CUDA_TRY(cudaMemsetAsync(ctx.mem + o_ctr, 0, 256, stream));
+    BatchArgs<T> ba;
+    ba.count = count;
+    ba.sys = reinterpret_cast<const BatchSys *>(ctx.mem + o_sys);
+    ba.order = reinterpret_cast<const int *>(ctx.mem + o_order);
+    ba.counter = reinterpret_cast<int *>(ctx.mem + o_ctr);
+    ba.ws = ctx.mem + o_ws;
+    ba.ws_stride = ws_stride;
+    ba.proto = proto;
+    void *args[] = {&ba};
+    CUDA_TRY(cudaEventRecord(ctx.ev0, stream));
+    CUDA_TRY(cudaLaunchKernel(func, dim3(P), dim3(kBlock), args, 0, stream));
+    CUDA_TRY(cudaEventRecord(ctx.ev1, stream));
+    std::vector<DevResult> hres(count);
+    CUDA_TRY(cudaMemcpyAsync(hres.data(), dres, sizeof(DevResult) * count, cudaMemcpyDeviceToHost, stream));
+    CUDA_TRY(cudaStreamSynchronize(stream));
+    float ms = 0.f;
+    CUDA_TRY(cudaEventElapsedTime(&ms, ctx.ev0, ctx.ev1));
+    plcg_status first = PLCG_OK;
+    for (int i = 0; i < count; ++i) {
+        const DevResult &o = hres[i];
+        if (results) {
+            results[i].status = o.status;
+            results[i].iters = o.iters;
+            results[i].spmvs = o.spmvs;
+            results[i].restarts = o.restarts;
+            results[i].refinements = o.refinements;
+            results[i].recursive_relres = o.recursive_relres;
+            results[i].true_relres = o.true_relres;
+            results[i].seconds = ms * 1e-3;
+        }
+        if (first == PLCG_OK && o.status != PLCG_OK) first = (plcg_status)o.status;
+    }
+    if (first != PLCG_OK) return fail(first, "at least one system of the batch did not converge");
+    return PLCG_OK;
+}
+
 extern "C" plcg_status plcg_solve_batched(int count, plcg_matrix *const *A, const double *const *b,
                                           double *const *x, const double *lmin, const double *lmax,
                                           const plcg_params *prm, plcg_result *results)
 {
-    (void)count; (void)A; (void)b; (void)x; (void)lmin; (void)lmax; (void)prm; (void)results;
-    return fail(PLCG_ERR_UNIMPL, "plcg_solve_batched: not built yet");
+    if (count < 0) return fail(PLCG_ERR_INVALID, "plcg_solve_batched: count < 0");
+    if (count == 0) return PLCG_OK;
+    if (!A || !b || !x || !prm) return fail(PLCG_ERR_INVALID, "plcg_solve_batched: NULL argument");
+    for (int i = 0; i < count; ++i) {
+        if (!A[i] || !b[i] || !x[i]) return fail(PLCG_ERR_INVALID, "system %d: NULL argument", i);
+        if (A[i]->kind != kOpStencil)
+            return fail(PLCG_ERR_UNIMPL, "plcg_solve_batched: system %d is not a stencil operator", i);
+        if (A[i]->device != A[0]->device)
+            return fail(PLCG_ERR_INVALID, "plcg_solve_batched: systems on different devices");
+    }
+    plcg_status st = check_params(A[0], prm);
+    if (st != PLCG_OK) return st;
+    if (prm->method == PLCG_METHOD_PLCG && prm->l > 4)
+        return fail(PLCG_ERR_UNIMPL, "plcg_solve_batched: l must be 1..4");
+    CUDA_TRY(cudaSetDevice(A[0]->device));
+    if (prm->prec == PLCG_FP64) return run_batched<double>(count, A, b, x, lmin, lmax, prm, results);
+    return run_batched<float>(count, A, b, x, lmin, lmax, prm, results);
 }

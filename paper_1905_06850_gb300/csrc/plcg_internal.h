@@ -76,4 +76,29 @@ struct SolveArgs {
     int force_timeout;
 };
 
+// One system of a batched solve (stencil operators only).
+struct BatchSys {
+    int dim;
+    int nx, ny, nz;
+    double center;            // includes the diagonal shift
+    double off;
+    const double *b;
+    double *x;
+    DevResult *out;
+    double sigma[kMaxL];
+};
+
+// Arguments of the batched kernel.  proto carries the solve parameters and
+// the ring layout; the per-system fields are filled in on the device.
+template <typename T>
+struct BatchArgs {
+    int count;
+    const BatchSys *sys;
+    const int *order;         // systems by decreasing size
+    int *counter;             // next position in order
+    char *ws;                 // per-CTA workspaces
+    size_t ws_stride;
+    SolveArgs<T> proto;
+};
+
 }  // namespace plcg

@@ -332,8 +332,11 @@ struct Smem {
     double out[kMaxDots + 2];
     double raw[kMaxDots];
     double G[kMaxL + 1][kMaxDots];   // finalised columns c-l .. c (column c at c mod (l+1))
+    double Ginv[kMaxL + 1];          // 1 / g_{c,c} of those columns
     double gam[kMaxL + 1], del[kMaxL + 1];
-    double eta[2], zeta[2];
+    double eta[2], zeta[2], ieta[2]; // eta_m, zeta_m, 1 / eta_m
+    double bring[kMaxL + 1][kMaxDots];   // one-CTA group: reduced dots of the last l+1 iterations
+    double bnorm[2];
     Coef<T> cf;
     int ok;
 };
@@ -349,10 +352,86 @@ __device__ __forceinline__ T *ring(const SolveArgs<T> &a, int k, long long j)
 }
 
 // ------------------------------------------------------------------------
+// Execution groups.  A solve runs either on the whole grid (one system per
+// launch; CTAs meet at a bounded grid barrier and exchange FP64 partials
+// through global memory) or on one CTA (batched solves: one system per CTA;
+// __syncthreads is the barrier and the reduced dots stay in shared memory).
+// ------------------------------------------------------------------------
+template <typename T>
+struct GridGroup {
+    unsigned epoch = 0;
+    __device__ __forceinline__ int64_t unit0() const { return blockIdx.x; }
+    __device__ __forceinline__ int64_t ustep() const { return gridDim.x; }
+    __device__ __forceinline__ bool leader() const { return blockIdx.x == 0; }
+    __device__ __forceinline__ bool sync(const SolveArgs<T> &a, Smem<T> &s)
+    {
+        return grid_barrier(a.bar, epoch, a.poll_limit, a.force_timeout, &a.out->abort, &s.ok);
+    }
+    // this CTA's reduced dots (s.out[0..nd)) into ring slot `slot`
+    __device__ __forceinline__ void put_dots(const SolveArgs<T> &a, Smem<T> &s, int slot, int nd)
+    {
+        if ((int)threadIdx.x < nd)
+            a.part[((size_t)slot * gridDim.x + blockIdx.x) * kMaxDots + threadIdx.x] = s.out[threadIdx.x];
+    }
+    // sum over CTAs of ring slot `slot` into dst[0..ND)
+    template <int ND>
+    __device__ __forceinline__ void get_dots(const SolveArgs<T> &a, Smem<T> &s, int slot, double *dst)
+    {
+        grid_partials_sum<ND>(a.part + (size_t)slot * gridDim.x * kMaxDots, kMaxDots, s.red, dst);
+    }
+    __device__ __forceinline__ void put_norms(const SolveArgs<T> &a, Smem<T> &s)
+    {
+        if (threadIdx.x == 0) {
+            a.npart[(size_t)blockIdx.x * kNormSlots + 0] = s.out[0];
+            a.npart[(size_t)blockIdx.x * kNormSlots + 1] = s.out[1];
+        }
+    }
+    __device__ __forceinline__ void get_norms(const SolveArgs<T> &a, Smem<T> &s)
+    {
+        grid_partials_sum<2>(a.npart, kNormSlots, s.red, s.out);
+    }
+};
+
+template <typename T>
+struct BlockGroup {
+    __device__ __forceinline__ int64_t unit0() const { return 0; }
+    __device__ __forceinline__ int64_t ustep() const { return 1; }
+    __device__ __forceinline__ bool leader() const { return true; }
+    __device__ __forceinline__ bool sync(const SolveArgs<T> &, Smem<T> &)
+    {
+        __syncthreads();
+        return true;
+    }
+    __device__ __forceinline__ void put_dots(const SolveArgs<T> &, Smem<T> &s, int slot, int nd)
+    {
+        if ((int)threadIdx.x < nd) s.bring[slot][threadIdx.x] = s.out[threadIdx.x];
+    }
+    template <int ND>
+    __device__ __forceinline__ void get_dots(const SolveArgs<T> &, Smem<T> &s, int slot, double *dst)
+    {
+        if ((int)threadIdx.x < ND) dst[threadIdx.x] = s.bring[slot][threadIdx.x];
+        __syncthreads();
+    }
+    __device__ __forceinline__ void put_norms(const SolveArgs<T> &, Smem<T> &s)
+    {
+        if (threadIdx.x < 2) s.bnorm[threadIdx.x] = s.out[threadIdx.x];
+    }
+    __device__ __forceinline__ void get_norms(const SolveArgs<T> &, Smem<T> &s)
+    {
+        if (threadIdx.x < 2) s.out[threadIdx.x] = s.bnorm[threadIdx.x];
+        __syncthreads();
+    }
+};
+
+// ------------------------------------------------------------------------
 // Scalar step of iteration i (thread 0 of every CTA; all CTAs compute the
 // same bits).  K2: finalise column c = i-l+1 of G (Alg. 1 lines 9-10);
 // line 11: breakdown check; K3: gamma_{i-l}, delta_{i-l} (lines 12-18);
 // K6 scalars: lambda, eta, zeta and the stop test (lines 24-33).
+// A dependent FP64 operation costs ~64 cycles on GB300 and a division or a
+// square root ~500, so the step keeps 1/g_{j,j} and 1/eta_m and needs one
+// square root and three reciprocals per iteration (1/g_{c,c} is off the
+// critical path).
 // ------------------------------------------------------------------------
 template <typename T, int L>
 __device__ void scalar_step(Smem<T> &s, const SolveArgs<T> &a, long long i, double rn,
@@ -374,6 +453,7 @@ __device__ void scalar_step(Smem<T> &s, const SolveArgs<T> &a, long long i, doub
             if (j < 0 || j < cc - 2 * L || j > cc) return 0.0;
             return s.G[cc % (L + 1)][j - cc + 2 * L];
         };
+        auto ginv = [&](long long j) -> double { return s.Ginv[j % (L + 1)]; };
         auto del = [&](long long j) -> double { return j < 0 ? 0.0 : s.del[j % (L + 1)]; };
         auto gam = [&](long long j) -> double { return s.gam[j % (L + 1)]; };
         // raw column c (dots of iteration i-l): position q is row c-2l+q
@@ -385,18 +465,18 @@ __device__ void scalar_step(Smem<T> &s, const SolveArgs<T> &a, long long i, doub
         for (long long j = (c - L + 1 > 0 ? c - L + 1 : 0); j <= c - 1; ++j) {
             double t = col[j - c + 2 * L];
             for (long long k = lo; k <= j - 1; ++k) t -= g(k, j) * col[k - c + 2 * L];
-            col[j - c + 2 * L] = t / g(j, j);
+            col[j - c + 2 * L] = t * ginv(j);
         }
         const double graw = col[2 * L];
         double arg = graw;
         for (long long k = lo; k <= c - 1; ++k) arg -= col[k - c + 2 * L] * col[k - c + 2 * L];
-        const double gmm = g(m, m);
+        const double gmm = g(m, m), igmm = ginv(m);
         const double gmc = col[m - c + 2 * L];
         double gm;
         if (m < L)
-            gm = (gmc + a.sigma[m] * gmm - (m >= 1 ? g(m - 1, m) * del(m - 1) : 0.0)) / gmm;
+            gm = (gmc + a.sigma[m] * gmm - (m >= 1 ? g(m - 1, m) * del(m - 1) : 0.0)) * igmm;
         else
-            gm = (gmm * gam(m - L) + gmc * del(m - L) - g(m - 1, m) * del(m - 1)) / gmm;
+            gm = (gmm * gam(m - L) + gmc * del(m - L) - g(m - 1, m) * del(m - 1)) * igmm;
         s.gam[m % (L + 1)] = gm;
         const double thr = 64.0 * Eps<T>::v * fabs(graw);
         if (!isfinite(arg) || !isfinite(gm)) {
@@ -413,13 +493,14 @@ __device__ void scalar_step(Smem<T> &s, const SolveArgs<T> &a, long long i, doub
                     cf.pv = (T)(1.0 / gm);
                     cf.f2 = (T)rn;
                 } else {
-                    const double lam = del(m - 1) / s.eta[(m - 1) & 1];
+                    const double lam = del(m - 1) * s.ieta[(m - 1) & 1];
                     const double em = gm - lam * del(m - 1);
+                    const double iem = 1.0 / em;
                     const double zm = -lam * s.zeta[(m - 1) & 1];
                     cf.fmode = 1;
                     cf.f1 = (T)s.zeta[(m - 1) & 1];
-                    cf.pv = (T)(1.0 / em);
-                    cf.pp = (T)(-del(m - 1) / em);
+                    cf.pv = (T)iem;
+                    cf.pp = (T)(-del(m - 1) * iem);
                     cf.f2 = (T)zm;
                 }
                 cf.end = kSegLucky;
@@ -433,10 +514,12 @@ __device__ void scalar_step(Smem<T> &s, const SolveArgs<T> &a, long long i, doub
             cf.v0 = ring(a, 0, m);
             return;
         }
-        col[2 * L] = sqrt(arg);
-        const double dm = (m < L) ? col[2 * L] / gmm : col[2 * L] * del(m - L) / gmm;
+        const double gcc = sqrt(arg);
+        col[2 * L] = gcc;
+        const double dm = (m < L) ? gcc * igmm : gcc * del(m - L) * igmm;
         s.del[m % (L + 1)] = dm;
         const double invd = 1.0 / dm;
+        s.Ginv[c % (L + 1)] = 1.0 / gcc;   // needed from the next iteration on
         cf.mode = 1;
         cf.invd = (T)invd;
         cf.al = (T)(-gm * invd);
@@ -447,17 +530,20 @@ __device__ void scalar_step(Smem<T> &s, const SolveArgs<T> &a, long long i, doub
         if (i == L) {
             s.eta[0] = gm;
             s.zeta[0] = rn;
+            s.ieta[0] = 1.0 / gm;
             cf.k6 = 1;
-            cf.pv = (T)(1.0 / gm);
+            cf.pv = (T)s.ieta[0];
         } else {
-            const double lam = del(m - 1) / s.eta[(m - 1) & 1];
+            const double lam = del(m - 1) * s.ieta[(m - 1) & 1];
             const double em = gm - lam * del(m - 1);
+            const double iem = 1.0 / em;
             const double zm = -lam * s.zeta[(m - 1) & 1];
             cf.k6 = 2;
             cf.zx = (T)s.zeta[(m - 1) & 1];
-            cf.pv = (T)(1.0 / em);
-            cf.pp = (T)(-del(m - 1) / em);
+            cf.pv = (T)iem;
+            cf.pp = (T)(-del(m - 1) * iem);
             s.eta[m & 1] = em;
+            s.ieta[m & 1] = iem;
             s.zeta[m & 1] = zm;
             if (!isfinite(zm)) {
                 cf.end = kSegNonfinite;
@@ -512,46 +598,15 @@ __device__ void scalar_step(Smem<T> &s, const SolveArgs<T> &a, long long i, doub
     }
 }
 
-// acc + sum_v a[v] b[v] with FP64 accumulation.  FP64: one FMA per term.
-// FP32 vectors: the VEC products of a group are summed exactly up to
-// O(eps^2) with error-free transformations -- Dekker's TwoProduct via FMA
-// (p + e = a*b exactly) and Knuth's TwoSum (s + e = a + b exactly), the
-// building blocks of Ogita, Rump & Oishi, "Accurate sum and dot product",
-// SIAM J. Sci. Comput. 26(6), 2005 -- and the group sum (s, t) is then
-// added to the FP64 accumulator.  This keeps per-point FP64 work (which runs
-// at a fraction of the FP32 rate on GB300) to two conversions and two adds per
-// group instead of three FP64 operations per term.
-template <typename T, int VEC>
-__device__ __forceinline__ double group_dot(const T (&a)[VEC], const T (&b)[VEC], double acc)
-{
-    if constexpr (sizeof(T) == 8 || VEC == 1) {
-#pragma unroll
-        for (int v = 0; v < VEC; ++v) acc = fma((double)a[v], (double)b[v], acc);
-        return acc;
-    } else {
-        float s = __fmul_rn(a[0], b[0]);
-        float t = __fmaf_rn(a[0], b[0], -s);
-#pragma unroll
-        for (int v = 1; v < VEC; ++v) {
-            const float h = __fmul_rn(a[v], b[v]);
-            const float lo = __fmaf_rn(a[v], b[v], -h);
-            const float s2 = __fadd_rn(s, h);
-            const float bb = __fsub_rn(s2, s);
-            const float e = __fadd_rn(__fsub_rn(s, __fsub_rn(s2, bb)), __fsub_rn(h, bb));
-            s = s2;
-            t = __fadd_rn(t, __fadd_rn(e, lo));
-        }
-        return (acc + (double)s) + (double)t;
-    }
-}
-
 // Per-thread accumulator of one dot product over the units a thread sweeps.
 // FP64 vectors: one FMA per term into the FP64 sum.  FP32 vectors: the
-// compensated dot product Dot2 of Ogita, Rump & Oishi (2005) -- TwoProduct
-// per term, TwoSum into a running FP32 pair (s, t) -- flushed into the FP64
-// sum every kFlushUnits units, so the running pair never covers more than
-// kFlushUnits * VEC terms (error O(eps_32^2) relative to the sum of |terms|
-// per flush) and the FP64 pipe sees two conversions and two adds per flush.
+// compensated dot product Dot2 of Ogita, Rump & Oishi, "Accurate sum and dot
+// product", SIAM J. Sci. Comput. 26(6), 2005 -- Dekker's TwoProduct (via FMA)
+// per term and Knuth's TwoSum into a running FP32 pair (s, t) -- flushed
+// into the FP64 sum every kFlushUnits units, so a pair never covers more than
+// kFlushUnits * VEC terms (error O(eps_32^2) of the sum of |terms| per flush)
+// and the FP64 pipe (a small fraction of the FP32 rate on GB300) sees two
+// conversions and two adds per flush instead of three operations per term.
 constexpr int kFlushUnits = 4;
 
 template <typename T, int VEC>
@@ -588,10 +643,10 @@ struct DotAcc {
 
 // ------------------------------------------------------------------------
 // Residual sweep: r = b - A x (FP64; the stored operator values widened),
-// partial ||r||^2 and ||b||^2.  Units of kBlock * V64 rows.
+// this CTA's ||r||^2 and ||b||^2 in s.out[0..1].  Units of kBlock * V64 rows.
 // ------------------------------------------------------------------------
-template <typename T, int VEC, int OP>
-__device__ void residual_sweep(const SolveArgs<T> &a, Smem<T> &s)
+template <typename T, int VEC, int OP, class Grp>
+__device__ void residual_sweep(const SolveArgs<T> &a, Smem<T> &s, const Grp &grp)
 {
     constexpr int V64 = (VEC >= 2) ? 2 : 1;
     constexpr int UNIT = kBlock * V64;
@@ -600,7 +655,7 @@ __device__ void residual_sweep(const SolveArgs<T> &a, Smem<T> &s)
     const double cC = (double)(T)a.st.center, cO = (double)(T)a.st.off;
     double acc[2] = {0.0, 0.0};
     Ld1<double> ld{a.x};
-    for (int64_t u = blockIdx.x; u < nunits; u += gridDim.x) {
+    for (int64_t u = grp.unit0(); u < nunits; u += grp.ustep()) {
         const int64_t g0 = u * UNIT + (int64_t)threadIdx.x * V64;
         if (g0 >= n) continue;
         double c[V64], w[V64], bv[V64];
@@ -621,30 +676,40 @@ __device__ void residual_sweep(const SolveArgs<T> &a, Smem<T> &s)
         vst<double, V64>(a.r + g0, rv);
     }
     block_sum<2>(acc, s.red, s.out);
-    if (threadIdx.x == 0) {
-        a.npart[(size_t)blockIdx.x * kNormSlots + 0] = s.out[0];
-        a.npart[(size_t)blockIdx.x * kNormSlots + 1] = s.out[1];
-    }
+}
+
+template <typename T>
+__device__ __forceinline__ void write_result(const SolveArgs<T> &a, int status, long long iters,
+                                             long long spmvs, long long restarts,
+                                             long long refinements, double recres, double normb,
+                                             double last_rn)
+{
+    DevResult *o = a.out;
+    o->status = (ld_volatile(&o->abort) && status == kStOk) ? kStTimeout : status;
+    o->iters = iters;
+    o->spmvs = spmvs;
+    o->restarts = restarts;
+    o->refinements = refinements;
+    o->recursive_relres = (normb > 0.0) ? recres / normb : 0.0;
+    o->true_relres = (normb > 0.0) ? last_rn / normb : 0.0;
 }
 
 // ------------------------------------------------------------------------
-// The p(l)-CG persistent kernel.
+// p(l)-CG: a whole solve on one group (grid or CTA).
 // ------------------------------------------------------------------------
-template <typename T, int L, int VEC, int OP>
-__global__ void __launch_bounds__(kBlock, (sizeof(T) == 4 && L <= 2) ? 3 : 2) plcg_kernel(SolveArgs<T> a)
+template <typename T, int L, int VEC, int OP, class Grp>
+__device__ void plcg_body(const SolveArgs<T> &a, Smem<T> &s, Grp &grp)
 {
-    __shared__ Smem<T> s;
     constexpr int UNIT = kBlock * VEC;
     constexpr bool kF32 = (sizeof(T) == 4);
     const int64_t n = a.n;
     const int64_t nunits = (n + UNIT - 1) / UNIT;
     const int tid = threadIdx.x;
-    unsigned epoch = 0;
     const T cC = (T)a.st.center, cO = (T)a.st.off;
     // (A z)_g = kc * c + kn * nb (see op_parts)
     const T kc = (OP == kOpStencil) ? cC : T(0), kn = (OP == kOpStencil) ? cO : T(1);
     // xi: the iterate K6 updates (FP64 path: x itself; FP32 path: the inner
-    // correction d, stored in the p-ring's spare vector)
+    // correction d of the refinement step)
     T *xi = kF32 ? a.rc : reinterpret_cast<T *>(a.x);
 
     long long iters = 0, spmvs = 0, restarts = 0, refinements = 0, segments = 0;
@@ -652,10 +717,9 @@ __global__ void __launch_bounds__(kBlock, (sizeof(T) == 4 && L <= 2) ? 3 : 2) pl
     double normb = 0.0, recres = 0.0, last_rn = 0.0;
     int status = kStOk;
 
-#define PLCG_BARRIER()                                                                       \
+#define PLCG_SYNC()                                                                          \
     do {                                                                                     \
-        if (!grid_barrier(a.bar, epoch, a.poll_limit, a.force_timeout, &a.out->abort,       \
-                          &s.ok)) {                                                          \
+        if (!grp.sync(a, s)) {                                                               \
             status = kStTimeout;                                                             \
             goto finish;                                                                     \
         }                                                                                    \
@@ -663,17 +727,20 @@ __global__ void __launch_bounds__(kBlock, (sizeof(T) == 4 && L <= 2) ? 3 : 2) pl
 
     for (;;) {
         // ---- true residual r = b - A x and its norm (Alg. 1 line 1 / the final check)
-        residual_sweep<T, VEC, OP>(a, s);
+        residual_sweep<T, VEC, OP>(a, s, grp);
+        grp.put_norms(a, s);
         spmvs++;
-        PLCG_BARRIER();
-        grid_partials_sum<2>(a.npart, kNormSlots, s.red, s.out);
+        PLCG_SYNC();
+        grp.get_norms(a, s);
         if (segments == 0) normb = sqrt(s.out[0]);
         const double rn = sqrt(s.out[1]);
         last_rn = rn;
         if (normb == 0.0) {
             // b = 0: x = 0 is the solution
-            for (int64_t g = (int64_t)blockIdx.x * kBlock + tid; g < n; g += (int64_t)gridDim.x * kBlock)
-                a.x[g] = 0.0;
+            for (int64_t u = grp.unit0(); u * kBlock < n; u += grp.ustep()) {
+                const int64_t g = u * kBlock + tid;
+                if (g < n) a.x[g] = 0.0;
+            }
             status = kStOk;
             break;
         }
@@ -697,7 +764,7 @@ __global__ void __launch_bounds__(kBlock, (sizeof(T) == 4 && L <= 2) ? 3 : 2) pl
         // ---- Alg. 1 line 1: z^(k)_0 := u_0 := r_0 / ||r_0|| for every k; g_00 := 1
         {
             const double inv = 1.0 / rn;
-            for (int64_t u = blockIdx.x; u < nunits; u += gridDim.x) {
+            for (int64_t u = grp.unit0(); u < nunits; u += grp.ustep()) {
                 const int64_t g0 = u * UNIT + (int64_t)tid * VEC;
                 if (g0 >= n) continue;
                 T z[VEC];
@@ -716,22 +783,21 @@ __global__ void __launch_bounds__(kBlock, (sizeof(T) == 4 && L <= 2) ? 3 : 2) pl
 #pragma unroll
                 for (int q = 0; q < kMaxDots; ++q) s.G[0][q] = 0.0;
                 s.G[0][2 * L] = 1.0;
+                s.Ginv[0] = 1.0;
             }
         }
-        PLCG_BARRIER();
+        PLCG_SYNC();
 
         for (long long i = 0;; ++i) {
-            if (i >= L) {   // MPI_Wait(req(i-l)): sum the partials of iteration i-l
-                grid_partials_sum<2 * L + 1>(a.part + (size_t)((i - L) % (L + 1)) * gridDim.x * kMaxDots,
-                                             kMaxDots, s.red, s.raw);
-            }
+            if (i >= L)   // MPI_Wait(req(i-l)): the reduced dots of iteration i-l
+                grp.template get_dots<2 * L + 1>(a, s, (int)((i - L) % (L + 1)), s.raw);
             if (tid == 0) scalar_step<T, L>(s, a, i, rn, tau, budget);
             __syncthreads();
             const Coef<T> &cf = s.cf;
             if (cf.end >= 0) {
                 // ---- final vector update of the segment
                 if (cf.end != kSegNonfinite) {
-                    for (int64_t u = blockIdx.x; u < nunits; u += gridDim.x) {
+                    for (int64_t u = grp.unit0(); u < nunits; u += grp.ustep()) {
                         const int64_t g0 = u * UNIT + (int64_t)tid * VEC;
                         if (g0 >= n) continue;
                         T xv[VEC], pv[VEC];
@@ -770,12 +836,9 @@ __global__ void __launch_bounds__(kBlock, (sizeof(T) == 4 && L <= 2) ? 3 : 2) pl
                 last_end = cf.end;
                 segments++;
                 if (cf.end == kSegNonfinite) { status = kStNonfinite; goto finish; }
-                {
-                    // |zeta| of the returned iterate for the report
-                    const long long mm = cf.kseg;
-                    recres = (cf.end == kSegLucky) ? 0.0 : fabs(s.zeta[mm & 1]);
-                }
-                PLCG_BARRIER();
+                recres = (cf.end == kSegLucky || cf.end == kSegBreakdown) ? 0.0
+                       : fabs(s.zeta[cf.kseg & 1]);
+                PLCG_SYNC();
                 break;
             }
 
@@ -784,7 +847,7 @@ __global__ void __launch_bounds__(kBlock, (sizeof(T) == 4 && L <= 2) ? 3 : 2) pl
             // the compiler cannot know), so its HBM reads overlap in flight.
             DotAcc<T, VEC> dac[2 * L + 1];
             int since_flush = 0;
-            for (int64_t u = blockIdx.x; u < nunits; u += gridDim.x) {
+            for (int64_t u = grp.unit0(); u < nunits; u += grp.ustep()) {
                 const int64_t g0 = u * UNIT + (int64_t)tid * VEC;
                 if (g0 >= n) continue;
                 const bool rec = cf.mode == 1;
@@ -884,43 +947,33 @@ __global__ void __launch_bounds__(kBlock, (sizeof(T) == 4 && L <= 2) ? 3 : 2) pl
             spmvs++;
             // MPI_Iallreduce(..., req(i)): publish this CTA's partials in slot i mod (l+1)
             block_sum<2 * L + 1>(acc, s.red, s.out);
-            if (tid <= 2 * L)
-                a.part[((size_t)(i % (L + 1)) * gridDim.x + blockIdx.x) * kMaxDots + tid] = s.out[tid];
-            PLCG_BARRIER();
+            grp.put_dots(a, s, (int)(i % (L + 1)), 2 * L + 1);
+            PLCG_SYNC();
         }
     }
 finish:
-    if (blockIdx.x == 0 && tid == 0) {
-        DevResult *o = a.out;
-        o->status = (ld_volatile(&o->abort) && status == kStOk) ? kStTimeout : status;
-        o->iters = iters;
-        o->spmvs = spmvs;
-        o->restarts = restarts;
-        o->refinements = refinements;
-        o->recursive_relres = (normb > 0.0) ? recres / normb : 0.0;
-        o->true_relres = (normb > 0.0) ? last_rn / normb : 0.0;
-    }
-#undef PLCG_BARRIER
+    if (grp.leader() && tid == 0)
+        write_result(a, status, iters, spmvs, restarts, refinements, recres, normb, last_rn);
+    __syncthreads();
+#undef PLCG_SYNC
 }
 
 // ------------------------------------------------------------------------
-// Classic CG (Hestenes-Stiefel) persistent kernel: two barriers per
+// Classic CG (Hestenes-Stiefel) on one group: two synchronisations per
 // iteration (after (p, Ap) and after (r, r)).  p lives in a ring of two
-// vectors because the SpMV of step k reads neighbours of p_k while p_{k+1}
-// is written.  q = A p is in a.p; the recursive residual is r itself on the
-// FP64 path and a.rc (FP32) on the FP32 path, whose inner iterate is the
-// ring's third vector.
+// vectors because the SpMV of step k reads neighbours of p_{k-1} while p_k is
+// written.  q = A p is in a.p; the recursive residual is r itself on the FP64
+// path and a.rc (FP32) on the FP32 path, whose inner iterate is the ring's
+// third vector.
 // ------------------------------------------------------------------------
-template <typename T, int VEC, int OP>
-__global__ void __launch_bounds__(kBlock, 3) cg_kernel(SolveArgs<T> a)
+template <typename T, int VEC, int OP, class Grp>
+__device__ void cg_body(const SolveArgs<T> &a, Smem<T> &s, Grp &grp)
 {
-    __shared__ Smem<T> s;
     constexpr int UNIT = kBlock * VEC;
     constexpr bool kF32 = (sizeof(T) == 4);
     const int64_t n = a.n;
     const int64_t nunits = (n + UNIT - 1) / UNIT;
     const int tid = threadIdx.x;
-    unsigned epoch = 0;
     const T cC = (T)a.st.center, cO = (T)a.st.off;
     T *pr[2] = {a.zring, a.zring + n};
     T *q = a.p;
@@ -932,26 +985,28 @@ __global__ void __launch_bounds__(kBlock, 3) cg_kernel(SolveArgs<T> a)
     double normb = 0.0, recres = 0.0, last_rn = 0.0;
     int status = kStOk;
 
-#define CG_BARRIER()                                                                         \
+#define CG_SYNC()                                                                            \
     do {                                                                                     \
-        if (!grid_barrier(a.bar, epoch, a.poll_limit, a.force_timeout, &a.out->abort,       \
-                          &s.ok)) {                                                          \
+        if (!grp.sync(a, s)) {                                                               \
             status = kStTimeout;                                                             \
             goto finish;                                                                     \
         }                                                                                    \
     } while (0)
 
     for (;;) {
-        residual_sweep<T, VEC, OP>(a, s);
+        residual_sweep<T, VEC, OP>(a, s, grp);
+        grp.put_norms(a, s);
         spmvs++;
-        CG_BARRIER();
-        grid_partials_sum<2>(a.npart, kNormSlots, s.red, s.out);
+        CG_SYNC();
+        grp.get_norms(a, s);
         if (segments == 0) normb = sqrt(s.out[0]);
         const double rn = sqrt(s.out[1]);
         last_rn = rn;
         if (normb == 0.0) {
-            for (int64_t g = (int64_t)blockIdx.x * kBlock + tid; g < n; g += (int64_t)gridDim.x * kBlock)
-                a.x[g] = 0.0;
+            for (int64_t u = grp.unit0(); u * kBlock < n; u += grp.ustep()) {
+                const int64_t g = u * kBlock + tid;
+                if (g < n) a.x[g] = 0.0;
+            }
             status = kStOk;
             break;
         }
@@ -974,8 +1029,8 @@ __global__ void __launch_bounds__(kBlock, 3) cg_kernel(SolveArgs<T> a)
         double rr = rn * rn;
         if constexpr (kF32) {
             // rc = (float) r, d = 0, rr from the rounded values
-            double acc[1] = {0.0};
-            for (int64_t u = blockIdx.x; u < nunits; u += gridDim.x) {
+            DotAcc<T, VEC> d0;
+            for (int64_t u = grp.unit0(); u < nunits; u += grp.ustep()) {
                 const int64_t g0 = u * UNIT + (int64_t)tid * VEC;
                 if (g0 >= n) continue;
                 T z[VEC], zero[VEC];
@@ -984,14 +1039,16 @@ __global__ void __launch_bounds__(kBlock, 3) cg_kernel(SolveArgs<T> a)
                     z[v] = (T)a.r[g0 + v];
                     zero[v] = T(0);
                 }
-                acc[0] = group_dot<T, VEC>(z, z, acc[0]);
+                d0.add(z, z);
+                d0.flush();
                 vst<T, VEC>(rc + g0, z);
                 vst<T, VEC>(xi + g0, zero);
             }
+            double acc[1] = {d0.acc};
             block_sum<1>(acc, s.red, s.out);
-            if (tid == 0) a.part[blockIdx.x * kMaxDots] = s.out[0];
-            CG_BARRIER();
-            grid_partials_sum<1>(a.part, kMaxDots, s.red, s.raw);
+            grp.put_dots(a, s, 0, 1);
+            CG_SYNC();
+            grp.template get_dots<1>(a, s, 0, s.raw);
             rr = s.raw[0];
         }
         long long k = 0;
@@ -1004,8 +1061,9 @@ __global__ void __launch_bounds__(kBlock, 3) cg_kernel(SolveArgs<T> a)
             // ---- p_k = r_k + beta_{k-1} p_{k-1};  q = A p_k;  (p_k, q)
             T *pn = pr[(k + 1) & 1];
             const T *po = pr[k & 1];
-            double acc[1] = {0.0};
-            for (int64_t u = blockIdx.x; u < nunits; u += gridDim.x) {
+            DotAcc<T, VEC> d1;
+            int since_flush = 0;
+            for (int64_t u = grp.unit0(); u < nunits; u += grp.ustep()) {
                 const int64_t g0 = u * UNIT + (int64_t)tid * VEC;
                 if (g0 >= n) continue;
                 T c[VEC], w[VEC];
@@ -1015,20 +1073,24 @@ __global__ void __launch_bounds__(kBlock, 3) cg_kernel(SolveArgs<T> a)
                     op_apply<T, T, VEC, OP>(a, cC, cO, LdAxpy<T>{rc, po, (T)beta}, g0, c, w);
                 vst<T, VEC>(pn + g0, c);
                 vst<T, VEC>(q + g0, w);
-                acc[0] = group_dot<T, VEC>(c, w, acc[0]);
+                d1.add(c, w);
+                if (++since_flush == kFlushUnits) { d1.flush(); since_flush = 0; }
             }
+            d1.flush();
             spmvs++;
+            double acc[1] = {d1.acc};
             block_sum<1>(acc, s.red, s.out);
-            if (tid == 0) a.part[(size_t)blockIdx.x * kMaxDots] = s.out[0];
-            CG_BARRIER();
-            grid_partials_sum<1>(a.part, kMaxDots, s.red, s.raw);
+            grp.put_dots(a, s, 0, 1);
+            CG_SYNC();
+            grp.template get_dots<1>(a, s, 0, s.raw);
             const double pq = s.raw[0];
             if (!(pq > 0.0)) { end = isfinite(pq) ? kSegBreakdown : kSegNonfinite; break; }
             const double alpha = rr / pq;
             const T al = (T)alpha;
             // ---- x += alpha p; r -= alpha q; (r, r)
-            double acc2[1] = {0.0};
-            for (int64_t u = blockIdx.x; u < nunits; u += gridDim.x) {
+            DotAcc<T, VEC> d2;
+            since_flush = 0;
+            for (int64_t u = grp.unit0(); u < nunits; u += grp.ustep()) {
                 const int64_t g0 = u * UNIT + (int64_t)tid * VEC;
                 if (g0 >= n) continue;
                 T pv[VEC], qv[VEC], xv[VEC], rv[VEC];
@@ -1041,14 +1103,17 @@ __global__ void __launch_bounds__(kBlock, 3) cg_kernel(SolveArgs<T> a)
                     xv[v] = fma(al, pv[v], xv[v]);
                     rv[v] = fma(-al, qv[v], rv[v]);
                 }
-                acc2[0] = group_dot<T, VEC>(rv, rv, acc2[0]);
                 vst<T, VEC>(xi + g0, xv);
                 vst<T, VEC>(rc + g0, rv);
+                d2.add(rv, rv);
+                if (++since_flush == kFlushUnits) { d2.flush(); since_flush = 0; }
             }
+            d2.flush();
+            double acc2[1] = {d2.acc};
             block_sum<1>(acc2, s.red, s.out);
-            if (tid == 0) a.part[(size_t)(gridDim.x + blockIdx.x) * kMaxDots] = s.out[0];
-            CG_BARRIER();
-            grid_partials_sum<1>(a.part + (size_t)gridDim.x * kMaxDots, kMaxDots, s.red, s.raw);
+            grp.put_dots(a, s, 1, 1);
+            CG_SYNC();
+            grp.template get_dots<1>(a, s, 1, s.raw);
             const double rr_new = s.raw[0];
             beta = rr_new / rr;
             rr = rr_new;
@@ -1060,7 +1125,7 @@ __global__ void __launch_bounds__(kBlock, 3) cg_kernel(SolveArgs<T> a)
         recres = sqrt(rr);
         if (end == kSegNonfinite) { status = kStNonfinite; goto finish; }
         if constexpr (kF32) {   // x += d
-            for (int64_t u = blockIdx.x; u < nunits; u += gridDim.x) {
+            for (int64_t u = grp.unit0(); u < nunits; u += grp.ustep()) {
                 const int64_t g0 = u * UNIT + (int64_t)tid * VEC;
                 if (g0 >= n) continue;
                 T xv[VEC];
@@ -1069,20 +1134,82 @@ __global__ void __launch_bounds__(kBlock, 3) cg_kernel(SolveArgs<T> a)
                 for (int v = 0; v < VEC; ++v) a.x[g0 + v] += (double)xv[v];
             }
         }
-        CG_BARRIER();
+        CG_SYNC();
     }
 finish:
-    if (blockIdx.x == 0 && tid == 0) {
-        DevResult *o = a.out;
-        o->status = (ld_volatile(&o->abort) && status == kStOk) ? kStTimeout : status;
-        o->iters = iters;
-        o->spmvs = spmvs;
-        o->restarts = restarts;
-        o->refinements = refinements;
-        o->recursive_relres = (normb > 0.0) ? recres / normb : 0.0;
-        o->true_relres = (normb > 0.0) ? last_rn / normb : 0.0;
+    if (grp.leader() && tid == 0)
+        write_result(a, status, iters, spmvs, restarts, refinements, recres, normb, last_rn);
+    __syncthreads();
+#undef CG_SYNC
+}
+
+// ------------------------------------------------------------------------
+// Single-system kernels: the whole grid solves one system (cooperative
+// launch, so that every CTA is resident and the grid barrier can complete).
+// ------------------------------------------------------------------------
+template <typename T, int L, int VEC, int OP>
+__global__ void __launch_bounds__(kBlock, (sizeof(T) == 4 && L <= 2) ? 3 : 2)
+plcg_kernel(SolveArgs<T> a)
+{
+    __shared__ Smem<T> s;
+    GridGroup<T> grp;
+    plcg_body<T, L, VEC, OP>(a, s, grp);
+}
+
+template <typename T, int VEC, int OP>
+__global__ void __launch_bounds__(kBlock, 3) cg_kernel(SolveArgs<T> a)
+{
+    __shared__ Smem<T> s;
+    GridGroup<T> grp;
+    cg_body<T, VEC, OP>(a, s, grp);
+}
+
+// ------------------------------------------------------------------------
+// Batched kernel: many independent stencil systems in one persistent launch.
+// Each CTA takes the next system of a work list (sorted by decreasing size,
+// so the longest solves start first) from an atomic counter, solves it alone
+// with __syncthreads as its barrier, writes that system's result and takes
+// the next; converged systems retire and free their CTA at once.
+// ------------------------------------------------------------------------
+template <typename T, int L>
+__global__ void __launch_bounds__(kBlock, 3) batched_kernel(BatchArgs<T> ba)
+{
+    __shared__ Smem<T> s;
+    __shared__ int s_next;
+    T *ws = reinterpret_cast<T *>(ba.ws + (size_t)blockIdx.x * ba.ws_stride);
+    for (;;) {
+        if (threadIdx.x == 0) s_next = atomicAdd(ba.counter, 1);
+        __syncthreads();
+        const int k = s_next;
+        __syncthreads();
+        if (k >= ba.count) return;
+        const BatchSys &sy = ba.sys[ba.order[k]];
+        SolveArgs<T> a = ba.proto;
+        a.n = (int64_t)sy.nx * sy.ny * sy.nz;
+        a.st.dim = sy.dim;
+        a.st.nx = sy.nx;
+        a.st.ny = sy.ny;
+        a.st.nz = sy.nz;
+        a.st.center = sy.center;
+        a.st.off = sy.off;
+        a.b = sy.b;
+        a.x = sy.x;
+        a.out = sy.out;
+        for (int j = 0; j < kMaxL; ++j) a.sigma[j] = sy.sigma[j];
+        // this CTA's workspace: ring vectors, p, rc (type T), then r (FP64)
+        const int64_t nv = a.n;
+        a.zring = ws;
+        int nvec = 0;
+        for (int j = 0; j <= kMaxL; ++j) nvec += (j <= a.l) ? a.depth[j] : 0;
+        if (a.method == 1) nvec = 3;
+        a.p = ws + (size_t)nvec * nv;
+        a.rc = a.p + nv;
+        a.r = reinterpret_cast<double *>(reinterpret_cast<char *>(ws) +
+                                         ((((size_t)(nvec + 2) * nv * sizeof(T)) + 255) / 256) * 256);
+        BlockGroup<T> grp;
+        if (a.method == 1) cg_body<T, 1, kOpStencil>(a, s, grp);
+        else plcg_body<T, L, 1, kOpStencil>(a, s, grp);
     }
-#undef CG_BARRIER
 }
 
 }  // namespace plcg

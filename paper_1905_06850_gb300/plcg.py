@@ -231,6 +231,26 @@ class Matrix:
         return _result(r)
 
 
+def solve_batched(mats, bs, xs, lmins=None, lmaxs=None, check=True, **kw):
+    """plcg_solve_batched: mats (list of stencil Matrix), bs/xs (lists of
+    float64 CUDA tensors; xs in: x0, out: solutions), optional per-system
+    shift intervals.  Returns (status, list of Result)."""
+    count = len(mats)
+    VP = C.c_void_p
+    hA = (VP * count)(*[m.handle.value for m in mats])
+    hb = (VP * count)(*[b.data_ptr() for b in bs])
+    hx = (VP * count)(*[x.data_ptr() for x in xs])
+    lo = None if lmins is None else (C.c_double * count)(*[float(v) for v in lmins])
+    hi = None if lmaxs is None else (C.c_double * count)(*[float(v) for v in lmaxs])
+    p, keep = make_params(**kw)
+    res = (plcg_result * count)()
+    st = load().plcg_solve_batched(count, hA, hb, hx, lo, hi, C.byref(p), res)
+    del keep
+    if check:
+        _check(st)
+    return st, [_result(r) for r in res]
+
+
 def solve(op: dict, b, x0=None, **kw):
     """Convenience: build the operator, solve on the GPU, return (x, Result)."""
     import torch
