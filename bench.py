@@ -275,6 +275,9 @@ def run_ours(args):
                             "iters_per_s": round(r.iters / r.seconds, 1)}
         extra["fp32_fp64corr"] = mp
 
+    if rank == 0 and not args.quick and not args.no_configs:
+        extra["other_configs"] = other_configs(plcg, W, dev, hbm_peak)
+
     # end to end through the host-pointer entry point (pinned host buffers)
     e2e = None
     if not args.quick:
@@ -318,6 +321,86 @@ def run_ours(args):
         **extra,
     }
     print(json.dumps(line), flush=True)
+
+
+def other_configs(plcg, W, dev, hbm_peak):
+    """Time-to-rtol on the other workloads: the 2D 100^2 Laplacian (FP64,
+    latency-bound), the 27-point heterogeneous CSR on 128^3 (FP32 with FP64
+    correction) and the batch of 4096 shifted 2D Poisson systems (FP32 with
+    FP64 correction, one persistent launch), each against classic CG."""
+    import torch
+    out = {}
+    # ---- 2D 5-point 100^2, FP64, rtol 1e-6
+    c = W.config_2d()
+    A = plcg.Matrix(c["op"])
+    b = torch.tensor(c["b"], device=dev)
+    d = {}
+    for name, kw in (("plcg_l1", {"l": 1}), ("plcg_l2", {"l": 2}), ("plcg_l3", {"l": 3}),
+                     ("classic_cg", {"method": "cg"})):
+        ts = []
+        for _ in range(5):
+            x = torch.zeros_like(b)
+            r = A.solve(b, x, interval=c["interval"], rtol=c["rtol"], **kw)
+            ts.append(r.seconds)
+        d[name] = {"iters": r.iters, "time_to_rtol_us": round(min(ts) * 1e6, 1),
+                   "us_per_iter": round(min(ts) / r.iters * 1e6, 2)}
+    A.close()
+    out["2d_100_fp64_rtol1e-6"] = d
+    # ---- 27-point heterogeneous CSR 128^3, FP32 vectors/values, FP64 correction
+    c = W.config_hetero27(nx=128)
+    op = c["op"]
+    n, nnz = op["n"], int(op["rowptr"][-1])
+    A = plcg.Matrix(op, prec="fp32")
+    b = torch.tensor(c["b"], device=dev)
+    d = {"n": n, "nnz": nnz}
+    for name, kw in (("plcg_l1", {"l": 1}), ("plcg_l2", {"l": 2}), ("plcg_l3", {"l": 3}),
+                     ("classic_cg", {"method": "cg"})):
+        ts = []
+        for _ in range(2):
+            x = torch.zeros_like(b)
+            r = A.solve(b, x, interval=c["interval"], rtol=1e-8, prec="fp32", max_restarts=64,
+                        check=False, **kw)
+            ts.append(r.seconds)
+        ll = kw.get("l", 1)
+        vec_passes = 10 if "method" in kw else 3 * (ll + 1) + 4
+        byt = r.iters * (vec_passes * 4 * n + 8 * nnz + 8 * n)
+        d[name] = {"status": r.status, "iters": r.iters, "restarts": r.restarts,
+                   "refinements": r.refinements, "time_to_rtol_s": round(min(ts), 5),
+                   "hbm_gbs": round(byt / min(ts) / 1e9, 1),
+                   "hbm_frac": round(byt / min(ts) / 1e9 / hbm_peak, 4)}
+    A.close()
+    out["h27_csr_128_fp32"] = d
+    # ---- batched: 4096 shifted 2D Poisson systems, FP32 with FP64 correction
+    systems = W.batched_systems(4096)
+    mats = [plcg.Matrix(s_["op"]) for s_ in systems]
+    bs = [torch.tensor(s_["b"], device=dev) for s_ in systems]
+    lo = [s_["interval"][0] for s_ in systems]
+    hi = [s_["interval"][1] for s_ in systems]
+    unknowns = sum(W.op_size(s_["op"]) for s_ in systems)
+    d = {"systems": len(systems), "unknowns": unknowns}
+    for name, kw in (("plcg_l1", {"l": 1}), ("plcg_l2", {"l": 2}), ("plcg_l3", {"l": 3}),
+                     ("classic_cg", {"method": "cg"})):
+        best = None
+        for _ in range(2):
+            xs = [torch.zeros_like(b_) for b_ in bs]
+            st, res = plcg.solve_batched(mats, bs, xs, lmins=lo, lmaxs=hi, prec="fp32", rtol=1e-8,
+                                         check=False, **kw)
+            t = res[0].seconds
+            best = t if best is None else min(best, t)
+        its = np.array([r.iters for r in res])
+        ok = sum(r.status == 0 for r in res)
+        ll = kw.get("l", 1)
+        vec_passes = 10 if "method" in kw else 3 * (ll + 1) + 4
+        byt = sum(W.op_size(s_["op"]) * r.iters for s_, r in zip(systems, res)) * vec_passes * 4
+        d[name] = {"status": st, "converged": ok, "batch_time_s": round(best, 5),
+                   "solves_per_s": round(len(systems) / best, 1),
+                   "iters_mean": round(float(its.mean()), 1), "iters_max": int(its.max()),
+                   "hbm_gbs": round(byt / best / 1e9, 1),
+                   "hbm_frac": round(byt / best / 1e9 / hbm_peak, 4)}
+    for m in mats:
+        m.close()
+    out["batched_4096_2d_fp32"] = d
+    return out
 
 
 # ---------------------------------------------------------------- CPU oracle
@@ -378,6 +461,7 @@ def main():
     ap.add_argument("--maxit", type=int, default=0, help="cap iterations (profiling runs)")
     ap.add_argument("--prec", default="fp64", choices=["fp64", "fp32"])
     ap.add_argument("--l", type=int, default=L_HEAD)
+    ap.add_argument("--no-configs", action="store_true", help="skip the other workloads")
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3
