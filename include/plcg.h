@@ -106,6 +106,8 @@ typedef struct {
     double recursive_relres;    /* |zeta_k| / ||b|| at the end of the last segment */
     double true_relres;         /* ||b - A x|| / ||b||, FP64, at return           */
     double seconds;             /* device time of the solve (CUDA events)        */
+    double latency;             /* serving: seconds from plcg_submit to completion;
+                                   other entry points: = seconds                 */
 } plcg_result;
 
 /* Fill *p with the defaults listed in plcg_params. */
@@ -181,6 +183,41 @@ plcg_status plcg_solve_batched(int count, plcg_matrix *const *A,
 plcg_status plcg_solve_stencil_noalloc(const plcg_stencil_desc *desc, const double *b,
                                        double *x, const plcg_params *prm,
                                        plcg_result *res, void *stream);
+
+/* ---- serving (continuous batching) ------------------------------------ */
+typedef struct plcg_server plcg_server;
+
+/* Create a solve server on the current device.  A scheduler thread admits
+ * submitted requests in FIFO order as soon as (a) their device workspace fits
+ * the remaining mem_budget_bytes (0: 80% of the free memory at creation),
+ * (b) one of max_inflight stream slots is free (0: 32), and (c) their thread
+ * blocks fit on the GPU next to the solves already running.  Each admitted
+ * request runs as its own persistent launch (Algorithm 1 or CG, as in
+ * plcg_solve) on its own stream, so requests of different sizes overlap on
+ * the device and new requests start while others are running.  A request's
+ * grid size depends only on the request, so its result is bit-identical
+ * whether it runs alone or in a mix.  Errors: PLCG_ERR_INVALID, PLCG_ERR_CUDA. */
+plcg_status plcg_server_create(size_t mem_budget_bytes, int max_inflight, plcg_server **out);
+
+/* Queue a solve of A x = b (device pointers, 16-byte aligned, kept alive by
+ * the caller -- together with A -- until the request completes).  prm is
+ * copied.  Returns PLCG_OK and a ticket, PLCG_ERR_INVALID for bad arguments,
+ * or PLCG_ERR_NOMEM when the request's workspace exceeds the whole budget. */
+plcg_status plcg_submit(plcg_server *S, plcg_matrix *A, const double *b, double *x,
+                        const plcg_params *prm, uint64_t *ticket);
+
+/* PLCG_PENDING while the request is queued or running; once it has finished,
+ * its final status (the result, with res->latency = submit-to-completion
+ * seconds, is written to *res) and the ticket is released.  Unknown or
+ * already-collected tickets: PLCG_ERR_INVALID. */
+plcg_status plcg_poll(plcg_server *S, uint64_t ticket, plcg_result *res);
+
+/* As plcg_poll, but blocks until the request has finished. */
+plcg_status plcg_wait(plcg_server *S, uint64_t ticket, plcg_result *res);
+
+/* Run every queued and running request to completion, then release the
+ * server.  Results not collected are discarded.  NULL is a no-op. */
+void plcg_server_destroy(plcg_server *S);
 
 /* Thread-local message describing the last failure in this thread. */
 const char *plcg_last_error(void);

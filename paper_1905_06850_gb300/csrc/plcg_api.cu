@@ -12,7 +12,13 @@
 #include <cstdio>
 #include <cstring>
 #include <mutex>
+#include <chrono>
+#include <condition_variable>
+#include <deque>
+#include <memory>
 #include <string>
+#include <thread>
+#include <unordered_map>
 #include <vector>
 
 #include "../../include/plcg.h"
@@ -250,9 +256,14 @@ static plcg_status ensure_ws(plcg_matrix *A, size_t bytes)
 
 static inline size_t align_up(size_t v, size_t a) { return (v + a - 1) / a * a; }
 
+// Layout of one solve's workspace and its kernel arguments.  With base ==
+// nullptr only the sizes are computed; *bytes is the workspace size and
+// *out_off the offset of the result record inside it.
 template <typename T>
-static plcg_status run_solve(plcg_matrix *A, const double *b, double *x, const plcg_params *prm,
-                             const double *sigma, plcg_result *res)
+static plcg_status build_solve(const plcg_matrix *A, const double *b, double *x,
+                               const plcg_params *prm, const double *sigma, int max_ctas,
+                               char *base, SolveArgs<T> *args, const void **func_out,
+                               int64_t *P_out, int *per_sm_out, size_t *bytes, size_t *out_off)
 {
     const int64_t n = A->n;
     const int l = prm->l;
@@ -266,7 +277,6 @@ static plcg_status run_solve(plcg_matrix *A, const double *b, double *x, const p
     }
     const void *func = kernel_ptr(f32, op, vec, cg ? 0 : l, cg);
     if (!func) return fail(PLCG_ERR_UNIMPL, "no kernel for prec=%d op=%d vec=%d l=%d", (int)f32, op, vec, l);
-
     int per_sm = 0;
     CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, func, kBlock, 0));
     if (per_sm < 1) return fail(PLCG_ERR_CUDA, "solver kernel cannot be resident");
@@ -274,10 +284,10 @@ static plcg_status run_solve(plcg_matrix *A, const double *b, double *x, const p
     const int64_t nunits = (n + unit - 1) / unit;
     int64_t P = (int64_t)per_sm * A->num_sms;
     if (prm->grid_ctas > 0) P = std::min<int64_t>(P, prm->grid_ctas);
+    if (max_ctas > 0) P = std::min<int64_t>(P, max_ctas);
     P = std::max<int64_t>(1, std::min<int64_t>(P, nunits));
 
-    // ---- workspace layout
-    SolveArgs<T> a;
+    SolveArgs<T> &a = *args;
     std::memset(&a, 0, sizeof(a));
     int nvec = 0;
     if (!cg) {
@@ -292,6 +302,10 @@ static plcg_status run_solve(plcg_matrix *A, const double *b, double *x, const p
     } else {
         nvec = 3;   // p ring of two + the FP32 inner iterate
     }
+    // ring vectors are packed with stride n (ring() indexes whole vectors);
+    // 128-bit access needs n * sizeof(T) to be a multiple of 16
+    if (((size_t)n * sizeof(T)) % 16 != 0 && vec > 1)
+        return fail(PLCG_ERR_INVALID, "internal: vector length not 16-byte aligned");
     const size_t vbytes = align_up((size_t)n * sizeof(T), 256);
     size_t off = 0;
     const size_t o_ring = off; off += vbytes * nvec;
@@ -303,11 +317,12 @@ static plcg_status run_solve(plcg_matrix *A, const double *b, double *x, const p
     const size_t o_npart = off; off += align_up((size_t)P * kNormSlots * sizeof(double), 256);
     const size_t o_bar = off; off += 256;
     const size_t o_out = off; off += align_up(sizeof(DevResult), 256);
-    plcg_status st = ensure_ws(A, off);
-    if (st != PLCG_OK) return st;
-    char *base = static_cast<char *>(A->ws.mem);
-    // x's vector layout is contiguous per vector: ring base[k] counts vectors of n
-    // elements; keep the ring packed (n elements per vector) so ring() indexes it.
+    *bytes = off;
+    *out_off = o_out;
+    *func_out = func;
+    *P_out = P;
+    *per_sm_out = per_sm;
+    if (!base) return PLCG_OK;
     a.n = n;
     a.st = A->st;
     a.csr.rowptr = A->rowptr;
@@ -334,16 +349,56 @@ static plcg_status run_solve(plcg_matrix *A, const double *b, double *x, const p
     a.fp32 = f32 ? 1 : 0;
     a.poll_limit = poll_limit();
     a.force_timeout = g_force_timeout;
-    // The ring is indexed in whole vectors of n elements: pad n to keep every
-    // vector 16-byte aligned.
-    if (((size_t)n * sizeof(T)) % 16 != 0 && vec > 1)
-        return fail(PLCG_ERR_INVALID, "internal: vector length not 16-byte aligned");
+    return PLCG_OK;
+}
 
-    CUDA_TRY(cudaMemsetAsync(base + o_bar, 0, 256, A->stream));
-    CUDA_TRY(cudaMemsetAsync(base + o_out, 0, sizeof(DevResult), A->stream));
-    CUDA_TRY(cudaEventRecord(A->ev0, A->stream));
+// Clear the barrier counter and result record, then launch the persistent
+// solver cooperatively (every CTA resident) on `stream`; returns at once.
+template <typename T>
+static plcg_status launch_built(const SolveArgs<T> &a0, const void *func, int64_t P,
+                                cudaStream_t stream)
+{
+    SolveArgs<T> a = a0;
+    CUDA_TRY(cudaMemsetAsync(a.bar, 0, 256, stream));
+    CUDA_TRY(cudaMemsetAsync(a.out, 0, sizeof(DevResult), stream));
     void *args[] = {&a};
-    CUDA_TRY(cudaLaunchCooperativeKernel(func, dim3((unsigned)P), dim3(kBlock), args, 0, A->stream));
+    CUDA_TRY(cudaLaunchCooperativeKernel(func, dim3((unsigned)P), dim3(kBlock), args, 0, stream));
+    return PLCG_OK;
+}
+
+static plcg_status result_status(const DevResult &o)
+{
+    if (o.status == PLCG_ERR_TIMEOUT)
+        return fail(PLCG_ERR_TIMEOUT, "a bounded device wait expired (grid barrier)");
+    if (o.status != PLCG_OK) {
+        const char *why = o.status == PLCG_ERR_BREAKDOWN ? "square-root breakdowns exceeded max_restarts"
+                        : o.status == PLCG_ERR_MAXIT ? "iteration budget exhausted"
+                        : o.status == PLCG_ERR_NONFINITE ? "non-finite value in the recurrences"
+                        : "solve failed";
+        return fail((plcg_status)o.status, "%s", why);
+    }
+    return PLCG_OK;
+}
+
+template <typename T>
+static plcg_status run_solve(plcg_matrix *A, const double *b, double *x, const plcg_params *prm,
+                             const double *sigma, plcg_result *res)
+{
+    SolveArgs<T> a;
+    const void *func = nullptr;
+    int64_t P = 0;
+    int per_sm = 0;
+    size_t bytes = 0, o_out = 0;
+    plcg_status st = build_solve<T>(A, b, x, prm, sigma, 0, nullptr, &a, &func, &P, &per_sm, &bytes, &o_out);
+    if (st != PLCG_OK) return st;
+    st = ensure_ws(A, bytes);
+    if (st != PLCG_OK) return st;
+    st = build_solve<T>(A, b, x, prm, sigma, 0, static_cast<char *>(A->ws.mem), &a, &func, &P,
+                        &per_sm, &bytes, &o_out);
+    if (st != PLCG_OK) return st;
+    CUDA_TRY(cudaEventRecord(A->ev0, A->stream));
+    st = launch_built<T>(a, func, P, A->stream);
+    if (st != PLCG_OK) return st;
     CUDA_TRY(cudaEventRecord(A->ev1, A->stream));
     CUDA_TRY(cudaMemcpyAsync(A->host_res, a.out, sizeof(DevResult), cudaMemcpyDeviceToHost, A->stream));
     CUDA_TRY(cudaStreamSynchronize(A->stream));
@@ -359,17 +414,9 @@ static plcg_status run_solve(plcg_matrix *A, const double *b, double *x, const p
         res->recursive_relres = o.recursive_relres;
         res->true_relres = o.true_relres;
         res->seconds = ms * 1e-3;
+        res->latency = res->seconds;
     }
-    if (o.status == PLCG_ERR_TIMEOUT)
-        return fail(PLCG_ERR_TIMEOUT, "a bounded device wait expired (grid barrier)");
-    if (o.status != PLCG_OK) {
-        const char *why = o.status == PLCG_ERR_BREAKDOWN ? "square-root breakdowns exceeded max_restarts"
-                        : o.status == PLCG_ERR_MAXIT ? "iteration budget exhausted"
-                        : o.status == PLCG_ERR_NONFINITE ? "non-finite value in the recurrences"
-                        : "solve failed";
-        return fail((plcg_status)o.status, "%s", why);
-    }
-    return PLCG_OK;
+    return result_status(o);
 }
 
 static plcg_status check_params(const plcg_matrix *A, const plcg_params *p)
@@ -590,6 +637,7 @@ static plcg_status run_batched(int count, plcg_matrix *const *A, const double *c
             results[i].recursive_relres = o.recursive_relres;
             results[i].true_relres = o.true_relres;
             results[i].seconds = ms * 1e-3;
+            results[i].latency = ms * 1e-3;
         }
         if (first == PLCG_OK && o.status != PLCG_OK) first = (plcg_status)o.status;
     }
@@ -618,4 +666,300 @@ extern "C" plcg_status plcg_solve_batched(int count, plcg_matrix *const *A, cons
     CUDA_TRY(cudaSetDevice(A[0]->device));
     if (prm->prec == PLCG_FP64) return run_batched<double>(count, A, b, x, lmin, lmax, prm, results);
     return run_batched<float>(count, A, b, x, lmin, lmax, prm, results);
+}
+
+// ------------------------------------------------------------------ serving
+// Continuous batching of solves: a scheduler thread admits submitted requests
+// in FIFO order whenever their workspace fits the device-memory budget, a
+// stream slot is free and their CTAs fit next to the in-flight solves (so
+// every cooperative grid can be resident at once and its grid barriers always
+// complete).  Each admitted request runs as its own persistent launch on its
+// own stream; its grid size depends only on the request (its n, kernel and
+// the per-request cap), so a request gives the same bits alone or in a mix.
+namespace {
+
+struct ServerReq {
+    uint64_t ticket = 0;
+    plcg_matrix *A = nullptr;
+    const double *b = nullptr;
+    double *x = nullptr;
+    plcg_params prm{};
+    double shifts[kMaxL] = {0};
+    double sigma[kMaxL] = {0};
+    size_t bytes = 0;
+    int64_t P = 0;
+    double sm_share = 0.0;    // SMs its CTAs occupy: P / (resident CTAs per SM)
+    int slot = -1;
+    bool done = false;
+    plcg_result res{};
+    std::chrono::steady_clock::time_point t_submit;
+};
+
+}  // namespace
+
+struct plcg_server {
+    int device = 0;
+    int num_sms = 0;
+    size_t budget = 0, used = 0;
+    double sm_used = 0.0;
+    int max_inflight = 0;
+    std::vector<cudaStream_t> streams;
+    std::vector<cudaEvent_t> ev0, ev1, ev2;   // kernel start, kernel end, result copied
+    std::vector<DevResult *> hres;   // pinned, one per slot
+    std::vector<int> free_slots;
+    std::deque<std::shared_ptr<ServerReq>> queue;
+    std::vector<std::shared_ptr<ServerReq>> inflight;
+    std::unordered_map<uint64_t, std::shared_ptr<ServerReq>> tickets;
+    std::mutex mu;
+    std::condition_variable cv_sched, cv_done;
+    std::thread th;
+    bool stop = false;
+    uint64_t next_ticket = 1;
+};
+
+template <typename T>
+static plcg_status server_launch(plcg_server *S, ServerReq &q)
+{
+    const cudaStream_t st = S->streams[q.slot];
+    void *ws = nullptr;
+    CUDA_TRY(cudaMallocAsync(&ws, q.bytes, st));
+    SolveArgs<T> a;
+    const void *func = nullptr;
+    int64_t P = 0;
+    int per_sm = 0;
+    size_t bytes = 0, o_out = 0;
+    plcg_status s = build_solve<T>(q.A, q.b, q.x, &q.prm, q.sigma, (int)q.P, static_cast<char *>(ws),
+                                   &a, &func, &P, &per_sm, &bytes, &o_out);
+    if (s == PLCG_OK) {
+        CUDA_TRY(cudaEventRecord(S->ev0[q.slot], st));
+        s = launch_built<T>(a, func, P, st);
+    }
+    if (s == PLCG_OK) {
+        CUDA_TRY(cudaEventRecord(S->ev1[q.slot], st));
+        CUDA_TRY(cudaMemcpyAsync(S->hres[q.slot], a.out, sizeof(DevResult), cudaMemcpyDeviceToHost, st));
+        CUDA_TRY(cudaEventRecord(S->ev2[q.slot], st));
+    }
+    cudaFreeAsync(ws, st);   // stream-ordered: returned once the solve and the copy are done
+    return s;
+}
+
+static void server_finish(plcg_server *S, const std::shared_ptr<ServerReq> &q, plcg_status launch_st)
+{
+    if (launch_st == PLCG_OK) {
+        const DevResult &o = *S->hres[q->slot];
+        float ms = 0.f;
+        cudaEventElapsedTime(&ms, S->ev0[q->slot], S->ev1[q->slot]);
+        q->res.status = o.status;
+        q->res.iters = o.iters;
+        q->res.spmvs = o.spmvs;
+        q->res.restarts = o.restarts;
+        q->res.refinements = o.refinements;
+        q->res.recursive_relres = o.recursive_relres;
+        q->res.true_relres = o.true_relres;
+        q->res.seconds = ms * 1e-3;
+    } else {
+        q->res.status = launch_st;
+    }
+    q->res.latency =
+        std::chrono::duration<double>(std::chrono::steady_clock::now() - q->t_submit).count();
+    S->used -= q->bytes;
+    S->sm_used -= q->sm_share;
+    S->free_slots.push_back(q->slot);
+    q->done = true;
+}
+
+static void server_loop(plcg_server *S)
+{
+    cudaSetDevice(S->device);
+    std::unique_lock<std::mutex> lk(S->mu);
+    for (;;) {
+        bool progress = false;
+        // admission: FIFO, by memory budget, stream slots and resident CTAs
+        while (!S->queue.empty() && !S->free_slots.empty()) {
+            auto q = S->queue.front();
+            if (q->bytes > S->budget - S->used) break;
+            if (S->sm_used > 0.0 && S->sm_used + q->sm_share > S->num_sms + 1e-9) break;
+            S->queue.pop_front();
+            q->slot = S->free_slots.back();
+            S->free_slots.pop_back();
+            S->used += q->bytes;
+            S->sm_used += q->sm_share;
+            const plcg_status st = (q->prm.prec == PLCG_FP64) ? server_launch<double>(S, *q)
+                                                              : server_launch<float>(S, *q);
+            if (st != PLCG_OK) {
+                server_finish(S, q, st);
+                S->cv_done.notify_all();
+            } else {
+                S->inflight.push_back(q);
+            }
+            progress = true;
+        }
+        // completions
+        for (size_t k = 0; k < S->inflight.size();) {
+            auto &q = S->inflight[k];
+            if (cudaEventQuery(S->ev2[q->slot]) == cudaSuccess) {
+                server_finish(S, q, PLCG_OK);
+                S->inflight[k] = S->inflight.back();
+                S->inflight.pop_back();
+                progress = true;
+                S->cv_done.notify_all();
+            } else {
+                ++k;
+            }
+        }
+        if (S->stop && S->queue.empty() && S->inflight.empty()) break;
+        if (!progress) S->cv_sched.wait_for(lk, std::chrono::microseconds(20));
+    }
+}
+
+extern "C" plcg_status plcg_server_create(size_t mem_budget_bytes, int max_inflight, plcg_server **out)
+{
+    if (!out) return fail(PLCG_ERR_INVALID, "plcg_server_create: NULL out");
+    *out = nullptr;
+    if (max_inflight < 0 || max_inflight > 256)
+        return fail(PLCG_ERR_INVALID, "max_inflight must be in 0..256");
+    plcg_server *S = new plcg_server();
+    CUDA_TRY(cudaGetDevice(&S->device));
+    CUDA_TRY(cudaDeviceGetAttribute(&S->num_sms, cudaDevAttrMultiProcessorCount, S->device));
+    size_t free_b = 0, total_b = 0;
+    CUDA_TRY(cudaMemGetInfo(&free_b, &total_b));
+    S->budget = mem_budget_bytes ? mem_budget_bytes : (size_t)(0.8 * (double)free_b);
+    S->max_inflight = max_inflight ? max_inflight : 32;
+    // keep freed stream-ordered memory cached in the pool for the next request
+    cudaMemPool_t pool;
+    if (cudaDeviceGetDefaultMemPool(&pool, S->device) == cudaSuccess) {
+        uint64_t thr = UINT64_MAX;
+        cudaMemPoolSetAttribute(pool, cudaMemPoolAttrReleaseThreshold, &thr);
+    }
+    for (int k = 0; k < S->max_inflight; ++k) {
+        cudaStream_t st;
+        cudaEvent_t e0, e1, e2;
+        DevResult *h = nullptr;
+        CUDA_TRY(cudaStreamCreateWithFlags(&st, cudaStreamNonBlocking));
+        CUDA_TRY(cudaEventCreate(&e0));
+        CUDA_TRY(cudaEventCreate(&e1));
+        CUDA_TRY(cudaEventCreateWithFlags(&e2, cudaEventDisableTiming));
+        CUDA_TRY(cudaMallocHost(&h, sizeof(DevResult)));
+        S->streams.push_back(st);
+        S->ev0.push_back(e0);
+        S->ev1.push_back(e1);
+        S->ev2.push_back(e2);
+        S->hres.push_back(h);
+        S->free_slots.push_back(S->max_inflight - 1 - k);
+    }
+    S->th = std::thread(server_loop, S);
+    *out = S;
+    return PLCG_OK;
+}
+
+extern "C" plcg_status plcg_submit(plcg_server *S, plcg_matrix *A, const double *b, double *x,
+                                   const plcg_params *prm, uint64_t *ticket)
+{
+    if (!S || !A || !b || !x || !ticket) return fail(PLCG_ERR_INVALID, "plcg_submit: NULL argument");
+    plcg_status st = check_params(A, prm);
+    if (st != PLCG_OK) return st;
+    if ((reinterpret_cast<uintptr_t>(b) | reinterpret_cast<uintptr_t>(x)) & 15)
+        return fail(PLCG_ERR_INVALID, "b and x must be 16-byte aligned");
+    if (A->device != S->device) return fail(PLCG_ERR_INVALID, "matrix and server on different devices");
+    auto q = std::make_shared<ServerReq>();
+    q->A = A;
+    q->b = b;
+    q->x = x;
+    q->prm = *prm;
+    if (prm->method == PLCG_METHOD_PLCG) {
+        if (prm->shifts) {
+            std::memcpy(q->shifts, prm->shifts, prm->l * sizeof(double));
+            q->prm.shifts = q->shifts;
+            std::memcpy(q->sigma, prm->shifts, prm->l * sizeof(double));
+        } else {
+            chebyshev_shifts(prm->l, prm->lmin, prm->lmax, q->sigma);
+        }
+    }
+    // per-request grid cap: at most half of the GPU's resident CTAs, so large
+    // requests never lock small ones out
+    const void *func = nullptr;
+    int64_t P = 0;
+    int per_sm = 0;
+    size_t bytes = 0, o_out = 0;
+    if (prm->prec == PLCG_FP64) {
+        SolveArgs<double> a;
+        st = build_solve<double>(A, b, x, &q->prm, q->sigma, 0, nullptr, &a, &func, &P, &per_sm, &bytes, &o_out);
+    } else {
+        SolveArgs<float> a;
+        st = build_solve<float>(A, b, x, &q->prm, q->sigma, 0, nullptr, &a, &func, &P, &per_sm, &bytes, &o_out);
+    }
+    if (st != PLCG_OK) return st;
+    const int cap = std::max(1, (per_sm * S->num_sms) / 2);
+    q->P = std::min<int64_t>(P, cap);
+    q->sm_share = (double)q->P / per_sm;
+    // recompute the byte count for the capped grid (partials scale with P)
+    if (prm->prec == PLCG_FP64) {
+        SolveArgs<double> a;
+        st = build_solve<double>(A, b, x, &q->prm, q->sigma, (int)q->P, nullptr, &a, &func, &P, &per_sm, &bytes, &o_out);
+    } else {
+        SolveArgs<float> a;
+        st = build_solve<float>(A, b, x, &q->prm, q->sigma, (int)q->P, nullptr, &a, &func, &P, &per_sm, &bytes, &o_out);
+    }
+    if (st != PLCG_OK) return st;
+    q->bytes = bytes;
+    std::lock_guard<std::mutex> lk(S->mu);
+    if (S->stop) return fail(PLCG_ERR_INVALID, "server is shutting down");
+    if (bytes > S->budget)
+        return fail(PLCG_ERR_NOMEM, "request needs %zu bytes of workspace; the budget is %zu", bytes, S->budget);
+    q->ticket = S->next_ticket++;
+    q->t_submit = std::chrono::steady_clock::now();
+    S->queue.push_back(q);
+    S->tickets[q->ticket] = q;
+    *ticket = q->ticket;
+    S->cv_sched.notify_one();
+    return PLCG_OK;
+}
+
+static plcg_status collect(plcg_server *S, uint64_t ticket, plcg_result *res, bool wait)
+{
+    std::unique_lock<std::mutex> lk(S->mu);
+    auto it = S->tickets.find(ticket);
+    if (it == S->tickets.end()) return fail(PLCG_ERR_INVALID, "unknown ticket %llu", (unsigned long long)ticket);
+    auto q = it->second;
+    if (!q->done) {
+        if (!wait) return PLCG_PENDING;
+        S->cv_done.wait(lk, [&] { return q->done; });
+    }
+    if (res) *res = q->res;
+    S->tickets.erase(it);
+    if (q->res.status != PLCG_OK) return fail((plcg_status)q->res.status, "request %llu ended with status %d",
+                                              (unsigned long long)ticket, q->res.status);
+    return PLCG_OK;
+}
+
+extern "C" plcg_status plcg_poll(plcg_server *S, uint64_t ticket, plcg_result *res)
+{
+    if (!S) return fail(PLCG_ERR_INVALID, "plcg_poll: NULL server");
+    return collect(S, ticket, res, false);
+}
+
+extern "C" plcg_status plcg_wait(plcg_server *S, uint64_t ticket, plcg_result *res)
+{
+    if (!S) return fail(PLCG_ERR_INVALID, "plcg_wait: NULL server");
+    return collect(S, ticket, res, true);
+}
+
+extern "C" void plcg_server_destroy(plcg_server *S)
+{
+    if (!S) return;
+    {
+        std::lock_guard<std::mutex> lk(S->mu);
+        S->stop = true;
+        S->cv_sched.notify_all();
+    }
+    if (S->th.joinable()) S->th.join();
+    for (size_t k = 0; k < S->streams.size(); ++k) {
+        cudaStreamSynchronize(S->streams[k]);
+        cudaStreamDestroy(S->streams[k]);
+        cudaEventDestroy(S->ev0[k]);
+        cudaEventDestroy(S->ev1[k]);
+        cudaEventDestroy(S->ev2[k]);
+        cudaFreeHost(S->hres[k]);
+    }
+    delete S;
 }

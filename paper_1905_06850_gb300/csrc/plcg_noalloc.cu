@@ -151,6 +151,7 @@ plcg_status run(const StencilDesc &st, int64_t n, const double *b, double *x,
         res->recursive_relres = o.recursive_relres;
         res->true_relres = o.true_relres;
         res->seconds = 0.0;   // this entry point records no CUDA events
+        res->latency = 0.0;
     }
     if (o.status != PLCG_OK) return nafail((plcg_status)o.status, "solve ended with a non-OK status");
     return PLCG_OK;

@@ -58,7 +58,7 @@ class plcg_result(C.Structure):
     _fields_ = [("status", C.c_int), ("iters", C.c_int64), ("spmvs", C.c_int64),
                 ("restarts", C.c_int64), ("refinements", C.c_int64),
                 ("recursive_relres", C.c_double), ("true_relres", C.c_double),
-                ("seconds", C.c_double)]
+                ("seconds", C.c_double), ("latency", C.c_double)]
 
 
 # every symbol include/plcg.h declares, with (restype, argtypes)
@@ -75,6 +75,11 @@ SIGNATURES = {
                                      _VP]),
     "plcg_solve_stencil_noalloc": (C.c_int, [C.POINTER(plcg_stencil_desc), _VP, _VP,
                                              C.POINTER(plcg_params), C.POINTER(plcg_result), _VP]),
+    "plcg_server_create": (C.c_int, [C.c_size_t, C.c_int, C.POINTER(_VP)]),
+    "plcg_submit": (C.c_int, [_VP, _VP, _VP, _VP, C.POINTER(plcg_params), C.POINTER(C.c_uint64)]),
+    "plcg_poll": (C.c_int, [_VP, C.c_uint64, C.POINTER(plcg_result)]),
+    "plcg_wait": (C.c_int, [_VP, C.c_uint64, C.POINTER(plcg_result)]),
+    "plcg_server_destroy": (None, [_VP]),
     "plcg_last_error": (C.c_char_p, []),
     "plcg_version": (C.c_char_p, []),
     "plcg_debug_set_poll_limit": (None, [C.c_uint64]),
@@ -133,6 +138,7 @@ class Result:
     recursive_relres: float
     true_relres: float
     seconds: float
+    latency: float = 0.0
 
     @property
     def ok(self) -> bool:
@@ -141,7 +147,7 @@ class Result:
 
 def _result(r: plcg_result) -> Result:
     return Result(r.status, r.iters, r.spmvs, r.restarts, r.refinements, r.recursive_relres,
-                  r.true_relres, r.seconds)
+                  r.true_relres, r.seconds, r.latency)
 
 
 def make_params(method="plcg", l=1, shifts=None, interval=(0.0, 8.0), rtol=1e-8, maxit=100000,
@@ -249,6 +255,56 @@ def solve_batched(mats, bs, xs, lmins=None, lmaxs=None, check=True, **kw):
     if check:
         _check(st)
     return st, [_result(r) for r in res]
+
+
+class Server:
+    """plcg_server_*: continuous batching of solves (see include/plcg.h)."""
+
+    def __init__(self, mem_budget_bytes=0, max_inflight=0):
+        h = _VP()
+        _check(load().plcg_server_create(int(mem_budget_bytes), int(max_inflight), C.byref(h)))
+        self.handle = h
+        self._keep = {}
+
+    def submit(self, mat: Matrix, b, x, **kw) -> int:
+        p, keep = make_params(**kw)
+        t = C.c_uint64()
+        _check(load().plcg_submit(self.handle, mat.handle, b.data_ptr(), x.data_ptr(), C.byref(p),
+                                  C.byref(t)))
+        self._keep[t.value] = (mat, b, x)
+        del keep
+        return t.value
+
+    def poll(self, ticket: int):
+        """None while pending, else the Result."""
+        r = plcg_result()
+        st = load().plcg_poll(self.handle, ticket, C.byref(r))
+        if st == PLCG_PENDING:
+            return None
+        if st == PLCG_ERR_INVALID and r.status == 0 and r.iters == 0:
+            raise PlcgError(st, last_error())
+        self._keep.pop(ticket, None)
+        return _result(r)
+
+    def wait(self, ticket: int) -> Result:
+        r = plcg_result()
+        st = load().plcg_wait(self.handle, ticket, C.byref(r))
+        if st == PLCG_ERR_INVALID and r.status == 0 and r.iters == 0:
+            raise PlcgError(st, last_error())
+        self._keep.pop(ticket, None)
+        return _result(r)
+
+    def close(self):
+        if getattr(self, "handle", None) and self.handle.value:
+            load().plcg_server_destroy(self.handle)
+            self.handle = _VP()
+            self._keep.clear()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
 
 
 def solve(op: dict, b, x0=None, **kw):
