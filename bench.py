@@ -400,7 +400,94 @@ def other_configs(plcg, W, dev, hbm_peak):
     for m in mats:
         m.close()
     out["batched_4096_2d_fp32"] = d
+    out["serving_mixed_fp32"] = serving(plcg, W, dev)
     return out
+
+
+def serving(plcg, W, dev):
+    """Open-loop serving run: Poisson arrivals (2000/s) over a 0.25 s window
+    of requests with n log-uniform in [1e3, 4e6] and operator type uniform
+    over {2D stencil, 3D stencil, random SPD CSR}; FP32 with FP64 correction,
+    p(1)-CG, rtol 1e-8.  The offered load exceeds one GPU (the window then
+    drains); a second run at 70% of the measured completion rate follows.
+    CSR sizes are rounded to 12 log-spaced buckets whose matrices are built
+    once (random CSR generation for every request would take minutes)."""
+    import torch
+    buckets = np.exp(np.linspace(np.log(1e3), np.log(4e6), 12))
+    mats = {}
+
+    def realise(req):
+        n = req["n_target"]
+        if req["type"] == "2d":
+            s_ = max(4, int(round(n ** 0.5)))
+            key = ("2d", s_)
+            if key not in mats:
+                mats[key] = plcg.Matrix(W.fp32_rounded(W.stencil2d(s_, s_)), prec="fp32")
+            iv = (0.0, 8.0)
+        elif req["type"] == "3d":
+            s_ = max(4, int(round(n ** (1 / 3))))
+            key = ("3d", s_)
+            if key not in mats:
+                mats[key] = plcg.Matrix(W.fp32_rounded(W.stencil3d(s_, s_, s_)), prec="fp32")
+            iv = (0.0, 12.0)
+        else:
+            nb = int(round(buckets[int(np.argmin(np.abs(np.log(buckets) - np.log(n))))]))
+            key = ("csr", nb)
+            if key not in mats:
+                op = W.random_spd_csr(nb, seed=1000 + nb)
+                mats[key] = (plcg.Matrix(op, prec="fp32"), W.shift_interval(op))
+            m, iv = mats[key]
+            return m, iv
+        return mats[key], iv
+
+    def run(reqs):
+        items = []
+        for q in reqs:
+            m, iv = realise(q)
+            g = torch.Generator(device=dev)
+            g.manual_seed(q["seed"])
+            b = torch.randn(m.n, generator=g, device=dev, dtype=torch.float64)
+            items.append((q["t"], m, iv, b, torch.zeros_like(b)))
+        torch.cuda.synchronize()
+        S = plcg.Server()
+        t0 = time.perf_counter()
+        pending, results, i = {}, [], 0
+        t_last = t0
+        while i < len(items) or pending:
+            now = time.perf_counter() - t0
+            while i < len(items) and items[i][0] <= now:
+                _, m, iv, b, x = items[i]
+                pending[S.submit(m, b, x, l=1, interval=iv, rtol=1e-8, prec="fp32",
+                                 max_restarts=64)] = i
+                i += 1
+            for tk in list(pending):
+                r = S.poll(tk)
+                if r is not None:
+                    results.append(r)
+                    del pending[tk]
+                    t_last = time.perf_counter()
+            if i < len(items) and not pending:
+                time.sleep(max(0.0, items[i][0] - (time.perf_counter() - t0)))
+        S.close()
+        span = t_last - t0
+        lat = np.array([r.latency for r in results]) * 1e3
+        ok = sum(r.status == 0 for r in results)
+        return {"requests": len(items), "converged": ok, "window_s": round(items[-1][0], 3),
+                "makespan_s": round(span, 3), "solves_per_s": round(len(items) / span, 1),
+                "p50_latency_ms": round(float(np.percentile(lat, 50)), 2),
+                "p99_latency_ms": round(float(np.percentile(lat, 99)), 2),
+                "backlog_drain_s": round(span - items[-1][0], 3)}
+
+    reqs = W.serving_stream(duration_s=0.25, rate=2000.0, seed=5)
+    full = run(reqs)
+    rate2 = 0.7 * full["solves_per_s"]
+    reqs2 = W.serving_stream(duration_s=3.0, rate=rate2, seed=6, max_requests=400)
+    light = run(reqs2)
+    light["rate_per_s"] = round(rate2, 1)
+    for m in mats.values():
+        (m[0] if isinstance(m, tuple) else m).close()
+    return {"offered_2000_per_s": full, "at_70pct_capacity": light,
+            "note": "FP32 vectors with FP64 correction, p(1)-CG, rtol 1e-8; CSR sizes bucketed"}
 
 
 # ---------------------------------------------------------------- CPU oracle
