@@ -141,6 +141,8 @@ extern "C" plcg_status plcg_create_stencil(const plcg_stencil_desc *d, void *str
     A->st.nz = (int)nz;
     A->st.center = d->center + d->diag_shift;
     A->st.off = d->off;
+    A->st.dnx = make_fastdiv((uint32_t)d->nx);
+    A->st.dny = make_fastdiv((uint32_t)d->ny);
     plcg_status st = matrix_common_init(A, stream);
     if (st != PLCG_OK) { plcg_destroy(A); return st; }
     *out = A;
@@ -531,6 +533,8 @@ static plcg_status run_batched(int count, plcg_matrix *const *A, const double *c
         y.nx = M->st.nx;
         y.ny = M->st.ny;
         y.nz = M->st.nz;
+        y.dnx = M->st.dnx;
+        y.dny = M->st.dny;
         y.center = M->st.center;
         y.off = M->st.off;
         y.b = b[i];

@@ -29,12 +29,31 @@ struct DevResult {
     double true_relres;
 };
 
+// Division of a 32-bit unsigned x < 2^31 by an invariant d >= 1 with one
+// multiply-high, an add and a shift: Granlund & Montgomery, "Division by
+// invariant integers using multiplication" (PLDI 1994): with
+// l = ceil(log2 d) and m = floor(2^32 (2^l - d) / d) + 1,
+// x / d = (umulhi(x, m) + x) >> l (no overflow since x < 2^31).
+struct FastDivU32 {
+    uint32_t m;
+    uint32_t s;
+};
+
+inline FastDivU32 make_fastdiv(uint32_t d)
+{
+    uint32_t l = 0;
+    while ((uint64_t(1) << l) < d) ++l;
+    const uint64_t m = ((uint64_t(1) << 32) * ((uint64_t(1) << l) - d)) / d + 1;
+    return FastDivU32{(uint32_t)m, l};
+}
+
 // Matrix-free constant-coefficient Dirichlet stencil (5-point 2D / 7-point 3D).
 struct StencilDesc {
     int dim;
     int nx, ny, nz;
     double center;   // includes the diagonal shift
     double off;
+    FastDivU32 dnx, dny;   // division by nx and by ny
 };
 
 // CSR arrays in device memory; val is float or double (see the kernel's T).
@@ -80,6 +99,7 @@ struct SolveArgs {
 struct BatchSys {
     int dim;
     int nx, ny, nz;
+    FastDivU32 dnx, dny;
     double center;            // includes the diagonal shift
     double off;
     const double *b;

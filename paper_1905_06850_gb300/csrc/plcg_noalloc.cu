@@ -224,6 +224,8 @@ extern "C" plcg_status plcg_solve_stencil_noalloc(const plcg_stencil_desc *d, co
     st.nz = (int)nz;
     st.center = d->center + d->diag_shift;
     st.off = d->off;
+    st.dnx = make_fastdiv((uint32_t)d->nx);
+    st.dny = make_fastdiv((uint32_t)d->ny);
     cudaStream_t s = static_cast<cudaStream_t>(stream);
     if (prm->prec == PLCG_FP64) return run<double>(st, n, b, x, prm, sigma, s, base, res);
     return run<float>(st, n, b, x, prm, sigma, s, base, res);

@@ -214,10 +214,12 @@ __device__ __forceinline__ void stencil_parts(const StencilDesc &st, const Ld &l
                                               V (&c)[VEC], V (&nb)[VEC])
 {
     const int nx = st.nx, ny = st.ny;
-    const int64_t line = g0 / nx;
-    const int x0 = (int)(g0 - line * nx);
-    const int y = (int)(line % ny);
-    const int64_t zc = line / ny;
+    // coordinates of row g0 (n < 2^31): x fastest, then y, then z
+    const uint32_t gu = (uint32_t)g0;
+    const uint32_t line = (__umulhi(gu, st.dnx.m) + gu) >> st.dnx.s;
+    const int x0 = (int)(gu - line * (uint32_t)nx);
+    const uint32_t zc = (__umulhi(line, st.dny.m) + line) >> st.dny.s;
+    const int y = (int)(line - zc * (uint32_t)ny);
     ld.template vec<VEC>(g0, c);
     const V left = (x0 > 0) ? ld.one(g0 - 1) : V(0);
     const V right = (x0 + VEC < nx) ? ld.one(g0 + VEC) : V(0);
@@ -242,7 +244,7 @@ __device__ __forceinline__ void stencil_parts(const StencilDesc &st, const Ld &l
 #pragma unroll
             for (int v = 0; v < VEC; ++v) nb[v] += t[v];
         }
-        if (zc < st.nz - 1) {
+        if ((int)zc < st.nz - 1) {
             ld.template vec<VEC>(g0 + nxy, t);
 #pragma unroll
             for (int v = 0; v < VEC; ++v) nb[v] += t[v];
@@ -273,28 +275,28 @@ __device__ __forceinline__ V csr_row(const CsrDesc &A, const Ld &ld, int64_t row
 
 // (c, nb) with (A z)_g = kc * c + kn * nb: stencil (center, off), CSR (0, 1).
 template <typename V, typename C, int VEC, int OP, class Ld>
-__device__ __forceinline__ void op_parts(const SolveArgs<C> &a, const Ld &ld, int64_t g0,
-                                         V (&c)[VEC], V (&nb)[VEC])
+__device__ __forceinline__ void op_parts(const StencilDesc &st, const CsrDesc &csr, const Ld &ld,
+                                         int64_t g0, V (&c)[VEC], V (&nb)[VEC])
 {
     if constexpr (OP == kOpStencil) {
-        stencil_parts<V, VEC>(a.st, ld, g0, c, nb);
+        stencil_parts<V, VEC>(st, ld, g0, c, nb);
     } else {
         static_assert(VEC == 1, "CSR rows are one per thread");
         c[0] = ld.one(g0);
-        nb[0] = csr_row<V, C>(a.csr, ld, g0);
+        nb[0] = csr_row<V, C>(csr, ld, g0);
     }
 }
 
 template <typename V, typename C, int VEC, int OP, class Ld>
-__device__ __forceinline__ void op_apply(const SolveArgs<C> &a, V cC, V cO, const Ld &ld,
-                                         int64_t g0, V (&c)[VEC], V (&w)[VEC])
+__device__ __forceinline__ void op_apply(const StencilDesc &st, const CsrDesc &csr, V cC, V cO,
+                                         const Ld &ld, int64_t g0, V (&c)[VEC], V (&w)[VEC])
 {
     if constexpr (OP == kOpStencil) {
-        stencil_apply<V, VEC>(a.st, cC, cO, ld, g0, c, w);
+        stencil_apply<V, VEC>(st, cC, cO, ld, g0, c, w);
     } else {
         static_assert(VEC == 1, "CSR rows are one per thread");
         c[0] = ld.one(g0);
-        w[0] = csr_row<V, C>(a.csr, ld, g0);
+        w[0] = csr_row<V, C>(csr, ld, g0);
     }
 }
 
@@ -697,13 +699,15 @@ __device__ __forceinline__ void write_result(const SolveArgs<T> &a, int status, 
 // ------------------------------------------------------------------------
 // p(l)-CG: a whole solve on one group (grid or CTA).
 // ------------------------------------------------------------------------
-template <typename T, int L, int VEC, int OP, class Grp>
+template <typename T, int L, int VEC, int OP, class Grp, int RPT = 1>
 __device__ void plcg_body(const SolveArgs<T> &a, Smem<T> &s, Grp &grp)
 {
     constexpr int UNIT = kBlock * VEC;
+    constexpr int USWEEP = UNIT * RPT;   // rows per unit of the iteration sweep
     constexpr bool kF32 = (sizeof(T) == 4);
     const int64_t n = a.n;
     const int64_t nunits = (n + UNIT - 1) / UNIT;
+    const int64_t nunits_s = (n + USWEEP - 1) / USWEEP;
     const int tid = threadIdx.x;
     const T cC = (T)a.st.center, cO = (T)a.st.off;
     // (A z)_g = kc * c + kn * nb (see op_parts)
@@ -842,95 +846,142 @@ __device__ void plcg_body(const SolveArgs<T> &a, Smem<T> &s, Grp &grp)
                 break;
             }
 
-            // ---- one full iteration sweep: K1, K4, K5 (partials), K6.  Each unit
-            // issues every load before any store (the vectors are distinct, but
-            // the compiler cannot know), so its HBM reads overlap in flight.
+            // ---- one full iteration sweep: K1, K4, K5 (partials), K6.  A thread
+            // owns RPT row groups of VEC rows per unit (stride kBlock * VEC) and
+            // issues every load of all of them before any store (the vectors are
+            // distinct, but the compiler cannot know), so its HBM/L2 reads
+            // overlap in flight.
+            // Copy what the sweep reads into locals: the coefficients live in
+            // shared memory and the vector stores go through generic pointers
+            // that the compiler cannot prove disjoint from it, so reading s.cf
+            // inside the loop would re-load every field after every store.
+            const StencilDesc st = a.st;
+            const CsrDesc csr = a.csr;
+            const T *const zl_cur = cf.zl_cur, *const zl_prev = cf.zl_prev;
+            T *const zl_new = cf.zl_new;
+            T *const pvec = a.p;
+            const T *curp[L], *prvp[L];
+            T *nwp[L];
+            T ak[L];
+#pragma unroll
+            for (int k = 0; k < L; ++k) {
+                curp[k] = cf.cur[k];
+                prvp[k] = cf.prv[k];
+                nwp[k] = cf.nw[k];
+                ak[k] = cf.ak[k];
+            }
+            int dsrc[2 * L + 1];
+            const T *dptr[2 * L + 1];
+#pragma unroll
+            for (int q = 0; q <= 2 * L; ++q) {
+                dsrc[q] = cf.dsrc[q];
+                dptr[q] = cf.dptr[q];
+            }
+            const T c_sig = cf.sig, c_invd = cf.invd, c_al = cf.al, c_bm = cf.bm;
+            const T c_zx = cf.zx, c_pv = cf.pv, c_pp = cf.pp;
+            const int c_k6 = cf.k6, c_prev0 = cf.prev0, c_ncopy = cf.ncopy;
+            const bool rec = cf.mode == 1;
+            T *cpyp[kMaxL];
+            for (int k = 0; k < c_ncopy; ++k) cpyp[k] = cf.cpy[k];
             DotAcc<T, VEC> dac[2 * L + 1];
             int since_flush = 0;
-            for (int64_t u = grp.unit0(); u < nunits; u += grp.ustep()) {
-                const int64_t g0 = u * UNIT + (int64_t)tid * VEC;
-                if (g0 >= n) continue;
-                const bool rec = cf.mode == 1;
+            for (int64_t u = grp.unit0(); u < nunits_s; u += grp.ustep()) {
+                int64_t g0[RPT];
+                bool ok[RPT];
+#pragma unroll
+                for (int r = 0; r < RPT; ++r) {
+                    g0[r] = u * USWEEP + ((int64_t)r * kBlock + tid) * VEC;
+                    ok[r] = g0[r] < n;
+                }
                 // -- loads
-                T c[VEC], nb[VEC];
-                op_parts<T, T, VEC, OP>(a, Ld1<T>{cf.zl_cur}, g0, c, nb);   // K1 operands
-                T zp[VEC], cur[L][VEC], pk[L][VEC], pv[VEC], xv[VEC];
+                T c[RPT][VEC], nb[RPT][VEC], zp[RPT][VEC], cur[RPT][L][VEC], pk[RPT][L][VEC];
+                T pv[RPT][VEC], xv[RPT][VEC];
 #pragma unroll
-                for (int v = 0; v < VEC; ++v) zp[v] = T(0);
-                if (rec) {
-                    vld<T, VEC>(cf.zl_prev + g0, zp);
+                for (int r = 0; r < RPT; ++r) {
 #pragma unroll
-                    for (int k = 0; k < L; ++k) vld<T, VEC>(cf.cur[k] + g0, cur[k]);
+                    for (int v = 0; v < VEC; ++v) zp[r][v] = T(0);
+                    if (!ok[r]) continue;
+                    op_parts<T, T, VEC, OP>(st, csr, Ld1<T>{zl_cur}, g0[r], c[r], nb[r]);   // K1 operands
+                    if (rec) {
+                        vld<T, VEC>(zl_prev + g0[r], zp[r]);
 #pragma unroll
-                    for (int k = 0; k < L; ++k) {
-                        if (k > 0 || cf.prev0) {
-                            vld<T, VEC>(cf.prv[k] + g0, pk[k]);
-                        } else {
+                        for (int k = 0; k < L; ++k) vld<T, VEC>(curp[k] + g0[r], cur[r][k]);
 #pragma unroll
-                            for (int v = 0; v < VEC; ++v) pk[k][v] = T(0);
+                        for (int k = 0; k < L; ++k) {
+                            if (k > 0 || c_prev0) {
+                                vld<T, VEC>(prvp[k] + g0[r], pk[r][k]);
+                            } else {
+#pragma unroll
+                                for (int v = 0; v < VEC; ++v) pk[r][k][v] = T(0);
+                            }
                         }
                     }
-                }
-                if (cf.k6 == 2) {
-                    vld<T, VEC>(a.p + g0, pv);
-                    vld<T, VEC>(xi + g0, xv);
-                }
-                // -- compute
-                T un[VEC], nw[L][VEC];
-                if (!rec) {
-                    // u_{i+1} = A z^(l)_i - sigma_i z^(l)_i
-#pragma unroll
-                    for (int v = 0; v < VEC; ++v) un[v] = fma(kc - cf.sig, c[v], kn * nb[v]);
-                } else {
-                    // K4: z^(l)_{i+1} = (A z^(l)_i - gamma z^(l)_i - delta' z^(l)_{i-1}) / delta
-                    // and z^(k)_{i-l+k+1}, k < l (Alg. 1 lines 19-21)
-                    const T uc = fma(kc, cf.invd, cf.al), un_nb = kn * cf.invd;
-#pragma unroll
-                    for (int v = 0; v < VEC; ++v)
-                        un[v] = fma(uc, c[v], fma(un_nb, nb[v], cf.bm * zp[v]));
-#pragma unroll
-                    for (int k = 0; k < L; ++k)
-#pragma unroll
-                        for (int v = 0; v < VEC; ++v) {
-                            const T up = (k == L - 1) ? c[v] : cur[k + 1][v];
-                            nw[k][v] = fma(up, cf.invd, fma(cf.ak[k], cur[k][v], cf.bm * pk[k][v]));
-                        }
-                }
-                // K6: p and the iterate (Alg. 1 lines 26-31)
-                if (cf.k6 == 1) {
-#pragma unroll
-                    for (int v = 0; v < VEC; ++v) pv[v] = cf.pv * cur[0][v];
-                } else if (cf.k6 == 2) {
-#pragma unroll
-                    for (int v = 0; v < VEC; ++v) {
-                        xv[v] = fma(cf.zx, pv[v], xv[v]);
-                        pv[v] = fma(cf.pv, cur[0][v], cf.pp * pv[v]);
+                    if (c_k6 == 2) {
+                        vld<T, VEC>(pvec + g0[r], pv[r]);
+                        vld<T, VEC>(xi + g0[r], xv[r]);
                     }
                 }
-                // -- stores
-                vst<T, VEC>(cf.zl_new + g0, un);
-                if (!rec) {
-                    for (int k = 0; k < cf.ncopy; ++k) vst<T, VEC>(cf.cpy[k] + g0, un);
-                } else {
 #pragma unroll
-                    for (int k = 0; k < L; ++k) vst<T, VEC>(cf.nw[k] + g0, nw[k]);
-                }
-                if (cf.k6 >= 1) vst<T, VEC>(a.p + g0, pv);
-                if (cf.k6 == 2) vst<T, VEC>(xi + g0, xv);
-                // -- K5: partial dot products with u_{i+1} = z^(l)_{i+1}
+                for (int r = 0; r < RPT; ++r) {
+                    if (!ok[r]) continue;
+                    // -- compute
+                    T un[VEC], nw[L][VEC];
+                    if (!rec) {
+                        // u_{i+1} = A z^(l)_i - sigma_i z^(l)_i
 #pragma unroll
-                for (int q = 0; q <= 2 * L; ++q) {
-                    const int src = cf.dsrc[q];
-                    if (src == 0) continue;
-                    T o[VEC];
-                    if (src == 1) {
-                        vld<T, VEC>(cf.dptr[q] + g0, o);
+                        for (int v = 0; v < VEC; ++v) un[v] = fma(kc - c_sig, c[r][v], kn * nb[r][v]);
                     } else {
+                        // K4: z^(l)_{i+1} = (A z^(l)_i - gamma z^(l)_i - delta' z^(l)_{i-1}) / delta
+                        // and z^(k)_{i-l+k+1}, k < l (Alg. 1 lines 19-21)
+                        const T uc = fma(kc, c_invd, c_al), un_nb = kn * c_invd;
 #pragma unroll
                         for (int v = 0; v < VEC; ++v)
-                            o[v] = (src == 2) ? un[v] : (src == 3) ? nw[0][v] : (src == 4) ? c[v] : zp[v];
+                            un[v] = fma(uc, c[r][v], fma(un_nb, nb[r][v], c_bm * zp[r][v]));
+#pragma unroll
+                        for (int k = 0; k < L; ++k)
+#pragma unroll
+                            for (int v = 0; v < VEC; ++v) {
+                                const T up = (k == L - 1) ? c[r][v] : cur[r][k + 1][v];
+                                nw[k][v] = fma(up, c_invd, fma(ak[k], cur[r][k][v], c_bm * pk[r][k][v]));
+                            }
                     }
-                    dac[q].add(un, o);
+                    // K6: p and the iterate (Alg. 1 lines 26-31)
+                    if (c_k6 == 1) {
+#pragma unroll
+                        for (int v = 0; v < VEC; ++v) pv[r][v] = c_pv * cur[r][0][v];
+                    } else if (c_k6 == 2) {
+#pragma unroll
+                        for (int v = 0; v < VEC; ++v) {
+                            xv[r][v] = fma(c_zx, pv[r][v], xv[r][v]);
+                            pv[r][v] = fma(c_pv, cur[r][0][v], c_pp * pv[r][v]);
+                        }
+                    }
+                    // -- stores
+                    vst<T, VEC>(zl_new + g0[r], un);
+                    if (!rec) {
+                        for (int k = 0; k < c_ncopy; ++k) vst<T, VEC>(cpyp[k] + g0[r], un);
+                    } else {
+#pragma unroll
+                        for (int k = 0; k < L; ++k) vst<T, VEC>(nwp[k] + g0[r], nw[k]);
+                    }
+                    if (c_k6 >= 1) vst<T, VEC>(pvec + g0[r], pv[r]);
+                    if (c_k6 == 2) vst<T, VEC>(xi + g0[r], xv[r]);
+                    // -- K5: partial dot products with u_{i+1} = z^(l)_{i+1}
+#pragma unroll
+                    for (int q = 0; q <= 2 * L; ++q) {
+                        const int src = dsrc[q];
+                        if (src == 0) continue;
+                        T o[VEC];
+                        if (src == 1) {
+                            vld<T, VEC>(dptr[q] + g0[r], o);
+                        } else {
+#pragma unroll
+                            for (int v = 0; v < VEC; ++v)
+                                o[v] = (src == 2) ? un[v] : (src == 3) ? nw[0][v] : (src == 4) ? c[r][v]
+                                     : zp[r][v];
+                        }
+                        dac[q].add(un, o);
+                    }
                 }
                 if (++since_flush == kFlushUnits) {
 #pragma unroll
@@ -966,10 +1017,11 @@ finish:
 // path and a.rc (FP32) on the FP32 path, whose inner iterate is the ring's
 // third vector.
 // ------------------------------------------------------------------------
-template <typename T, int VEC, int OP, class Grp>
+template <typename T, int VEC, int OP, class Grp, int RPT = 1>
 __device__ void cg_body(const SolveArgs<T> &a, Smem<T> &s, Grp &grp)
 {
     constexpr int UNIT = kBlock * VEC;
+    constexpr int USWEEP = UNIT * RPT;
     constexpr bool kF32 = (sizeof(T) == 4);
     const int64_t n = a.n;
     const int64_t nunits = (n + UNIT - 1) / UNIT;
@@ -977,6 +1029,8 @@ __device__ void cg_body(const SolveArgs<T> &a, Smem<T> &s, Grp &grp)
     const T cC = (T)a.st.center, cO = (T)a.st.off;
     T *pr[2] = {a.zring, a.zring + n};
     T *q = a.p;
+    const StencilDesc st = a.st;
+    const CsrDesc csr = a.csr;
     T *rc = kF32 ? a.rc : reinterpret_cast<T *>(a.r);
     T *xi = kF32 ? a.zring + 2 * n : reinterpret_cast<T *>(a.x);
 
@@ -1063,17 +1117,26 @@ __device__ void cg_body(const SolveArgs<T> &a, Smem<T> &s, Grp &grp)
             const T *po = pr[k & 1];
             DotAcc<T, VEC> d1;
             int since_flush = 0;
-            for (int64_t u = grp.unit0(); u < nunits; u += grp.ustep()) {
-                const int64_t g0 = u * UNIT + (int64_t)tid * VEC;
-                if (g0 >= n) continue;
-                T c[VEC], w[VEC];
-                if (k == 0)
-                    op_apply<T, T, VEC, OP>(a, cC, cO, LdFirst<T>{rc}, g0, c, w);
-                else
-                    op_apply<T, T, VEC, OP>(a, cC, cO, LdAxpy<T>{rc, po, (T)beta}, g0, c, w);
-                vst<T, VEC>(pn + g0, c);
-                vst<T, VEC>(q + g0, w);
-                d1.add(c, w);
+            const int64_t nunits_s = (n + USWEEP - 1) / USWEEP;
+            for (int64_t u = grp.unit0(); u < nunits_s; u += grp.ustep()) {
+                T c[RPT][VEC], w[RPT][VEC];
+                int64_t g0[RPT];
+#pragma unroll
+                for (int r = 0; r < RPT; ++r) {
+                    g0[r] = u * USWEEP + ((int64_t)r * kBlock + tid) * VEC;
+                    if (g0[r] >= n) continue;
+                    if (k == 0)
+                        op_apply<T, T, VEC, OP>(st, csr, cC, cO, LdFirst<T>{rc}, g0[r], c[r], w[r]);
+                    else
+                        op_apply<T, T, VEC, OP>(st, csr, cC, cO, LdAxpy<T>{rc, po, (T)beta}, g0[r], c[r], w[r]);
+                }
+#pragma unroll
+                for (int r = 0; r < RPT; ++r) {
+                    if (g0[r] >= n) continue;
+                    vst<T, VEC>(pn + g0[r], c[r]);
+                    vst<T, VEC>(q + g0[r], w[r]);
+                    d1.add(c[r], w[r]);
+                }
                 if (++since_flush == kFlushUnits) { d1.flush(); since_flush = 0; }
             }
             d1.flush();
@@ -1090,22 +1153,30 @@ __device__ void cg_body(const SolveArgs<T> &a, Smem<T> &s, Grp &grp)
             // ---- x += alpha p; r -= alpha q; (r, r)
             DotAcc<T, VEC> d2;
             since_flush = 0;
-            for (int64_t u = grp.unit0(); u < nunits; u += grp.ustep()) {
-                const int64_t g0 = u * UNIT + (int64_t)tid * VEC;
-                if (g0 >= n) continue;
-                T pv[VEC], qv[VEC], xv[VEC], rv[VEC];
-                vld<T, VEC>(pn + g0, pv);
-                vld<T, VEC>(q + g0, qv);
-                vld<T, VEC>(xi + g0, xv);
-                vld<T, VEC>(rc + g0, rv);
+            for (int64_t u = grp.unit0(); u < nunits_s; u += grp.ustep()) {
+                T pv[RPT][VEC], qv[RPT][VEC], xv[RPT][VEC], rv[RPT][VEC];
+                int64_t g0[RPT];
 #pragma unroll
-                for (int v = 0; v < VEC; ++v) {
-                    xv[v] = fma(al, pv[v], xv[v]);
-                    rv[v] = fma(-al, qv[v], rv[v]);
+                for (int r = 0; r < RPT; ++r) {
+                    g0[r] = u * USWEEP + ((int64_t)r * kBlock + tid) * VEC;
+                    if (g0[r] >= n) continue;
+                    vld<T, VEC>(pn + g0[r], pv[r]);
+                    vld<T, VEC>(q + g0[r], qv[r]);
+                    vld<T, VEC>(xi + g0[r], xv[r]);
+                    vld<T, VEC>(rc + g0[r], rv[r]);
                 }
-                vst<T, VEC>(xi + g0, xv);
-                vst<T, VEC>(rc + g0, rv);
-                d2.add(rv, rv);
+#pragma unroll
+                for (int r = 0; r < RPT; ++r) {
+                    if (g0[r] >= n) continue;
+#pragma unroll
+                    for (int v = 0; v < VEC; ++v) {
+                        xv[r][v] = fma(al, pv[r][v], xv[r][v]);
+                        rv[r][v] = fma(-al, qv[r][v], rv[r][v]);
+                    }
+                    vst<T, VEC>(xi + g0[r], xv[r]);
+                    vst<T, VEC>(rc + g0[r], rv[r]);
+                    d2.add(rv[r], rv[r]);
+                }
                 if (++since_flush == kFlushUnits) { d2.flush(); since_flush = 0; }
             }
             d2.flush();
@@ -1171,8 +1242,13 @@ __global__ void __launch_bounds__(kBlock, 3) cg_kernel(SolveArgs<T> a)
 // with __syncthreads as its barrier, writes that system's result and takes
 // the next; converged systems retire and free their CTA at once.
 // ------------------------------------------------------------------------
+// Row groups per thread in the batched kernel, where one CTA streams a whole
+// system and needs several loads in flight per thread (fewer for larger l,
+// whose sweep holds more vectors in registers).
+template <int L> constexpr int kBatchRPT = (L == 1) ? 4 : 2;
+
 template <typename T, int L>
-__global__ void __launch_bounds__(kBlock, 3) batched_kernel(BatchArgs<T> ba)
+__global__ void __launch_bounds__(kBlock, 2) batched_kernel(BatchArgs<T> ba)
 {
     __shared__ Smem<T> s;
     __shared__ int s_next;
@@ -1190,6 +1266,8 @@ __global__ void __launch_bounds__(kBlock, 3) batched_kernel(BatchArgs<T> ba)
         a.st.nx = sy.nx;
         a.st.ny = sy.ny;
         a.st.nz = sy.nz;
+        a.st.dnx = sy.dnx;
+        a.st.dny = sy.dny;
         a.st.center = sy.center;
         a.st.off = sy.off;
         a.b = sy.b;
@@ -1207,8 +1285,8 @@ __global__ void __launch_bounds__(kBlock, 3) batched_kernel(BatchArgs<T> ba)
         a.r = reinterpret_cast<double *>(reinterpret_cast<char *>(ws) +
                                          ((((size_t)(nvec + 2) * nv * sizeof(T)) + 255) / 256) * 256);
         BlockGroup<T> grp;
-        if (a.method == 1) cg_body<T, 1, kOpStencil>(a, s, grp);
-        else plcg_body<T, L, 1, kOpStencil>(a, s, grp);
+        if (a.method == 1) cg_body<T, 1, kOpStencil, BlockGroup<T>, 4>(a, s, grp);
+        else plcg_body<T, L, 1, kOpStencil, BlockGroup<T>, kBatchRPT<L>>(a, s, grp);
     }
 }
 
