@@ -378,8 +378,10 @@ def other_configs(plcg, W, dev, hbm_peak):
     hi = [s_["interval"][1] for s_ in systems]
     unknowns = sum(W.op_size(s_["op"]) for s_ in systems)
     d = {"systems": len(systems), "unknowns": unknowns}
+    from paper_1905_06850_gb300 import autotune
     for name, kw in (("plcg_l1", {"l": 1}), ("plcg_l2", {"l": 2}), ("plcg_l3", {"l": 3}),
                      ("classic_cg", {"method": "cg"})):
+        sched, _ = autotune.tune_batched(mats, bs, lo, hi, prec="fp32", rtol=1e-8, **kw)
         best = None
         for _ in range(2):
             xs = [torch.zeros_like(b_) for b_ in bs]
@@ -393,10 +395,13 @@ def other_configs(plcg, W, dev, hbm_peak):
         vec_passes = 10 if "method" in kw else 3 * (ll + 1) + 4
         byt = sum(W.op_size(s_["op"]) * r.iters for s_, r in zip(systems, res)) * vec_passes * 4
         d[name] = {"status": st, "converged": ok, "batch_time_s": round(best, 5),
+                   "schedule": {"gang_size": sched[0], "large_work_factor": sched[1],
+                                "max_gang_fraction": sched[2]},
                    "solves_per_s": round(len(systems) / best, 1),
                    "iters_mean": round(float(its.mean()), 1), "iters_max": int(its.max()),
                    "hbm_gbs": round(byt / best / 1e9, 1),
                    "hbm_frac": round(byt / best / 1e9 / hbm_peak, 4)}
+    autotune.set_schedule(0)
     for m in mats:
         m.close()
     out["batched_4096_2d_fp32"] = d

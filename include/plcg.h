@@ -153,7 +153,9 @@ plcg_status plcg_solve_host(plcg_matrix *A, const double *b, double *x,
  * systems retire and their blocks take the next system.  prm applies to
  * every system except that shifts == NULL places Chebyshev shifts on each
  * system's own [lmin_i, lmax_i] given in lmin[], lmax[] (may be NULL: then
- * prm->lmin/lmax for all).  results[count] may be NULL.  Only stencil
+ * prm->lmin/lmax for all).  Systems of large estimated work are solved by
+ * gangs of thread blocks (see plcg_set_batched_schedule), the rest by one
+ * thread block each; each results[i].seconds is the whole batch's time.  results[count] may be NULL.  Only stencil
  * matrices are supported (PLCG_ERR_UNIMPL otherwise).
  * Returns PLCG_OK when every system returned PLCG_OK, else the first
  * non-OK status in index order. */
@@ -218,6 +220,16 @@ plcg_status plcg_wait(plcg_server *S, uint64_t ticket, plcg_result *res);
 /* Run every queued and running request to completion, then release the
  * server.  Results not collected are discarded.  NULL is a no-op. */
 void plcg_server_destroy(plcg_server *S);
+
+/* Schedule of plcg_solve_batched (set by an autotuner; process-wide).  The
+ * systems whose estimated work n * sqrt(kappa) exceeds large_work_factor
+ * times one CTA's fair share of the batch are solved by gangs of gang_size
+ * thread blocks each (at most max_gang_fraction of the launch's blocks form
+ * gangs); the others get one thread block each.  gang_size = 0 restores the
+ * defaults (8, 1.0, 0.5); gang_size = 1 disables gangs.  Errors:
+ * PLCG_ERR_INVALID. */
+plcg_status plcg_set_batched_schedule(int gang_size, double large_work_factor,
+                                      double max_gang_fraction);
 
 /* Thread-local message describing the last failure in this thread. */
 const char *plcg_last_error(void);

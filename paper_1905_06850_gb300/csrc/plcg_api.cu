@@ -506,6 +506,45 @@ BatchCtx g_batch[64];
 
 }  // namespace
 
+// Batched schedule (set by the autotuner through plcg_set_batched_schedule):
+// gang size G, the work threshold (as a multiple of one CTA's fair share)
+// above which a system goes to the gangs, and the largest fraction of the
+// launch's CTAs that may form gangs.
+static int g_batch_G = 8;
+static double g_batch_beta = 1.0;
+static double g_batch_gang_frac = 0.5;
+
+extern "C" plcg_status plcg_set_batched_schedule(int gang_size, double large_work_factor,
+                                                 double max_gang_fraction)
+{
+    if (gang_size == 0) {
+        g_batch_G = 8;
+        g_batch_beta = 1.0;
+        g_batch_gang_frac = 0.5;
+        return PLCG_OK;
+    }
+    if (gang_size < 1 || gang_size > 64 || !(large_work_factor > 0.0) ||
+        !(max_gang_fraction >= 0.0 && max_gang_fraction <= 1.0))
+        return fail(PLCG_ERR_INVALID, "bad batched schedule");
+    g_batch_G = gang_size;
+    g_batch_beta = large_work_factor;
+    g_batch_gang_frac = max_gang_fraction;
+    return PLCG_OK;
+}
+
+// Estimated solve work of a stencil system: n * sqrt(kappa), with kappa from
+// the closed-form extreme eigenvalues of the constant-coefficient Dirichlet
+// stencil (a Kronecker sum: center + 2 off cos(j pi / (n_d + 1)) per axis).
+static double stencil_work(const plcg_matrix *M)
+{
+    const double pi = 3.14159265358979323846;
+    const int dims[3] = {M->st.nx, M->st.ny, M->st.nz};
+    double s = 0.0;
+    for (int d = 0; d < M->st.dim; ++d) s += 2.0 * std::fabs(M->st.off) * std::cos(pi / (dims[d] + 1.0));
+    const double lmin = std::max(M->st.center - s, 1e-300), lmax = M->st.center + s;
+    return (double)M->n * std::sqrt(std::max(1.0, lmax / lmin));
+}
+
 template <typename T>
 static plcg_status run_batched(int count, plcg_matrix *const *A, const double *const *b,
                                double *const *x, const double *lmin, const double *lmax,
@@ -522,10 +561,10 @@ static plcg_status run_batched(int count, plcg_matrix *const *A, const double *c
     BatchCtx &ctx = g_batch[dev];
     std::lock_guard<std::mutex> lock(ctx.mu);
 
-    // host descriptors; work list by decreasing size (longest first)
+    // host descriptors and work estimates
     std::vector<BatchSys> sys(count);
-    std::vector<int> order(count);
-    int64_t nmax = 0;
+    std::vector<double> work(count);
+    double wsum = 0.0;
     for (int i = 0; i < count; ++i) {
         const plcg_matrix *M = A[i];
         BatchSys &y = sys[i];
@@ -551,11 +590,9 @@ static plcg_status run_batched(int count, plcg_matrix *const *A, const double *c
                 chebyshev_shifts(l, lo, hi, y.sigma);
             }
         }
-        order[i] = i;
-        nmax = std::max<int64_t>(nmax, M->n);
+        work[i] = stencil_work(M);
+        wsum += work[i];
     }
-    std::stable_sort(order.begin(), order.end(),
-                     [&](int p, int q) { return A[p]->n > A[q]->n; });
 
     // ring layout (as for a single solve)
     SolveArgs<T> proto;
@@ -587,13 +624,40 @@ static plcg_status run_batched(int count, plcg_matrix *const *A, const double *c
     CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, func, kBlock, 0));
     if (per_sm < 1) return fail(PLCG_ERR_CUDA, "batched kernel cannot be resident");
     const int P = (int)std::max<int64_t>(1, std::min<int64_t>(count, (int64_t)per_sm * A[0]->num_sms));
+
+    // schedule: systems whose work exceeds beta * (fair share of one CTA) go to gangs
+    std::vector<int> order(count);
+    for (int i = 0; i < count; ++i) order[i] = i;
+    std::stable_sort(order.begin(), order.end(), [&](int p, int q) { return work[p] > work[q]; });
+    const int G = std::max(1, std::min(g_batch_G, P));
+    const double share = wsum / P;
+    std::vector<int> large, small;
+    for (int k = 0; k < count; ++k)
+        (G > 1 && work[order[k]] > g_batch_beta * share ? large : small).push_back(order[k]);
+    int ngangs = std::min<int>((int)large.size(), (int)(g_batch_gang_frac * P) / G);
+    if (ngangs == 0) {
+        small.insert(small.begin(), large.begin(), large.end());
+        large.clear();
+    }
+    int64_t nmax_s = 1, nmax_l = 1;
+    for (int i : small) nmax_s = std::max<int64_t>(nmax_s, A[i]->n);
+    for (int i : large) nmax_l = std::max<int64_t>(nmax_l, A[i]->n);
     const size_t ws_stride =
-        align_up(align_up((size_t)(nvec + 2) * nmax * sizeof(T), 256) + (size_t)nmax * sizeof(double), 256);
+        align_up(align_up((size_t)(nvec + 2) * nmax_s * sizeof(T), 256) + (size_t)nmax_s * sizeof(double), 256);
+    const size_t gws_stride = ngangs ?
+        align_up(align_up((size_t)(nvec + 2) * nmax_l * sizeof(T), 256) + (size_t)nmax_l * sizeof(double), 256) : 0;
     size_t off = 0;
     const size_t o_sys = off; off += align_up(sizeof(BatchSys) * count, 256);
-    const size_t o_order = off; off += align_up(sizeof(int) * count, 256);
+    const size_t o_ordl = off; off += align_up(sizeof(int) * std::max<size_t>(1, large.size()), 256);
+    const size_t o_ords = off; off += align_up(sizeof(int) * std::max<size_t>(1, small.size()), 256);
     const size_t o_res = off; off += align_up(sizeof(DevResult) * count, 256);
     const size_t o_ctr = off; off += 256;
+    const size_t o_gbar = off; off += align_up(sizeof(unsigned) * 32 * std::max(1, ngangs), 256);
+    const size_t o_gab = off; off += align_up(sizeof(int) * std::max(1, ngangs), 256);
+    const size_t o_gslot = off; off += align_up(sizeof(int) * std::max(1, ngangs), 256);
+    const size_t o_gpart = off; off += align_up(sizeof(double) * (kMaxL + 1) * G * kMaxDots * std::max(1, ngangs), 256);
+    const size_t o_gnpart = off; off += align_up(sizeof(double) * G * kNormSlots * std::max(1, ngangs), 256);
+    const size_t o_gws = off; off += gws_stride * ngangs;
     const size_t o_ws = off; off += ws_stride * P;
     if (ctx.bytes < off) {
         if (ctx.mem) { cudaStreamSynchronize(stream); cudaFree(ctx.mem); ctx.mem = nullptr; ctx.bytes = 0; }
@@ -608,21 +672,39 @@ static plcg_status run_batched(int count, plcg_matrix *const *A, const double *c
     for (int i = 0; i < count; ++i) sys[i].out = dres + i;
     CUDA_TRY(cudaMemcpyAsync(ctx.mem + o_sys, sys.data(), sizeof(BatchSys) * count,
                              cudaMemcpyHostToDevice, stream));
-    CUDA_TRY(cudaMemcpyAsync(ctx.mem + o_order, order.data(), sizeof(int) * count,
-                             cudaMemcpyHostToDevice, stream));
+    if (!large.empty())
+        CUDA_TRY(cudaMemcpyAsync(ctx.mem + o_ordl, large.data(), sizeof(int) * large.size(),
+                                 cudaMemcpyHostToDevice, stream));
+    if (!small.empty())
+        CUDA_TRY(cudaMemcpyAsync(ctx.mem + o_ords, small.data(), sizeof(int) * small.size(),
+                                 cudaMemcpyHostToDevice, stream));
     CUDA_TRY(cudaMemsetAsync(ctx.mem + o_res, 0, sizeof(DevResult) * count, stream));
     CUDA_TRY(cudaMemsetAsync(ctx.mem + o_ctr, 0, 256, stream));
+    CUDA_TRY(cudaMemsetAsync(ctx.mem + o_gbar, 0, o_gpart - o_gbar, stream));   // barriers, aborts, slots
     BatchArgs<T> ba;
-    ba.count = count;
+    std::memset(&ba, 0, sizeof(ba));
     ba.sys = reinterpret_cast<const BatchSys *>(ctx.mem + o_sys);
-    ba.order = reinterpret_cast<const int *>(ctx.mem + o_order);
-    ba.counter = reinterpret_cast<int *>(ctx.mem + o_ctr);
+    ba.nlarge = ngangs ? (int)large.size() : 0;
+    ba.nsmall = (int)small.size();
+    ba.order_large = reinterpret_cast<const int *>(ctx.mem + o_ordl);
+    ba.order_small = reinterpret_cast<const int *>(ctx.mem + o_ords);
+    ba.ctr_large = reinterpret_cast<int *>(ctx.mem + o_ctr);
+    ba.ctr_small = reinterpret_cast<int *>(ctx.mem + o_ctr + 128);
+    ba.ngangs = ngangs;
+    ba.G = G;
+    ba.gbar = reinterpret_cast<unsigned *>(ctx.mem + o_gbar);
+    ba.gabort = reinterpret_cast<int *>(ctx.mem + o_gab);
+    ba.gslot = reinterpret_cast<int *>(ctx.mem + o_gslot);
+    ba.gpart = reinterpret_cast<double *>(ctx.mem + o_gpart);
+    ba.gnpart = reinterpret_cast<double *>(ctx.mem + o_gnpart);
+    ba.gws = ctx.mem + o_gws;
+    ba.gws_stride = gws_stride;
     ba.ws = ctx.mem + o_ws;
     ba.ws_stride = ws_stride;
     ba.proto = proto;
     void *args[] = {&ba};
     CUDA_TRY(cudaEventRecord(ctx.ev0, stream));
-    CUDA_TRY(cudaLaunchKernel(func, dim3(P), dim3(kBlock), args, 0, stream));
+    CUDA_TRY(cudaLaunchCooperativeKernel(func, dim3(P), dim3(kBlock), args, 0, stream));
     CUDA_TRY(cudaEventRecord(ctx.ev1, stream));
     std::vector<DevResult> hres(count);
     CUDA_TRY(cudaMemcpyAsync(hres.data(), dres, sizeof(DevResult) * count, cudaMemcpyDeviceToHost, stream));

@@ -112,11 +112,21 @@ struct BatchSys {
 // the ring layout; the per-system fields are filled in on the device.
 template <typename T>
 struct BatchArgs {
-    int count;
     const BatchSys *sys;
-    const int *order;         // systems by decreasing size
-    int *counter;             // next position in order
-    char *ws;                 // per-CTA workspaces
+    // "large" list: solved by gangs of G CTAs; "small" list: one CTA each
+    int nlarge, nsmall;
+    const int *order_large;   // system indices, largest estimated work first
+    const int *order_small;
+    int *ctr_large, *ctr_small;   // next positions in the lists
+    int ngangs, G;
+    unsigned *gbar;           // [ngangs][32] gang barrier counters (own cache lines)
+    int *gabort;              // [ngangs]
+    int *gslot;               // [ngangs] system a gang's leader took
+    double *gpart;            // [ngangs][kMaxL + 1][G][kMaxDots]
+    double *gnpart;           // [ngangs][G][kNormSlots]
+    char *gws;                // per-gang workspaces
+    size_t gws_stride;
+    char *ws;                 // per-CTA workspaces (one-CTA path)
     size_t ws_stride;
     SolveArgs<T> proto;
 };

@@ -50,14 +50,14 @@ __device__ __forceinline__ int ld_volatile(const int *p) { return *(volatile con
 // bound ran out (the CTA then sets the abort flag) or another CTA aborted;
 // the caller must then leave the kernel.  force_timeout adds one phantom
 // arrival to the target so that the wait runs out (test hook).
-__device__ __forceinline__ bool grid_barrier(unsigned *bar, unsigned &epoch,
-                                             unsigned long long limit, int force,
-                                             int *abort_flag, int *s_ok)
+__device__ __forceinline__ bool group_barrier(unsigned *bar, unsigned &epoch, unsigned members,
+                                              unsigned long long limit, int force,
+                                              int *abort_flag, int *s_ok)
 {
     __syncthreads();
     if (threadIdx.x == 0) {
         epoch += 1u;
-        const unsigned target = epoch * gridDim.x + (force ? 1u : 0u);
+        const unsigned target = epoch * members + (force ? 1u : 0u);
         __threadfence();
         red_release_add_u32(bar, 1u);
         int ok = 1;
@@ -73,6 +73,13 @@ __device__ __forceinline__ bool grid_barrier(unsigned *bar, unsigned &epoch,
     }
     __syncthreads();
     return *s_ok != 0;
+}
+
+__device__ __forceinline__ bool grid_barrier(unsigned *bar, unsigned &epoch,
+                                             unsigned long long limit, int force,
+                                             int *abort_flag, int *s_ok)
+{
+    return group_barrier(bar, epoch, gridDim.x, limit, force, abort_flag, s_ok);
 }
 
 // ------------------------------------------------------------------------
@@ -98,19 +105,26 @@ __device__ __forceinline__ void block_sum(double (&v)[ND], double *s_red, double
     __syncthreads();
 }
 
-// Sum over all CTAs of part[c * stride + q], q < ND; result in s_out[q].
+// Sum over `count` CTAs of part[c * stride + q], q < ND; result in s_out[q].
 template <int ND>
-__device__ __forceinline__ void grid_partials_sum(const double *part, int stride, double *s_red,
-                                                  double *s_out)
+__device__ __forceinline__ void partials_sum(const double *part, int count, int stride,
+                                             double *s_red, double *s_out)
 {
     double v[ND];
 #pragma unroll
     for (int q = 0; q < ND; ++q) v[q] = 0.0;
-    for (int c = threadIdx.x; c < (int)gridDim.x; c += kBlock) {
+    for (int c = threadIdx.x; c < count; c += kBlock) {
 #pragma unroll
         for (int q = 0; q < ND; ++q) v[q] += __ldcg(part + (size_t)c * stride + q);
     }
     block_sum<ND>(v, s_red, s_out);
+}
+
+template <int ND>
+__device__ __forceinline__ void grid_partials_sum(const double *part, int stride, double *s_red,
+                                                  double *s_out)
+{
+    partials_sum<ND>(part, (int)gridDim.x, stride, s_red, s_out);
 }
 
 // ------------------------------------------------------------------------
@@ -422,6 +436,48 @@ struct BlockGroup {
     {
         if (threadIdx.x < 2) s.out[threadIdx.x] = s.bnorm[threadIdx.x];
         __syncthreads();
+    }
+};
+
+// A gang: G CTAs of one cooperative launch solving one system together
+// (batched solves of large systems); bounded barrier and FP64 partials of its
+// own, so gangs proceed independently of each other.
+template <typename T>
+struct GangGroup {
+    int rank, G;
+    unsigned *bar;
+    unsigned epoch;
+    double *part;             // [(l+1) slots][G][kMaxDots]
+    double *npart;            // [G][kNormSlots]
+    int *abort_flag;
+    unsigned long long limit;
+    __device__ __forceinline__ int64_t unit0() const { return rank; }
+    __device__ __forceinline__ int64_t ustep() const { return G; }
+    __device__ __forceinline__ bool leader() const { return rank == 0; }
+    __device__ __forceinline__ bool sync(const SolveArgs<T> &, Smem<T> &s)
+    {
+        return group_barrier(bar, epoch, (unsigned)G, limit, 0, abort_flag, &s.ok);
+    }
+    __device__ __forceinline__ void put_dots(const SolveArgs<T> &, Smem<T> &s, int slot, int nd)
+    {
+        if ((int)threadIdx.x < nd)
+            part[((size_t)slot * G + rank) * kMaxDots + threadIdx.x] = s.out[threadIdx.x];
+    }
+    template <int ND>
+    __device__ __forceinline__ void get_dots(const SolveArgs<T> &, Smem<T> &s, int slot, double *dst)
+    {
+        partials_sum<ND>(part + (size_t)slot * G * kMaxDots, G, kMaxDots, s.red, dst);
+    }
+    __device__ __forceinline__ void put_norms(const SolveArgs<T> &, Smem<T> &s)
+    {
+        if (threadIdx.x == 0) {
+            npart[(size_t)rank * kNormSlots + 0] = s.out[0];
+            npart[(size_t)rank * kNormSlots + 1] = s.out[1];
+        }
+    }
+    __device__ __forceinline__ void get_norms(const SolveArgs<T> &, Smem<T> &s)
+    {
+        partials_sum<2>(npart, G, kNormSlots, s.red, s.out);
     }
 };
 
@@ -1236,54 +1292,95 @@ __global__ void __launch_bounds__(kBlock, 3) cg_kernel(SolveArgs<T> a)
 }
 
 // ------------------------------------------------------------------------
-// Batched kernel: many independent stencil systems in one persistent launch.
-// Each CTA takes the next system of a work list (sorted by decreasing size,
-// so the longest solves start first) from an atomic counter, solves it alone
-// with __syncthreads as its barrier, writes that system's result and takes
-// the next; converged systems retire and free their CTA at once.
+// Batched kernel: many independent stencil systems in one persistent
+// (cooperative) launch.  The first ngangs * G CTAs form gangs of G CTAs that
+// take the systems of the "large" list (largest estimated work first) and
+// solve each one together; every CTA -- gang members once that list is
+// exhausted -- then takes systems of the "small" list one per CTA, with
+// __syncthreads as its barrier.  Converged systems retire at once and free
+// their CTA or gang for the next system.
 // ------------------------------------------------------------------------
-// Row groups per thread in the batched kernel, where one CTA streams a whole
+// Row groups per thread in the one-CTA path, where a CTA streams a whole
 // system and needs several loads in flight per thread (fewer for larger l,
 // whose sweep holds more vectors in registers).
 template <int L> constexpr int kBatchRPT = (L == 1) ? 4 : 2;
+
+template <typename T>
+__device__ __forceinline__ void batch_args(const BatchArgs<T> &ba, const BatchSys &sy, T *ws,
+                                           SolveArgs<T> &a)
+{
+    a = ba.proto;
+    a.n = (int64_t)sy.nx * sy.ny * sy.nz;
+    a.st.dim = sy.dim;
+    a.st.nx = sy.nx;
+    a.st.ny = sy.ny;
+    a.st.nz = sy.nz;
+    a.st.dnx = sy.dnx;
+    a.st.dny = sy.dny;
+    a.st.center = sy.center;
+    a.st.off = sy.off;
+    a.b = sy.b;
+    a.x = sy.x;
+    a.out = sy.out;
+    for (int j = 0; j < kMaxL; ++j) a.sigma[j] = sy.sigma[j];
+    // workspace: ring vectors, p, rc (type T), then r (FP64)
+    const int64_t nv = a.n;
+    a.zring = ws;
+    int nvec = 0;
+    for (int j = 0; j <= kMaxL; ++j) nvec += (j <= a.l) ? a.depth[j] : 0;
+    if (a.method == 1) nvec = 3;
+    a.p = ws + (size_t)nvec * nv;
+    a.rc = a.p + nv;
+    a.r = reinterpret_cast<double *>(reinterpret_cast<char *>(ws) +
+                                     ((((size_t)(nvec + 2) * nv * sizeof(T)) + 255) / 256) * 256);
+}
 
 template <typename T, int L>
 __global__ void __launch_bounds__(kBlock, 2) batched_kernel(BatchArgs<T> ba)
 {
     __shared__ Smem<T> s;
     __shared__ int s_next;
-    T *ws = reinterpret_cast<T *>(ba.ws + (size_t)blockIdx.x * ba.ws_stride);
+    const int b = blockIdx.x;
+    if (b < ba.ngangs * ba.G) {
+        const int gang = b / ba.G;
+        GangGroup<T> grp;
+        grp.rank = b % ba.G;
+        grp.G = ba.G;
+        grp.bar = ba.gbar + (size_t)gang * 32;
+        grp.epoch = 0;
+        grp.part = ba.gpart + (size_t)gang * (kMaxL + 1) * ba.G * kMaxDots;
+        grp.npart = ba.gnpart + (size_t)gang * ba.G * kNormSlots;
+        grp.abort_flag = ba.gabort + gang;
+        grp.limit = ba.proto.poll_limit;
+        T *ws = reinterpret_cast<T *>(ba.gws + (size_t)gang * ba.gws_stride);
+        SolveArgs<T> a;
+        for (;;) {
+            if (grp.rank == 0 && threadIdx.x == 0) {
+                const int k = atomicAdd(ba.ctr_large, 1);
+                ba.gslot[gang] = (k < ba.nlarge) ? ba.order_large[k] : -1;
+            }
+            if (!grp.sync(a, s)) return;   // a broken gang barrier ends this gang
+            if (threadIdx.x == 0) s_next = ld_volatile(ba.gslot + gang);
+            __syncthreads();
+            const int sysi = s_next;
+            if (sysi < 0) break;
+            batch_args(ba, ba.sys[sysi], ws, a);
+            if (a.method == 1) cg_body<T, 1, kOpStencil>(a, s, grp);
+            else plcg_body<T, L, 1, kOpStencil>(a, s, grp);
+            if (ld_volatile(grp.abort_flag)) return;
+            // every member has read gslot before the leader overwrites it: they
+            // all passed the solve's own barriers since reading it
+        }
+    }
+    T *ws = reinterpret_cast<T *>(ba.ws + (size_t)b * ba.ws_stride);
     for (;;) {
-        if (threadIdx.x == 0) s_next = atomicAdd(ba.counter, 1);
+        if (threadIdx.x == 0) s_next = atomicAdd(ba.ctr_small, 1);
         __syncthreads();
         const int k = s_next;
         __syncthreads();
-        if (k >= ba.count) return;
-        const BatchSys &sy = ba.sys[ba.order[k]];
-        SolveArgs<T> a = ba.proto;
-        a.n = (int64_t)sy.nx * sy.ny * sy.nz;
-        a.st.dim = sy.dim;
-        a.st.nx = sy.nx;
-        a.st.ny = sy.ny;
-        a.st.nz = sy.nz;
-        a.st.dnx = sy.dnx;
-        a.st.dny = sy.dny;
-        a.st.center = sy.center;
-        a.st.off = sy.off;
-        a.b = sy.b;
-        a.x = sy.x;
-        a.out = sy.out;
-        for (int j = 0; j < kMaxL; ++j) a.sigma[j] = sy.sigma[j];
-        // this CTA's workspace: ring vectors, p, rc (type T), then r (FP64)
-        const int64_t nv = a.n;
-        a.zring = ws;
-        int nvec = 0;
-        for (int j = 0; j <= kMaxL; ++j) nvec += (j <= a.l) ? a.depth[j] : 0;
-        if (a.method == 1) nvec = 3;
-        a.p = ws + (size_t)nvec * nv;
-        a.rc = a.p + nv;
-        a.r = reinterpret_cast<double *>(reinterpret_cast<char *>(ws) +
-                                         ((((size_t)(nvec + 2) * nv * sizeof(T)) + 255) / 256) * 256);
+        if (k >= ba.nsmall) return;
+        SolveArgs<T> a;
+        batch_args(ba, ba.sys[ba.order_small[k]], ws, a);
         BlockGroup<T> grp;
         if (a.method == 1) cg_body<T, 1, kOpStencil, BlockGroup<T>, 4>(a, s, grp);
         else plcg_body<T, L, 1, kOpStencil, BlockGroup<T>, kBatchRPT<L>>(a, s, grp);

@@ -80,6 +80,7 @@ SIGNATURES = {
     "plcg_poll": (C.c_int, [_VP, C.c_uint64, C.POINTER(plcg_result)]),
     "plcg_wait": (C.c_int, [_VP, C.c_uint64, C.POINTER(plcg_result)]),
     "plcg_server_destroy": (None, [_VP]),
+    "plcg_set_batched_schedule": (C.c_int, [C.c_int, C.c_double, C.c_double]),
     "plcg_last_error": (C.c_char_p, []),
     "plcg_version": (C.c_char_p, []),
     "plcg_debug_set_poll_limit": (None, [C.c_uint64]),

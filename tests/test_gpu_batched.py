@@ -121,3 +121,31 @@ def test_batched_edge_cases(P):
     st, _ = P.solve_batched([csr], [b], [x], check=False)
     assert st == P.PLCG_ERR_UNIMPL
     csr.close()
+
+
+@pytest.mark.parametrize("schedule", [(4, 0.01, 1.0), (8, 1.0, 0.5), (1, 1.0, 0.0)],
+                         ids=["all-gangs", "default", "no-gangs"])
+def test_batched_gang_schedules(P, schedule):
+    """The gang path (several thread blocks per system, own barrier and
+    partials) and the one-block path both match the oracle."""
+    from paper_1905_06850_gb300 import autotune
+    systems = make_batch(count=30, seed=17)
+    # a few large systems so that gangs have work under the default schedule
+    for i, s_ in enumerate((180, 200, 160)):
+        op = W.stencil2d(s_, s_, shift=0.002 * (i + 1))
+        systems.append((op, np.random.default_rng(100 + i).standard_normal(s_ * s_),
+                        (op["center"] - 4.0, op["center"] + 4.0)))
+    try:
+        autotune.set_schedule(*schedule)
+        for prec, l in (("fp64", 1), ("fp32", 2)):
+            st, res, xs = run(P, systems, prec, l=l, rtol=1e-8)
+            assert st == P.PLCG_OK, P.last_error()
+            for (op, b, iv), r, x in zip(systems, res, xs):
+                oop = W.fp32_rounded(op) if prec == "fp32" else op
+                ref = O.plcg(oop, b, l=l, sigma=O.chebyshev_shifts(l, *iv), rtol=1e-8, dots_2l1=False)
+                assert r.ok and r.true_relres < 1e-8
+                assert rel(x, ref.x) <= (1e-10 if prec == "fp64" else 1e-5), (op["nx"], schedule)
+        st, res, xs = run(P, systems, "fp32", method="cg", rtol=1e-8)
+        assert st == P.PLCG_OK and all(r.true_relres < 1e-8 for r in res)
+    finally:
+        autotune.set_schedule(0)
