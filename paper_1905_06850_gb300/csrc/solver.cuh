@@ -19,6 +19,8 @@
 #include <float.h>
 #include <stdint.h>
 
+#include <type_traits>
+
 #include "plcg_internal.h"
 
 namespace plcg {
@@ -340,6 +342,36 @@ struct Coef {
     T *nw[kMaxL];
     T *cpy[kMaxL];
     const T *v0;              // final sweep: z^(0)_m
+};
+
+// The fields of Coef the iteration sweep reads, as a register copy for the
+// one-CTA path (see the sweep); the rarely used cpy and dptr stay in shared
+// memory.
+template <typename T, int L>
+struct SweepCoef {
+    int mode, k6, prev0, ncopy;
+    T sig, invd, al, bm, zx, pv, pp;
+    T ak[L];
+    int dsrc[2 * L + 1];
+    const T *zl_cur, *zl_prev;
+    T *zl_new;
+    const T *cur[L], *prv[L];
+    T *nw[L];
+    __device__ __forceinline__ SweepCoef(const Coef<T> &c)
+        : mode(c.mode), k6(c.k6), prev0(c.prev0), ncopy(c.ncopy), sig(c.sig), invd(c.invd),
+          al(c.al), bm(c.bm), zx(c.zx), pv(c.pv), pp(c.pp), zl_cur(c.zl_cur), zl_prev(c.zl_prev),
+          zl_new(c.zl_new)
+    {
+#pragma unroll
+        for (int k = 0; k < L; ++k) {
+            ak[k] = c.ak[k];
+            cur[k] = c.cur[k];
+            prv[k] = c.prv[k];
+            nw[k] = c.nw[k];
+        }
+#pragma unroll
+        for (int q = 0; q <= 2 * L; ++q) dsrc[q] = c.dsrc[q];
+    }
 };
 
 template <typename T>
@@ -907,38 +939,19 @@ __device__ void plcg_body(const SolveArgs<T> &a, Smem<T> &s, Grp &grp)
             // issues every load of all of them before any store (the vectors are
             // distinct, but the compiler cannot know), so its HBM/L2 reads
             // overlap in flight.
-            // Copy what the sweep reads into locals: the coefficients live in
-            // shared memory and the vector stores go through generic pointers
-            // that the compiler cannot prove disjoint from it, so reading s.cf
-            // inside the loop would re-load every field after every store.
-            const StencilDesc st = a.st;
-            const CsrDesc csr = a.csr;
-            const T *const zl_cur = cf.zl_cur, *const zl_prev = cf.zl_prev;
-            T *const zl_new = cf.zl_new;
+            // The coefficients live in shared memory and the vector stores go
+            // through generic pointers the compiler cannot prove disjoint from
+            // it, so every field read after a store is re-loaded.  The one-CTA
+            // path (RPT > 1, few warps) copies them into registers; the grid
+            // path keeps them in shared memory, where re-loads cost less than
+            // the registers (and occupancy) a copy would take.
+            using CoefRef = std::conditional_t<(RPT > 1), SweepCoef<T, L>, const Coef<T> &>;
+            using StRef = std::conditional_t<(RPT > 1), StencilDesc, const StencilDesc &>;
+            CoefRef C = s.cf;
+            StRef st = a.st;
+            const CsrDesc &csr = a.csr;
             T *const pvec = a.p;
-            const T *curp[L], *prvp[L];
-            T *nwp[L];
-            T ak[L];
-#pragma unroll
-            for (int k = 0; k < L; ++k) {
-                curp[k] = cf.cur[k];
-                prvp[k] = cf.prv[k];
-                nwp[k] = cf.nw[k];
-                ak[k] = cf.ak[k];
-            }
-            int dsrc[2 * L + 1];
-            const T *dptr[2 * L + 1];
-#pragma unroll
-            for (int q = 0; q <= 2 * L; ++q) {
-                dsrc[q] = cf.dsrc[q];
-                dptr[q] = cf.dptr[q];
-            }
-            const T c_sig = cf.sig, c_invd = cf.invd, c_al = cf.al, c_bm = cf.bm;
-            const T c_zx = cf.zx, c_pv = cf.pv, c_pp = cf.pp;
-            const int c_k6 = cf.k6, c_prev0 = cf.prev0, c_ncopy = cf.ncopy;
-            const bool rec = cf.mode == 1;
-            T *cpyp[kMaxL];
-            for (int k = 0; k < c_ncopy; ++k) cpyp[k] = cf.cpy[k];
+            const bool rec = C.mode == 1;
             DotAcc<T, VEC> dac[2 * L + 1];
             int since_flush = 0;
             for (int64_t u = grp.unit0(); u < nunits_s; u += grp.ustep()) {
@@ -957,22 +970,22 @@ __device__ void plcg_body(const SolveArgs<T> &a, Smem<T> &s, Grp &grp)
 #pragma unroll
                     for (int v = 0; v < VEC; ++v) zp[r][v] = T(0);
                     if (!ok[r]) continue;
-                    op_parts<T, T, VEC, OP>(st, csr, Ld1<T>{zl_cur}, g0[r], c[r], nb[r]);   // K1 operands
+                    op_parts<T, T, VEC, OP>(st, csr, Ld1<T>{C.zl_cur}, g0[r], c[r], nb[r]);   // K1 operands
                     if (rec) {
-                        vld<T, VEC>(zl_prev + g0[r], zp[r]);
+                        vld<T, VEC>(C.zl_prev + g0[r], zp[r]);
 #pragma unroll
-                        for (int k = 0; k < L; ++k) vld<T, VEC>(curp[k] + g0[r], cur[r][k]);
+                        for (int k = 0; k < L; ++k) vld<T, VEC>(C.cur[k] + g0[r], cur[r][k]);
 #pragma unroll
                         for (int k = 0; k < L; ++k) {
-                            if (k > 0 || c_prev0) {
-                                vld<T, VEC>(prvp[k] + g0[r], pk[r][k]);
+                            if (k > 0 || C.prev0) {
+                                vld<T, VEC>(C.prv[k] + g0[r], pk[r][k]);
                             } else {
 #pragma unroll
                                 for (int v = 0; v < VEC; ++v) pk[r][k][v] = T(0);
                             }
                         }
                     }
-                    if (c_k6 == 2) {
+                    if (C.k6 == 2) {
                         vld<T, VEC>(pvec + g0[r], pv[r]);
                         vld<T, VEC>(xi + g0[r], xv[r]);
                     }
@@ -985,51 +998,51 @@ __device__ void plcg_body(const SolveArgs<T> &a, Smem<T> &s, Grp &grp)
                     if (!rec) {
                         // u_{i+1} = A z^(l)_i - sigma_i z^(l)_i
 #pragma unroll
-                        for (int v = 0; v < VEC; ++v) un[v] = fma(kc - c_sig, c[r][v], kn * nb[r][v]);
+                        for (int v = 0; v < VEC; ++v) un[v] = fma(kc - C.sig, c[r][v], kn * nb[r][v]);
                     } else {
                         // K4: z^(l)_{i+1} = (A z^(l)_i - gamma z^(l)_i - delta' z^(l)_{i-1}) / delta
                         // and z^(k)_{i-l+k+1}, k < l (Alg. 1 lines 19-21)
-                        const T uc = fma(kc, c_invd, c_al), un_nb = kn * c_invd;
+                        const T uc = fma(kc, C.invd, C.al), un_nb = kn * C.invd;
 #pragma unroll
                         for (int v = 0; v < VEC; ++v)
-                            un[v] = fma(uc, c[r][v], fma(un_nb, nb[r][v], c_bm * zp[r][v]));
+                            un[v] = fma(uc, c[r][v], fma(un_nb, nb[r][v], C.bm * zp[r][v]));
 #pragma unroll
                         for (int k = 0; k < L; ++k)
 #pragma unroll
                             for (int v = 0; v < VEC; ++v) {
                                 const T up = (k == L - 1) ? c[r][v] : cur[r][k + 1][v];
-                                nw[k][v] = fma(up, c_invd, fma(ak[k], cur[r][k][v], c_bm * pk[r][k][v]));
+                                nw[k][v] = fma(up, C.invd, fma(C.ak[k], cur[r][k][v], C.bm * pk[r][k][v]));
                             }
                     }
                     // K6: p and the iterate (Alg. 1 lines 26-31)
-                    if (c_k6 == 1) {
+                    if (C.k6 == 1) {
 #pragma unroll
-                        for (int v = 0; v < VEC; ++v) pv[r][v] = c_pv * cur[r][0][v];
-                    } else if (c_k6 == 2) {
+                        for (int v = 0; v < VEC; ++v) pv[r][v] = C.pv * cur[r][0][v];
+                    } else if (C.k6 == 2) {
 #pragma unroll
                         for (int v = 0; v < VEC; ++v) {
-                            xv[r][v] = fma(c_zx, pv[r][v], xv[r][v]);
-                            pv[r][v] = fma(c_pv, cur[r][0][v], c_pp * pv[r][v]);
+                            xv[r][v] = fma(C.zx, pv[r][v], xv[r][v]);
+                            pv[r][v] = fma(C.pv, cur[r][0][v], C.pp * pv[r][v]);
                         }
                     }
                     // -- stores
-                    vst<T, VEC>(zl_new + g0[r], un);
+                    vst<T, VEC>(C.zl_new + g0[r], un);
                     if (!rec) {
-                        for (int k = 0; k < c_ncopy; ++k) vst<T, VEC>(cpyp[k] + g0[r], un);
+                        for (int k = 0; k < C.ncopy; ++k) vst<T, VEC>(s.cf.cpy[k] + g0[r], un);
                     } else {
 #pragma unroll
-                        for (int k = 0; k < L; ++k) vst<T, VEC>(nwp[k] + g0[r], nw[k]);
+                        for (int k = 0; k < L; ++k) vst<T, VEC>(C.nw[k] + g0[r], nw[k]);
                     }
-                    if (c_k6 >= 1) vst<T, VEC>(pvec + g0[r], pv[r]);
-                    if (c_k6 == 2) vst<T, VEC>(xi + g0[r], xv[r]);
+                    if (C.k6 >= 1) vst<T, VEC>(pvec + g0[r], pv[r]);
+                    if (C.k6 == 2) vst<T, VEC>(xi + g0[r], xv[r]);
                     // -- K5: partial dot products with u_{i+1} = z^(l)_{i+1}
 #pragma unroll
                     for (int q = 0; q <= 2 * L; ++q) {
-                        const int src = dsrc[q];
+                        const int src = C.dsrc[q];
                         if (src == 0) continue;
                         T o[VEC];
                         if (src == 1) {
-                            vld<T, VEC>(dptr[q] + g0[r], o);
+                            vld<T, VEC>(s.cf.dptr[q] + g0[r], o);
                         } else {
 #pragma unroll
                             for (int v = 0; v < VEC; ++v)
@@ -1085,8 +1098,8 @@ __device__ void cg_body(const SolveArgs<T> &a, Smem<T> &s, Grp &grp)
     const T cC = (T)a.st.center, cO = (T)a.st.off;
     T *pr[2] = {a.zring, a.zring + n};
     T *q = a.p;
-    const StencilDesc st = a.st;
-    const CsrDesc csr = a.csr;
+    std::conditional_t<(RPT > 1), StencilDesc, const StencilDesc &> st = a.st;
+    const CsrDesc &csr = a.csr;
     T *rc = kF32 ? a.rc : reinterpret_cast<T *>(a.r);
     T *xi = kF32 ? a.zring + 2 * n : reinterpret_cast<T *>(a.x);
 
