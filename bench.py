@@ -118,9 +118,9 @@ def kernel_source_hash() -> str:
     return h.hexdigest()[:16]
 
 
-def profiled_traffic(name: str):
-    """DRAM bytes per point-iteration from a committed ncu summary, when its
-    kernel-source hash matches the current sources (else None)."""
+def profiled_record(name: str):
+    """A committed ncu summary (profiles/*.json), or None when it is missing
+    or its kernel-source hash no longer matches the current sources."""
     path = os.path.join(ROOT, "profiles", name)
     try:
         with open(path) as f:
@@ -129,7 +129,7 @@ def profiled_traffic(name: str):
         return None
     if d.get("source_hash") != kernel_source_hash():
         return None
-    return d.get("dram_bytes_per_point_iter")
+    return d
 
 
 def passes_per_iter(l: int, method: str) -> int:
@@ -142,9 +142,11 @@ def passes_per_iter(l: int, method: str) -> int:
 
 
 def dp_flops_per_point(l: int) -> int:
-    """FP64 flops per point per p(l)-CG iteration on the 7-point stencil
-    (FMA = 2): SpMV 8, K4 5 per basis, K5 2 per dot (l+1 dots), K6 5."""
-    return 8 + 5 * (l + 1) + 2 * (l + 1) + 5
+    """Algorithmic FP64 flops per row per p(l)-CG iteration on the 7-point
+    constant-coefficient stencil: the SpMV (5 neighbour adds, center*c +
+    off*sum: 8 flops) plus the (6l + 10) flops of AXPYs and dot products
+    that Table 1 of the paper counts."""
+    return 8 + 6 * l + 10
 
 
 # ---------------------------------------------------------------- our arm
@@ -219,14 +221,20 @@ def run_ours(args):
     dp_flops = statistics.mean(iters) * dp_flops_per_point(L_HEAD) * n
     achieved_dp_tf = dp_flops / statistics.mean(kern_s) / 1e12
     dp_peak_tf = 1.25   # nominal FP64 rate of GB300 (recipe table); see the design doc
-    traffic_ppi = profiled_traffic("plcg_3d_fp64_l1.json")
-    traffic = None if traffic_ppi is None else traffic_ppi * n * statistics.mean(iters)
+    # measured DRAM traffic per launch: bytes per row per sweep of an ncu
+    # capture (smaller grid, same kernel) x rows x sweeps (iterations + 2
+    # residual sweeps) of this solve
+    rec = profiled_record("plcg_3d_fp64_l1.json") if (args.prec, args.l) == ("fp64", 1) else None
+    traffic = None if rec is None else round(rec["dram_bytes_per_point_iter"] * n * (statistics.mean(iters) + 2))
     hbm_frac = achieved_gbs / hbm_peak
     dp_frac = achieved_dp_tf / dp_peak_tf
     if dp_frac >= hbm_frac:
         roofline = {"bound": "alu", "achieved": round(achieved_dp_tf, 4), "peak": dp_peak_tf,
                     "unit": "TFLOP/s", "frac": round(dp_frac, 4), "traffic": traffic,
-                    "peak_source": "nominal FP64 1.25 TFLOP/s (GB300 FP64 units x clock)",
+                    "peak_source": "nominal FP64 1.25 TFLOP/s (GB300 FP64 units x clock; a DFMA "
+                                   "microbenchmark reaches 1.01)",
+                    "flops_per_row_iter": dp_flops_per_point(args.l),
+                    "ncu_fp64_pipe_pct": None if rec is None else rec.get("fp64_pipe_pct"),
                     "hbm": {"achieved_gbs": round(achieved_gbs, 1), "peak_gbs": hbm_peak,
                             "frac": round(hbm_frac, 4), "peak_source": hbm_src}}
     else:
@@ -263,7 +271,10 @@ def run_ours(args):
             r = A.solve(b, xf, l=l, interval=interval, rtol=RTOL, prec="fp32")
             err = float(np.linalg.norm(b_np - W.rhs(op, xf.cpu().numpy())) / np.linalg.norm(b_np))
             byt = r.iters * passes_per_iter(l, "plcg") * 4 * n
+            rec32 = profiled_record("plcg_3d_fp32_l1.json") if l == 1 else None
             mp[f"l{l}"] = {"iters": r.iters, "refinements": r.refinements,
+                           "traffic": None if rec32 is None else
+                           round(rec32["dram_bytes_per_point_iter"] * n * (r.iters + 2 * (r.refinements + 1))),
                            "time_to_rtol_s": round(r.seconds, 5),
                            "iters_per_s": round(r.iters / r.seconds, 1),
                            "hbm_gbs": round(byt / r.seconds / 1e9, 1),
