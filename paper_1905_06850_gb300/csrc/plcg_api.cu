@@ -351,6 +351,9 @@ static plcg_status build_solve(const plcg_matrix *A, const double *b, double *x,
     a.fp32 = f32 ? 1 : 0;
     a.poll_limit = poll_limit();
     a.force_timeout = g_force_timeout;
+    // l >= 2: compute each iteration's scalars during the previous sweep where
+    // that latency is a visible share of an iteration (smaller systems)
+    a.lookahead = (!cg && l >= 2 && n < (int64_t(1) << 22)) ? 1 : 0;
     return PLCG_OK;
 }
 
@@ -619,26 +622,30 @@ static plcg_status run_batched(int count, plcg_matrix *const *A, const double *c
     proto.inner_floor = prm->inner_rtol_floor;
     proto.fp32 = f32 ? 1 : 0;
     proto.poll_limit = poll_limit();
+    proto.lookahead = (!cg && l >= 2) ? 1 : 0;
 
     int per_sm = 0;
     CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, func, kBlock, 0));
     if (per_sm < 1) return fail(PLCG_ERR_CUDA, "batched kernel cannot be resident");
-    const int P = (int)std::max<int64_t>(1, std::min<int64_t>(count, (int64_t)per_sm * A[0]->num_sms));
+    const int Pmax = per_sm * A[0]->num_sms;
 
-    // schedule: systems whose work exceeds beta * (fair share of one CTA) go to gangs
+    // schedule: systems whose work exceeds beta * (fair share of one CTA of a
+    // full launch) go to gangs; the launch then has the gangs' CTAs plus at
+    // most one CTA per remaining system
     std::vector<int> order(count);
     for (int i = 0; i < count; ++i) order[i] = i;
     std::stable_sort(order.begin(), order.end(), [&](int p, int q) { return work[p] > work[q]; });
-    const int G = std::max(1, std::min(g_batch_G, P));
-    const double share = wsum / P;
+    const int G = std::max(1, std::min(g_batch_G, Pmax));
+    const double share = wsum / std::min<int64_t>((int64_t)count * G, Pmax);
     std::vector<int> large, small;
     for (int k = 0; k < count; ++k)
         (G > 1 && work[order[k]] > g_batch_beta * share ? large : small).push_back(order[k]);
-    int ngangs = std::min<int>((int)large.size(), (int)(g_batch_gang_frac * P) / G);
+    int ngangs = std::min<int>((int)large.size(), (int)(g_batch_gang_frac * Pmax) / G);
     if (ngangs == 0) {
         small.insert(small.begin(), large.begin(), large.end());
         large.clear();
     }
+    const int P = (int)std::max<int64_t>(1, std::min<int64_t>(Pmax, (int64_t)ngangs * G + (int64_t)small.size()));
     int64_t nmax_s = 1, nmax_l = 1;
     for (int i : small) nmax_s = std::max<int64_t>(nmax_s, A[i]->n);
     for (int i : large) nmax_l = std::max<int64_t>(nmax_l, A[i]->n);

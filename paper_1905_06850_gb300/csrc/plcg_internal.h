@@ -93,6 +93,7 @@ struct SolveArgs {
     int fp32;                 // 1: T = float with FP64 outer refinement
     unsigned long long poll_limit;
     int force_timeout;
+    int lookahead;            // l >= 2: compute the next iteration's scalars during the sweep
 };
 
 // One system of a batched solve (stencil operators only).

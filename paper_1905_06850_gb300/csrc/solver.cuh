@@ -56,21 +56,24 @@ __device__ __forceinline__ bool group_barrier(unsigned *bar, unsigned &epoch, un
                                               unsigned long long limit, int force,
                                               int *abort_flag, int *s_ok)
 {
+    // bar.sync orders the CTA's writes before thread 0's release-add (release
+    // is cumulative over what happened before it); the acquire-load that sees
+    // the last arrival orders the reads after the trailing bar.sync.
     __syncthreads();
     if (threadIdx.x == 0) {
         epoch += 1u;
         const unsigned target = epoch * members + (force ? 1u : 0u);
-        __threadfence();
         red_release_add_u32(bar, 1u);
         int ok = 1;
         unsigned long long polls = 0;
         while ((int)(ld_acquire_u32(bar) - target) < 0) {
-            if (ld_volatile(abort_flag)) { ok = 0; break; }
-            if (++polls > limit) { atomicExch(abort_flag, 1); ok = 0; break; }
-            __nanosleep(64);
+            if ((++polls & 31) == 0) {
+                if (ld_volatile(abort_flag)) { ok = 0; break; }
+                if (polls > limit) { atomicExch(abort_flag, 1); ok = 0; break; }
+                __nanosleep(32);
+            }
         }
         if (ok && ld_volatile(abort_flag)) ok = 0;
-        __threadfence();
         *s_ok = ok;
     }
     __syncthreads();
@@ -100,9 +103,15 @@ __device__ __forceinline__ void block_sum(double (&v)[ND], double *s_red, double
     }
     __syncthreads();
     if (threadIdx.x < ND) {
-        double s = 0.0;
-        for (int w = 0; w < kBlock / 32; ++w) s += s_red[w * ND + threadIdx.x];
-        s_out[threadIdx.x] = s;
+        // pairwise over the warps (a dependent FP64 add costs ~64 cycles on GB300)
+        double w8[kBlock / 32];
+#pragma unroll
+        for (int w = 0; w < kBlock / 32; ++w) w8[w] = s_red[w * ND + threadIdx.x];
+#pragma unroll
+        for (int h = kBlock / 64; h >= 1; h >>= 1)
+#pragma unroll
+            for (int w = 0; w < h; ++w) w8[w] += w8[w + h];
+        s_out[threadIdx.x] = w8[0];
     }
     __syncthreads();
 }
@@ -127,6 +136,30 @@ __device__ __forceinline__ void grid_partials_sum(const double *part, int stride
                                                   double *s_out)
 {
     partials_sum<ND>(part, (int)gridDim.x, stride, s_red, s_out);
+}
+
+// One warp: sum over `count` CTAs of part[c * stride + q], q < ND, in a fixed
+// order; lane 0 writes dst[q] (shared memory), then the warp syncs.
+template <int ND>
+__device__ __forceinline__ void warp_partials_sum(const double *part, int count, int stride,
+                                                  double *dst)
+{
+    const int lane = threadIdx.x & 31;
+    double v[ND];
+#pragma unroll
+    for (int q = 0; q < ND; ++q) v[q] = 0.0;
+    for (int c = lane; c < count; c += 32) {
+#pragma unroll
+        for (int q = 0; q < ND; ++q) v[q] += __ldcg(part + (size_t)c * stride + q);
+    }
+#pragma unroll
+    for (int q = 0; q < ND; ++q) {
+        double t = v[q];
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) t += __shfl_down_sync(0xffffffffu, t, o);
+        if (lane == 0) dst[q] = t;
+    }
+    __syncwarp();
 }
 
 // ------------------------------------------------------------------------
@@ -385,7 +418,8 @@ struct Smem {
     double eta[2], zeta[2], ieta[2]; // eta_m, zeta_m, 1 / eta_m
     double bring[kMaxL + 1][kMaxDots];   // one-CTA group: reduced dots of the last l+1 iterations
     double bnorm[2];
-    Coef<T> cf;
+    double raw2[kMaxDots];           // the scalar warp's copy of a reduced dot column
+    Coef<T> cfb[2];                  // coefficients of iterations i (i & 1) and i + 1
     int ok;
 };
 
@@ -396,7 +430,8 @@ template <> struct Eps<float> { static constexpr double v = (double)FLT_EPSILON;
 template <typename T>
 __device__ __forceinline__ T *ring(const SolveArgs<T> &a, int k, long long j)
 {
-    return a.zring + (a.base[k] + (j % a.depth[k])) * a.n;
+    // j < 2^31 (iteration indices); 32-bit modulo
+    return a.zring + (a.base[k] + (int64_t)((unsigned)j % (unsigned)a.depth[k])) * a.n;
 }
 
 // ------------------------------------------------------------------------
@@ -426,6 +461,14 @@ struct GridGroup {
     __device__ __forceinline__ void get_dots(const SolveArgs<T> &a, Smem<T> &s, int slot, double *dst)
     {
         grid_partials_sum<ND>(a.part + (size_t)slot * gridDim.x * kMaxDots, kMaxDots, s.red, dst);
+    }
+    // one warp sums ring slot `slot` over the CTAs into dst (every CTA's warp
+    // adds in the same order, so all CTAs get the same bits)
+    template <int ND>
+    __device__ __forceinline__ void get_dots_warp(const SolveArgs<T> &a, Smem<T> &, int slot,
+                                                  double *dst)
+    {
+        warp_partials_sum<ND>(a.part + (size_t)slot * gridDim.x * kMaxDots, (int)gridDim.x, kMaxDots, dst);
     }
     __device__ __forceinline__ void put_norms(const SolveArgs<T> &a, Smem<T> &s)
     {
@@ -459,6 +502,14 @@ struct BlockGroup {
     {
         if ((int)threadIdx.x < ND) dst[threadIdx.x] = s.bring[slot][threadIdx.x];
         __syncthreads();
+    }
+    // the scalar warp of this very CTA reads the ring in shared memory
+    template <int ND>
+    __device__ __forceinline__ void get_dots_warp(const SolveArgs<T> &, Smem<T> &s, int slot,
+                                                  double *dst)
+    {
+        for (int q = threadIdx.x & 31; q < ND; q += 32) dst[q] = s.bring[slot][q];
+        __syncwarp();
     }
     __device__ __forceinline__ void put_norms(const SolveArgs<T> &, Smem<T> &s)
     {
@@ -500,6 +551,12 @@ struct GangGroup {
     {
         partials_sum<ND>(part + (size_t)slot * G * kMaxDots, G, kMaxDots, s.red, dst);
     }
+    template <int ND>
+    __device__ __forceinline__ void get_dots_warp(const SolveArgs<T> &, Smem<T> &, int slot,
+                                                  double *dst)
+    {
+        warp_partials_sum<ND>(part + (size_t)slot * G * kMaxDots, G, kMaxDots, dst);
+    }
     __device__ __forceinline__ void put_norms(const SolveArgs<T> &, Smem<T> &s)
     {
         if (threadIdx.x == 0) {
@@ -524,10 +581,9 @@ struct GangGroup {
 // critical path).
 // ------------------------------------------------------------------------
 template <typename T, int L>
-__device__ void scalar_step(Smem<T> &s, const SolveArgs<T> &a, long long i, double rn,
-                            double tau, long long budget)
+__device__ void scalar_step(Smem<T> &s, Coef<T> &cf, const double *raw, const SolveArgs<T> &a,
+                            long long i, double rn, double tau, long long budget)
 {
-    Coef<T> &cf = s.cf;
     cf.end = -1;
     cf.fmode = 0;
     cf.ncopy = 0;
@@ -548,7 +604,7 @@ __device__ void scalar_step(Smem<T> &s, const SolveArgs<T> &a, long long i, doub
         auto gam = [&](long long j) -> double { return s.gam[j % (L + 1)]; };
         // raw column c (dots of iteration i-l): position q is row c-2l+q
 #pragma unroll
-        for (int q = 0; q <= 2 * L; ++q) col[q] = (c - 2 * L + q >= 0) ? s.raw[q] : 0.0;
+        for (int q = 0; q <= 2 * L; ++q) col[q] = (c - 2 * L + q >= 0) ? raw[q] : 0.0;
         const long long lo = (c - 2 * L > 0) ? c - 2 * L : 0;
         if (!a.dots_2l1)   // Sec. 2.2: g_{j,c} = g_{c-l,j+l} for j = c-2l .. c-l-1
             for (long long j = lo; j <= c - L - 1; ++j) col[j - c + 2 * L] = g(c - L, j + L);
@@ -791,11 +847,9 @@ template <typename T, int L, int VEC, int OP, class Grp, int RPT = 1>
 __device__ void plcg_body(const SolveArgs<T> &a, Smem<T> &s, Grp &grp)
 {
     constexpr int UNIT = kBlock * VEC;
-    constexpr int USWEEP = UNIT * RPT;   // rows per unit of the iteration sweep
     constexpr bool kF32 = (sizeof(T) == 4);
     const int64_t n = a.n;
     const int64_t nunits = (n + UNIT - 1) / UNIT;
-    const int64_t nunits_s = (n + USWEEP - 1) / USWEEP;
     const int tid = threadIdx.x;
     const T cC = (T)a.st.center, cO = (T)a.st.off;
     // (A z)_g = kc * c + kn * nb (see op_parts)
@@ -880,12 +934,21 @@ __device__ void plcg_body(const SolveArgs<T> &a, Smem<T> &s, Grp &grp)
         }
         PLCG_SYNC();
 
+        // Coefficients of iteration 0 (fill phase: no dot products needed yet).
+        // Afterwards, the coefficients of iteration i + 1 need the dots of
+        // iteration i + 1 - l.  Serial mode (l = 1, or lookahead off): after the
+        // barrier that ends iteration i, every CTA sums those partials and
+        // thread 0 runs the scalar step while the others wait.  Lookahead mode
+        // (l >= 2): those dots are already complete during iteration i, so the
+        // last warp of every CTA computes them while the other warps sweep --
+        // Alg. 2's overlap of the global reduction (MPI_Iallreduce ... MPI_Wait
+        // l iterations later) with the local work, on one GPU.
+        const bool la = (L >= 2) && a.lookahead;
+        const int nsw = la ? kBlock - 32 : kBlock;   // threads that sweep
+        if (tid == 0) scalar_step<T, L>(s, s.cfb[0], s.raw, a, 0, rn, tau, budget);
+        __syncthreads();
         for (long long i = 0;; ++i) {
-            if (i >= L)   // MPI_Wait(req(i-l)): the reduced dots of iteration i-l
-                grp.template get_dots<2 * L + 1>(a, s, (int)((i - L) % (L + 1)), s.raw);
-            if (tid == 0) scalar_step<T, L>(s, a, i, rn, tau, budget);
-            __syncthreads();
-            const Coef<T> &cf = s.cf;
+            const Coef<T> &cf = s.cfb[i & 1];
             if (cf.end >= 0) {
                 // ---- final vector update of the segment
                 if (cf.end != kSegNonfinite) {
@@ -934,6 +997,14 @@ __device__ void plcg_body(const SolveArgs<T> &a, Smem<T> &s, Grp &grp)
                 break;
             }
 
+            if (la && tid >= nsw) {
+                // scalar warp: the coefficients of iteration i + 1
+                if (i + 1 >= L)
+                    grp.template get_dots_warp<2 * L + 1>(a, s, (int)((i + 1 - L) % (L + 1)), s.raw2);
+                if ((tid & 31) == 0)
+                    scalar_step<T, L>(s, s.cfb[(i + 1) & 1], s.raw2, a, i + 1, rn, tau, budget);
+                __syncwarp();
+            }
             // ---- one full iteration sweep: K1, K4, K5 (partials), K6.  A thread
             // owns RPT row groups of VEC rows per unit (stride kBlock * VEC) and
             // issues every load of all of them before any store (the vectors are
@@ -947,19 +1018,21 @@ __device__ void plcg_body(const SolveArgs<T> &a, Smem<T> &s, Grp &grp)
             // the registers (and occupancy) a copy would take.
             using CoefRef = std::conditional_t<(RPT > 1), SweepCoef<T, L>, const Coef<T> &>;
             using StRef = std::conditional_t<(RPT > 1), StencilDesc, const StencilDesc &>;
-            CoefRef C = s.cf;
+            CoefRef C = cf;
             StRef st = a.st;
             const CsrDesc &csr = a.csr;
             T *const pvec = a.p;
             const bool rec = C.mode == 1;
             DotAcc<T, VEC> dac[2 * L + 1];
             int since_flush = 0;
+            const int64_t usw = (int64_t)nsw * VEC * RPT;   // rows per sweep unit
+            const int64_t nunits_s = (tid < nsw) ? (n + usw - 1) / usw : 0;
             for (int64_t u = grp.unit0(); u < nunits_s; u += grp.ustep()) {
                 int64_t g0[RPT];
                 bool ok[RPT];
 #pragma unroll
                 for (int r = 0; r < RPT; ++r) {
-                    g0[r] = u * USWEEP + ((int64_t)r * kBlock + tid) * VEC;
+                    g0[r] = u * usw + ((int64_t)r * nsw + tid) * VEC;
                     ok[r] = g0[r] < n;
                 }
                 // -- loads
@@ -1028,7 +1101,7 @@ __device__ void plcg_body(const SolveArgs<T> &a, Smem<T> &s, Grp &grp)
                     // -- stores
                     vst<T, VEC>(C.zl_new + g0[r], un);
                     if (!rec) {
-                        for (int k = 0; k < C.ncopy; ++k) vst<T, VEC>(s.cf.cpy[k] + g0[r], un);
+                        for (int k = 0; k < C.ncopy; ++k) vst<T, VEC>(cf.cpy[k] + g0[r], un);
                     } else {
 #pragma unroll
                         for (int k = 0; k < L; ++k) vst<T, VEC>(C.nw[k] + g0[r], nw[k]);
@@ -1042,7 +1115,7 @@ __device__ void plcg_body(const SolveArgs<T> &a, Smem<T> &s, Grp &grp)
                         if (src == 0) continue;
                         T o[VEC];
                         if (src == 1) {
-                            vld<T, VEC>(s.cf.dptr[q] + g0[r], o);
+                            vld<T, VEC>(cf.dptr[q] + g0[r], o);
                         } else {
 #pragma unroll
                             for (int v = 0; v < VEC; ++v)
@@ -1069,6 +1142,15 @@ __device__ void plcg_body(const SolveArgs<T> &a, Smem<T> &s, Grp &grp)
             block_sum<2 * L + 1>(acc, s.red, s.out);
             grp.put_dots(a, s, (int)(i % (L + 1)), 2 * L + 1);
             PLCG_SYNC();
+            if (!la) {   // MPI_Wait(req(i+1-l)) and the scalar step, serially (warp 0)
+                if (tid < 32) {
+                    if (i + 1 >= L)
+                        grp.template get_dots_warp<2 * L + 1>(a, s, (int)((i + 1 - L) % (L + 1)), s.raw);
+                    if (tid == 0)
+                        scalar_step<T, L>(s, s.cfb[(i + 1) & 1], s.raw, a, i + 1, rn, tau, budget);
+                }
+                __syncthreads();
+            }
         }
     }
 finish:
