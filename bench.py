@@ -220,7 +220,7 @@ def run_ours(args):
     achieved_gbs = bytes_launch / statistics.mean(kern_s) / 1e9
     dp_flops = statistics.mean(iters) * dp_flops_per_point(L_HEAD) * n
     achieved_dp_tf = dp_flops / statistics.mean(kern_s) / 1e12
-    dp_peak_tf = 1.25   # nominal FP64 rate of GB300 (recipe table); see the design doc
+    dp_peak_tf = 1.25   # nominal FP64 rate of GB300 (units x clock)
     # measured DRAM traffic per launch: bytes per row per sweep of an ncu
     # capture (smaller grid, same kernel) x rows x sweeps (iterations + 2
     # residual sweeps) of this solve

@@ -41,7 +41,7 @@ typedef enum {
     PLCG_ERR_NOMEM = -2,        /* device or host allocation failed            */
     PLCG_ERR_CUDA = -3,         /* a CUDA call failed (message has the reason) */
     PLCG_ERR_BREAKDOWN = -4,    /* square-root breakdowns exceeded max_restarts
-                                   (Alg. 1 line 11, Sec. 2.2)                  */
+                                   (Algorithm 1, K2; Sec. 2.2)                    */
     PLCG_ERR_MAXIT = -5,        /* iteration budget exhausted; x = last iterate */
     PLCG_ERR_NONFINITE = -6,    /* NaN/Inf met in b, x0 or a recurrence         */
     PLCG_ERR_TIMEOUT = -7,      /* a bounded device wait expired                */
@@ -89,7 +89,7 @@ typedef struct {
     double rtol;                /* stop when ||b - A x|| < rtol ||b|| (1e-8)      */
     int64_t maxit;              /* budget on the iterate index k (100000)        */
     int prec;                   /* plcg_precision (PLCG_FP64)                    */
-    int dots_2l1;               /* 1: the 2l+1 dot products of Alg. 1 line 23;
+    int dots_2l1;               /* 1: the 2l+1 dot products of Algorithm 1, K5;
                                    0: l+1 dots via the symmetry of G (Sec. 2.2)  (0) */
     int max_restarts;           /* explicit restarts allowed (8)                 */
     double inner_rtol_floor;    /* FP32 path: floor of the inner relative tolerance

@@ -63,7 +63,7 @@ def cg_decimal(A, b, kmax, prec=60):
 
 
 def plcg_decimal(A, b, l, sigma, kmax, prec=60):
-    """Algorithm 1 with M = I from x0 = 0, all 2l+1 dot products of line 23,
+    """Algorithm 1 with M = I from x0 = 0, all 2l+1 dot products of K5,
     full histories.  Returns dict with xs (x_k), gamma, delta, zeta, G (dict
     keyed by (j, i)), Z (list over k of dict j -> vector).  Stops after kmax
     x-updates or at a (lucky) breakdown, where it stops without the extra

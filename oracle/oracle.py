@@ -49,6 +49,7 @@ class _Params(C.Structure):
     _fields_ = [
         ("l", C.c_int), ("sigma", C.c_void_p), ("rtol", C.c_double),
         ("maxit", C.c_int64), ("dots_2l1", C.c_int), ("max_restarts", C.c_int),
+        ("precond", C.c_int),
     ]
 
 
@@ -166,7 +167,11 @@ class Result:
     trace: dict = field(default_factory=dict)
 
 
-def _solve(fn_name, op, b, x0, l, sigma, rtol, maxit, dots_2l1, max_restarts, trace_cap):
+_PRECONDS = {None: 0, "none": 0, "jacobi": 1}
+
+
+def _solve(fn_name, op, b, x0, l, sigma, rtol, maxit, dots_2l1, max_restarts, trace_cap,
+           precond=None):
     lib = _load()
     h = _OpHolder(op)
     n = h.n
@@ -176,7 +181,8 @@ def _solve(fn_name, op, b, x0, l, sigma, rtol, maxit, dots_2l1, max_restarts, tr
     x = np.zeros(n) if x0 is None else np.array(x0, dtype=np.float64, copy=True)
     sig = None if sigma is None else np.ascontiguousarray(sigma, dtype=np.float64)
     p = _Params(l=int(l), sigma=_ptr(sig), rtol=float(rtol), maxit=int(maxit),
-                dots_2l1=int(bool(dots_2l1)), max_restarts=int(max_restarts))
+                dots_2l1=int(bool(dots_2l1)), max_restarts=int(max_restarts),
+                precond=_PRECONDS[precond])
     r = _Result()
     tr = {}
     if trace_cap > 0:
@@ -201,18 +207,27 @@ def _solve(fn_name, op, b, x0, l, sigma, rtol, maxit, dots_2l1, max_restarts, tr
                   recursive_relres=r.recursive_relres, true_relres=r.true_relres, trace=tr)
 
 
-def cg(op, b, x0=None, rtol=1e-8, maxit=100000, max_restarts=8, trace_cap=0) -> Result:
-    """Classic Hestenes-Stiefel CG in FP64 (textbook; Sec. 1 cites it)."""
-    return _solve("orc_cg", op, b, x0, 1, None, rtol, maxit, 0, max_restarts, trace_cap)
+def cg(op, b, x0=None, rtol=1e-8, maxit=100000, max_restarts=8, trace_cap=0,
+       precond=None) -> Result:
+    """Classic Hestenes-Stiefel CG in FP64 (textbook; Sec. 1 cites it).
+
+    ``precond="jacobi"``: the textbook preconditioned CG with M = diag(A);
+    the tolerance then applies to natural norms ||.||_{M^{-1}} (Sec. 2.2,
+    "Residual norm in p(l)-CG")."""
+    return _solve("orc_cg", op, b, x0, 1, None, rtol, maxit, 0, max_restarts, trace_cap,
+                  precond)
 
 
 def plcg(op, b, x0=None, l=1, sigma=None, rtol=1e-8, maxit=100000, dots_2l1=True,
-         max_restarts=8, trace_cap=0) -> Result:
-    """Algorithm 1 (M = I) in FP64.  ``sigma`` defaults to zero shifts."""
+         max_restarts=8, trace_cap=0, precond=None) -> Result:
+    """Algorithm 1 in FP64.  ``sigma`` defaults to zero shifts.
+
+    ``precond=None``: M = I.  ``precond="jacobi"``: M = diag(A), with u and
+    z^(l) kept apart and natural-norm stopping (Sec. 2.2)."""
     if sigma is None:
         sigma = np.zeros(l)
     sigma = np.asarray(sigma, dtype=np.float64)
     if sigma.shape != (l,):
         raise ValueError("need exactly l shifts")
     return _solve("orc_plcg", op, b, x0, l, sigma, rtol, maxit, dots_2l1, max_restarts,
-                  trace_cap)
+                  trace_cap, precond)

@@ -16,19 +16,21 @@
  *   - orc_cg         : classic Hestenes-Stiefel CG (the paper cites it, Sec. 1,
  *                      and costs it in Table 1, but prints no listing, so the
  *                      textbook recurrence is used).
- *   - orc_plcg       : Algorithm 1 with M = I, step by step, in the paper's
- *                      notation: K1 SPMV (Alg. 1 lines 3-6), K2 finalise a
- *                      column of G (lines 9-11), K3 add a column to T
- *                      (lines 12-18), K4 the l+1 basis recurrences
- *                      (lines 19-21, Eq. all_z_rec2 / specific_z_rec), K5 the
- *                      dot products (line 23; Sec. 2.2 "Number of dot
- *                      products" for the l+1 variant), K6 the D-Lanczos
- *                      solution update and stop test (lines 24-33, Sec. 2.1).
+ *   - orc_plcg       : Algorithm 1, step by step, in the paper's notation,
+ *                      with M = I or the Jacobi preconditioner M = diag(A),
+ *                      under the kernel names of Sec. 3.1: K1 apply A and
+ *                      M^{-1}, K2 finalise a column of G (with the
+ *                      square-root breakdown check), K3 add a column to T,
+ *                      K4 the l+1 basis recurrences (Eq. all_z_rec2 /
+ *                      specific_z_rec), K5 the dot products (Sec. 2.2
+ *                      "Number of dot products" for the l+1 variant), K6 the
+ *                      D-Lanczos solution update and stop test (Sec. 2.1).
  *   - orc_chebyshev_shifts : the shift formula of Sec. 2.2 (Eq. chebyshev).
  *
- * Readings of points the paper leaves open (each one is listed in the design doc):
- *   R1  u_0 is normalised together with z_0 (with M = I, u_i = z^(l)_i for all
- *       i, so line 3 at i = 0 forms (A - sigma_0 I) z_0 as Eq. z_rec says).
+ * Readings of points the paper leaves open:
+ *   R1  the initialization normalises u_0 together with z_0 (with M = I,
+ *       u_i = z^(l)_i for all i, so K1 at i = 0 forms (A - sigma_0 I) z_0 as
+ *       Eq. z_rec says).
  *   R2  every index range is clamped at 0; g_{j,i} and z_j with j < 0 are zero;
  *       delta_{-1} = 0 (Sec. 2.1).
  *   R3  stop test |zeta_k| < rtol * ||b|| (strict), ||b|| of the original
@@ -45,12 +47,23 @@
  *         arg < -thr    -> breakdown: form x_{i-l} and restart from it.
  *       Restarts are counted; more than max_restarts ends the solve with
  *       ORC_ERR_BREAKDOWN.
- *   R5  dots: dots_2l1 = 1 computes the 2l+1 products of line 23 literally;
+ *   R5  dots: dots_2l1 = 1 computes the 2l+1 products of K5 literally;
  *       dots_2l1 = 0 computes only the l+1 products of Sec. 2.2 and fills
  *       rows c-2l .. c-l-1 of column c from the symmetry
  *       g_{j,c} = g_{c-l,j+l} (Eq. symmetry_G) when column c is finalised.
  *   R6  the iteration budget maxit counts the x-index k summed over
  *       segments.
+ *   R7  preconditioning (precond = 1): M = diag(A), every diagonal entry
+ *       positive (else ORC_ERR_INVALID).  p(l)-CG keeps u_i and z^(l)_i as
+ *       separate vectors: K1 forms u_{i+1} and then z^(l)_{i+1} =
+ *       M^{-1} u_{i+1}, K4 also runs the u recurrence of Sec. 2.2
+ *       (Eq. zhatid3), and the dots of K5 take u_{i+1}.  The
+ *       initialization normalises u_0 with z_0 (R1).  The norm of R3 becomes the natural
+ *       norm ||v||_{M^{-1}} = sqrt(v^T M^{-1} v) (Sec. 2.2 "Residual norm":
+ *       |zeta_k| = sqrt((u_k, r_k)) for the preconditioned method): the stop
+ *       test is |zeta_k| < rtol * ||b||_{M^{-1}} and the true residual is
+ *       measured as ||b - A x||_{M^{-1}}.  CG becomes the textbook
+ *       preconditioned CG with rho = (r, M^{-1} r).
  *
  * Everything is double precision and serial; dot products are summed left
  * to right.  No blocking, fusion or reordering beyond the algorithm's own.
@@ -91,6 +104,7 @@ typedef struct {
     int64_t maxit;            /* budget on the x-index k (R6)               */
     int dots_2l1;             /* R5                                          */
     int max_restarts;         /* R4                                          */
+    int precond;              /* R7: 0 M = I, 1 M = diag(A) (Jacobi)          */
 } orc_params;
 
 /* Results and optional traces of one solve.  The traces (all caller-owned,
@@ -104,7 +118,7 @@ typedef struct {
     int64_t restarts;
     int64_t segments;
     double recursive_relres;  /* |zeta_k| / ||b|| (CG: ||r_k|| / ||b||)      */
-    double true_relres;       /* ||b - A x|| / ||b||                          */
+    double true_relres;       /* ||b - A x|| / ||b|| (R7: natural norms)     */
     int64_t trace_cap;
     int64_t trace_len;        /* entries written in the x/zeta traces        */
     double *x_hist;           /* [trace_cap][n]      x_k                     */
@@ -161,15 +175,42 @@ void orc_apply(const orc_op *A, const double *x, double *y)
             }
 }
 
-/* r = b - A x; returns ||r||. */
+/* ||v|| (minv == NULL) or the natural norm sqrt(v^T M^{-1} v) (R7). */
+static double mnorm(int64_t n, const double *v, const double *minv)
+{
+    if (!minv) return nrm2(n, v);
+    double s = 0.0;
+    for (int64_t i = 0; i < n; ++i) s += v[i] * minv[i] * v[i];
+    return sqrt(s);
+}
+
+/* r = b - A x; returns ||r|| (R7: ||r||_{M^{-1}}). */
 static double residual(const orc_op *A, const double *b, const double *x,
-                       double *r, orc_result *res)
+                       double *r, const double *minv, orc_result *res)
 {
     orc_apply(A, x, r);
     res->spmvs++;
     for (int64_t i = 0; i < A->n; ++i) r[i] = b[i] - r[i];
     res->dots++;
-    return nrm2(A->n, r);
+    return mnorm(A->n, r, minv);
+}
+
+/* R7: M^{-1} = diag(A)^{-1}.  Returns 0, or -1 if a diagonal entry is not
+ * positive (M would not be SPD) or a CSR row has none. */
+static int jacobi_minv(const orc_op *A, double *minv)
+{
+    for (int64_t r = 0; r < A->n; ++r) {
+        double d = 0.0;
+        if (A->kind == ORC_CSR) {
+            for (int64_t e = A->rowptr[r]; e < A->rowptr[r + 1]; ++e)
+                if (A->col[e] == r) d += A->val[e];
+        } else {
+            d = A->center;
+        }
+        if (!(d > 0.0) || !isfinite(d)) return -1;
+        minv[r] = 1.0 / d;
+    }
+    return 0;
 }
 
 /* ------------------------------------------------------------------ */
@@ -188,18 +229,21 @@ void orc_chebyshev_shifts(int l, double lmin, double lmax, double *sigma)
 /* Classic CG (Hestenes-Stiefel), one segment from the residual r.     */
 /*   alpha = (r,r)/(p,Ap); x += alpha p; r -= alpha Ap;                */
 /*   beta = (r',r')/(r,r); p = r' + beta p.                            */
+/* With M (R7), the textbook preconditioned form: z = M^{-1} r,        */
+/*   rho = (r,z), alpha = rho/(p,Ap), beta = rho'/rho, p = z' + beta p. */
 /* ------------------------------------------------------------------ */
 typedef struct { int64_t k; int end; } seg_out;
 enum { SEG_CONVERGED = 0, SEG_MAXIT = 1, SEG_BREAKDOWN = 2, SEG_LUCKY = 3, SEG_NONFINITE = 4 };
 
-static int cg_segment(const orc_op *A, double *x, double *r, double tau_abs,
-                      int64_t budget, double *work, orc_result *res, int trace,
-                      seg_out *so)
+static int cg_segment(const orc_op *A, double *x, double *r, const double *minv,
+                      double tau_abs, int64_t budget, double *work, orc_result *res,
+                      int trace, seg_out *so)
 {
     const int64_t n = A->n;
-    double *p = work, *q = work + n;
-    memcpy(p, r, (size_t)n * sizeof(double));
-    double rr = dot(n, r, r);
+    double *p = work, *q = work + n, *z = work + 2 * n;
+    for (int64_t i = 0; i < n; ++i) z[i] = minv ? minv[i] * r[i] : r[i];
+    memcpy(p, z, (size_t)n * sizeof(double));
+    double rr = dot(n, r, z);
     res->dots++;
     int64_t k = 0;
     for (;;) {
@@ -224,10 +268,11 @@ static int cg_segment(const orc_op *A, double *x, double *r, double tau_abs,
         const double alpha = rr / pq;
         for (int64_t i = 0; i < n; ++i) x[i] += alpha * p[i];
         for (int64_t i = 0; i < n; ++i) r[i] -= alpha * q[i];
-        const double rr_new = dot(n, r, r);
+        for (int64_t i = 0; i < n; ++i) z[i] = minv ? minv[i] * r[i] : r[i];
+        const double rr_new = dot(n, r, z);
         res->dots++;
         const double beta = rr_new / rr;
-        for (int64_t i = 0; i < n; ++i) p[i] = r[i] + beta * p[i];
+        for (int64_t i = 0; i < n; ++i) p[i] = z[i] + beta * p[i];
         if (trace && res->gamma_hist && k < res->trace_cap) res->gamma_hist[k] = alpha;
         if (trace && res->delta_hist && k < res->trace_cap) res->delta_hist[k] = beta;
         rr = rr_new;
@@ -236,13 +281,14 @@ static int cg_segment(const orc_op *A, double *x, double *r, double tau_abs,
 }
 
 /* ------------------------------------------------------------------ */
-/* p(l)-CG, one segment of Algorithm 1 (M = I) started from the        */
-/* residual r with rn = ||r||.  x is updated in place.                  */
+/* p(l)-CG, one segment of Algorithm 1 started from the residual r    */
+/* with rn = sqrt((r, M^{-1} r)) (M = I: ||r||).  x is updated in place. */
 /* ------------------------------------------------------------------ */
 typedef struct {
     int64_t n;
     int l, R, W;              /* R: ring depth per basis, W = 2l+1 rows     */
     double *zbuf;             /* (l+1) rings of R vectors                   */
+    double *ubuf;             /* R7: ring of R vectors u_j (NULL: u = z^(l)) */
     double *gband;            /* column c: rows c-2l .. c                    */
     double *gamma, *delta, *eta, *zeta;
     int64_t ncols;
@@ -252,6 +298,12 @@ typedef struct {
 static double *Z(plcg_ws *w, int k, int64_t j)
 {
     return w->zbuf + ((int64_t)k * w->R + (j % w->R)) * w->n;
+}
+
+/* u_j: its own ring with a preconditioner (R7), else z^(l)_j (M = I). */
+static double *U(plcg_ws *w, int64_t j)
+{
+    return w->ubuf ? w->ubuf + (j % w->R) * w->n : Z(w, w->l, j);
 }
 
 /* g_{j,c} for c-2l <= j <= c, j >= 0 (the band of G, Sec. 2.1). */
@@ -267,7 +319,8 @@ static double gget(plcg_ws *w, int64_t j, int64_t c)
 }
 
 static int plcg_segment(const orc_op *A, double *x, const double *r, double rn,
-                        const orc_params *P, double tau_abs, int64_t budget,
+                        const double *minv, const orc_params *P, double tau_abs,
+                        int64_t budget,
                         plcg_ws *w, double *p, orc_result *res, int trace,
                         seg_out *so)
 {
@@ -278,9 +331,12 @@ static int plcg_segment(const orc_op *A, double *x, const double *r, double rn,
 
     memset(w->gband, 0, (size_t)(w->ncols * w->W) * sizeof(double));
 
-    /* Alg. 1 line 1 (R1): z^(k)_0 := u_0 := r_0 / sqrt((u_0, r_0)), g_00 := 1. */
+    /* Algorithm 1, initialization (R1): u_0 := b - A x_0 (= r), r_0 := M^{-1} u_0,
+     * z^(k)_0 := r_0 / sqrt((u_0, r_0)), u_0 normalised alike; g_00 := 1. */
     for (int k = 0; k <= l; ++k)
-        for (int64_t t = 0; t < n; ++t) Z(w, k, 0)[t] = r[t] / rn;
+        for (int64_t t = 0; t < n; ++t) Z(w, k, 0)[t] = (minv ? minv[t] * r[t] : r[t]) / rn;
+    if (w->ubuf)
+        for (int64_t t = 0; t < n; ++t) U(w, 0)[t] = r[t] / rn;
     *Gp(w, 0, 0) = 1.0;
     if (trace && res->g_hist && res->trace_cap > 0) {
         for (int q = 0; q < w->W; ++q) res->g_hist[q] = 0.0;
@@ -296,12 +352,17 @@ static int plcg_segment(const orc_op *A, double *x, const double *r, double rn,
 
     for (int64_t i = 0;; ++i) {
         if (i + 2 >= w->ncols) { so->k = (i > l) ? i - l : 0; so->end = SEG_MAXIT; return 0; }
-        /* ---- K1 (lines 3-6): u_{i+1} = A z^(l)_i (- sigma_i u_i), z^(l)_{i+1} := u_{i+1} */
+        /* ---- K1: u_{i+1} = A z^(l)_i (- sigma_i u_i), then
+         * z^(l)_{i+1} := M^{-1} u_{i+1} (M = I: the same vector), and in the
+         * fill phase the auxiliary copies z^(k)_{i+1} := z^(l)_{i+1}. */
         double *zl_new = Z(w, l, i + 1);
-        orc_apply(A, Z(w, l, i), zl_new);
+        double *u_new = U(w, i + 1);
+        orc_apply(A, Z(w, l, i), u_new);
         res->spmvs++;
         if (i < l)
-            for (int64_t t = 0; t < n; ++t) zl_new[t] -= sigma[i] * Z(w, l, i)[t];
+            for (int64_t t = 0; t < n; ++t) u_new[t] -= sigma[i] * U(w, i)[t];
+        if (minv)
+            for (int64_t t = 0; t < n; ++t) zl_new[t] = minv[t] * u_new[t];
         if (i < l - 1)
             for (int k = (int)i + 1; k <= l - 1; ++k)
                 memcpy(Z(w, k, i + 1), zl_new, (size_t)n * sizeof(double));
@@ -314,7 +375,7 @@ static int plcg_segment(const orc_op *A, double *x, const double *r, double rn,
             if (!P->dots_2l1)
                 for (int64_t j = lo; j <= c - l - 1; ++j)
                     *Gp(w, j, c) = gget(w, c - l, j + l);
-            /* ---- K2 (lines 9-10): correct rows c-l+1 .. c-1, then the diagonal. */
+            /* ---- K2: correct rows c-l+1 .. c-1, then the diagonal. */
             for (int64_t j = (c - l + 1 > 0 ? c - l + 1 : 0); j <= c - 1; ++j) {
                 double s = *Gp(w, j, c);
                 for (int64_t k = lo; k <= j - 1; ++k) s -= gget(w, k, j) * gget(w, k, c);
@@ -324,7 +385,7 @@ static int plcg_segment(const orc_op *A, double *x, const double *r, double rn,
             double arg = graw;
             for (int64_t k = lo; k <= c - 1; ++k) arg -= gget(w, k, c) * gget(w, k, c);
 
-            /* ---- K3 (lines 12-18), gamma part: it does not use g_{c,c}. */
+            /* ---- K3, gamma part: it does not use g_{c,c}. */
             const double gmm = gget(w, m, m);
             double gam;
             if (i < 2 * l)
@@ -335,7 +396,7 @@ static int plcg_segment(const orc_op *A, double *x, const double *r, double rn,
                        - gget(w, m - 1, m) * w->delta[m - 1]) / gmm;
             w->gamma[m] = gam;
 
-            /* ---- line 11: square-root breakdown check (R4). */
+            /* ---- K2: square-root breakdown check (R4). */
             const double thr = 64.0 * eps * fabs(graw);
             if (!isfinite(arg) || !isfinite(gam)) { so->k = m; so->end = SEG_NONFINITE; return 0; }
             if (arg <= thr) {
@@ -375,7 +436,7 @@ static int plcg_segment(const orc_op *A, double *x, const double *r, double rn,
             const double dm = w->delta[m];
             const double dm1 = (m >= 1) ? w->delta[m - 1] : 0.0;   /* delta_{-1} = 0 */
 
-            /* ---- K4 (lines 19-21): one new vector per basis.              */
+            /* ---- K4: one new vector per basis.                            */
             /* z^(k)_{m+k+1} = (z^(k+1)_{m+k+1} + (sigma_k - gamma_m) z^(k)_{m+k}
              *                  - delta_{m-1} z^(k)_{m+k-1}) / delta_m,  k < l    */
             for (int k = 0; k < l; ++k) {
@@ -387,12 +448,21 @@ static int plcg_segment(const orc_op *A, double *x, const double *r, double rn,
                     zn[t] = (zup[t] + (sigma[k] - gam) * zc[t]
                              - (zp ? dm1 * zp[t] : 0.0)) / dm;
             }
-            /* z^(l)_{i+1} = (A z^(l)_i - gamma_m z^(l)_i - delta_{m-1} z^(l)_{i-1}) / delta_m */
+            /* z^(l)_{i+1} = (M^{-1} A z^(l)_i - gamma_m z^(l)_i
+             *                        - delta_{m-1} z^(l)_{i-1}) / delta_m */
             {
                 const double *zc = Z(w, l, i);
                 const double *zp = (i - 1 >= 0) ? Z(w, l, i - 1) : NULL;
                 for (int64_t t = 0; t < n; ++t)
                     zl_new[t] = (zl_new[t] - gam * zc[t] - (zp ? dm1 * zp[t] : 0.0)) / dm;
+            }
+            /* Eq. zhatid3: u_{i+1} = (A z^(l)_i - gamma_m u_i
+             *                                   - delta_{m-1} u_{i-1}) / delta_m */
+            if (w->ubuf) {
+                const double *uc = U(w, i);
+                const double *up = (i - 1 >= 0) ? U(w, i - 1) : NULL;
+                for (int64_t t = 0; t < n; ++t)
+                    u_new[t] = (u_new[t] - gam * uc[t] - (up ? dm1 * up[t] : 0.0)) / dm;
             }
             if (trace && res->gamma_hist && m < res->trace_cap) res->gamma_hist[m] = gam;
             if (trace && res->delta_hist && m < res->trace_cap) res->delta_hist[m] = dm;
@@ -400,16 +470,16 @@ static int plcg_segment(const orc_op *A, double *x, const double *r, double rn,
                 for (int q = 0; q < w->W; ++q) res->g_hist[c * w->W + q] = w->gband[c * w->W + q];
         }
 
-        /* ---- K5 (line 23): g_{j,i+1} with u_{i+1} = z^(l)_{i+1} (M = I).  */
+        /* ---- K5: g_{j,i+1} = (u_{i+1}, z^(0)_j) / (u_{i+1}, z^(l)_j). */
         {
             const int64_t c1 = i + 1;
             const int64_t j0 = P->dots_2l1 ? ((i - 2 * l + 1 > 0) ? i - 2 * l + 1 : 0) : i - l + 1;
             for (int64_t j = (j0 > 0 ? j0 : 0); j <= i - l + 1; ++j) {
-                *Gp(w, j, c1) = dot(n, zl_new, Z(w, 0, j));
+                *Gp(w, j, c1) = dot(n, u_new, Z(w, 0, j));
                 res->dots++;
             }
             for (int64_t j = (i - l + 2 > 0 ? i - l + 2 : 0); j <= i + 1; ++j) {
-                *Gp(w, j, c1) = dot(n, zl_new, Z(w, l, j));
+                *Gp(w, j, c1) = dot(n, u_new, Z(w, l, j));
                 res->dots++;
             }
             if (trace && res->graw_hist && c1 < res->trace_cap)
@@ -434,7 +504,7 @@ static int plcg_segment(const orc_op *A, double *x, const double *r, double rn,
                 }
         }
 
-        /* ---- K6 (lines 24-33): D-Lanczos update, Sec. 2.1. */
+        /* ---- K6: D-Lanczos update, Sec. 2.1. */
         if (i == l) {
             w->eta[0] = w->gamma[0];
             w->zeta[0] = rn;
@@ -478,13 +548,15 @@ static int solve(int method, const orc_op *A, const double *b, double *x,
     res->recursive_relres = res->true_relres = 0.0;
 
     double *r = (double *)malloc((size_t)n * sizeof(double));
-    double *work = (double *)malloc((size_t)(2 * n) * sizeof(double));
+    double *work = (double *)malloc((size_t)(3 * n) * sizeof(double));
+    double *minv = P->precond ? (double *)malloc((size_t)n * sizeof(double)) : NULL;
     plcg_ws w;
     memset(&w, 0, sizeof(w));
     if (method == 1) {
         w.n = n; w.l = l; w.R = l + 2; w.W = 2 * l + 1;
         w.ncols = P->maxit + 2 * (int64_t)l + 4;
         w.zbuf = (double *)malloc((size_t)((l + 1) * w.R) * (size_t)n * sizeof(double));
+        if (P->precond) w.ubuf = (double *)malloc((size_t)w.R * (size_t)n * sizeof(double));
         w.gband = (double *)malloc((size_t)(w.ncols * w.W) * sizeof(double));
         w.gamma = (double *)calloc((size_t)w.ncols, sizeof(double));
         w.delta = (double *)calloc((size_t)w.ncols, sizeof(double));
@@ -492,12 +564,15 @@ static int solve(int method, const orc_op *A, const double *b, double *x,
         w.zeta = (double *)calloc((size_t)w.ncols, sizeof(double));
     }
     int status = ORC_OK;
-    if (!r || !work || (method == 1 && (!w.zbuf || !w.gband || !w.gamma || !w.delta || !w.eta || !w.zeta))) {
+    if (!r || !work || (P->precond && !minv) ||
+        (method == 1 && (!w.zbuf || !w.gband || !w.gamma || !w.delta || !w.eta || !w.zeta ||
+                         (P->precond && !w.ubuf)))) {
         status = ORC_ERR_NOMEM;
         goto done;
     }
+    if (P->precond && jacobi_minv(A, minv) != 0) { status = ORC_ERR_INVALID; goto done; }
 
-    const double normb = nrm2(n, b);
+    const double normb = mnorm(n, b, minv);   /* R7: the natural norm */
     if (normb == 0.0) {
         memset(x, 0, (size_t)n * sizeof(double));
         res->status = ORC_OK;
@@ -507,7 +582,7 @@ static int solve(int method, const orc_op *A, const double *b, double *x,
     const double tau_abs = P->rtol * normb;
     int last_end = SEG_CONVERGED;
     for (;;) {
-        const double rn = residual(A, b, x, r, res);
+        const double rn = residual(A, b, x, r, minv, res);
         res->true_relres = rn / normb;
         if (!isfinite(rn)) { status = ORC_ERR_NONFINITE; break; }
         if (rn < tau_abs) { status = ORC_OK; break; }
@@ -522,14 +597,14 @@ static int solve(int method, const orc_op *A, const double *b, double *x,
         seg_out so;
         const int trace = (res->segments == 0);
         const int64_t budget = P->maxit - res->iters;
-        if (method == 0) cg_segment(A, x, r, tau_abs, budget, work, res, trace, &so);
-        else plcg_segment(A, x, r, rn, P, tau_abs, budget, &w, work, res, trace, &so);
+        if (method == 0) cg_segment(A, x, r, minv, tau_abs, budget, work, res, trace, &so);
+        else plcg_segment(A, x, r, rn, minv, P, tau_abs, budget, &w, work, res, trace, &so);
         res->segments++;
         res->iters += so.k;
         last_end = so.end;
         if (so.end == SEG_NONFINITE) { status = ORC_ERR_NONFINITE; break; }
         if (so.end == SEG_MAXIT && res->iters >= P->maxit) {
-            const double rn2 = residual(A, b, x, r, res);
+            const double rn2 = residual(A, b, x, r, minv, res);
             res->true_relres = rn2 / normb;
             status = (rn2 < tau_abs) ? ORC_OK : ORC_ERR_MAXIT;
             break;
@@ -539,7 +614,7 @@ static int solve(int method, const orc_op *A, const double *b, double *x,
 
 done:
     res->status = status;
-    free(r); free(work);
+    free(r); free(work); free(minv); free(w.ubuf);
     free(w.zbuf); free(w.gband); free(w.gamma); free(w.delta); free(w.eta); free(w.zeta);
     return status;
 }

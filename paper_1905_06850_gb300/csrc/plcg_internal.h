@@ -7,7 +7,7 @@
 namespace plcg {
 
 constexpr int kMaxL = 8;                  // largest pipeline length l
-constexpr int kMaxDots = 2 * kMaxL + 1;   // dot products per iteration (Alg. 1 line 23)
+constexpr int kMaxDots = 2 * kMaxL + 1;   // dot products per iteration (Algorithm 1, K5)
 constexpr int kBlock = 256;               // threads per CTA of the persistent solver
 constexpr int kNormSlots = 2;             // doubles per CTA in the norm partials
 

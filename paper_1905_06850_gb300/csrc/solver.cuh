@@ -572,9 +572,9 @@ struct GangGroup {
 
 // ------------------------------------------------------------------------
 // Scalar step of iteration i (thread 0 of every CTA; all CTAs compute the
-// same bits).  K2: finalise column c = i-l+1 of G (Alg. 1 lines 9-10);
-// line 11: breakdown check; K3: gamma_{i-l}, delta_{i-l} (lines 12-18);
-// K6 scalars: lambda, eta, zeta and the stop test (lines 24-33).
+// same bits).  K2: finalise column c = i-l+1 of G (Algorithm 1)
+// and its breakdown check; K3: gamma_{i-l}, delta_{i-l};
+// K6 scalars: lambda, eta, zeta and the stop test.
 // A dependent FP64 operation costs ~64 cycles on GB300 and a division or a
 // square root ~500, so the step keeps 1/g_{j,j} and 1/eta_m and needs one
 // square root and three reciprocals per iteration (1/g_{c,c} is off the
@@ -720,7 +720,7 @@ __device__ void scalar_step(Smem<T> &s, Coef<T> &cf, const double *raw, const So
             cf.nw[k] = ring(a, k, m + k + 1);
         }
     }
-    // K5 operands: position q is row j = i-2l+1+q of column i+1 (Alg. 1 line 23)
+    // K5 operands: position q is row j = i-2l+1+q of column i+1 (Algorithm 1, K5)
 #pragma unroll
     for (int q = 0; q <= 2 * L; ++q) {
         const long long j = i - 2 * L + 1 + q;
@@ -872,7 +872,7 @@ __device__ void plcg_body(const SolveArgs<T> &a, Smem<T> &s, Grp &grp)
     } while (0)
 
     for (;;) {
-        // ---- true residual r = b - A x and its norm (Alg. 1 line 1 / the final check)
+        // ---- true residual r = b - A x and its norm (Algorithm 1 initialization / the final check)
         residual_sweep<T, VEC, OP>(a, s, grp);
         grp.put_norms(a, s);
         spmvs++;
@@ -907,7 +907,7 @@ __device__ void plcg_body(const SolveArgs<T> &a, Smem<T> &s, Grp &grp)
         const double tau = kF32 ? fmax(a.inner_floor * rn, 0.5 * a.rtol * normb) : a.rtol * normb;
         const long long budget = a.maxit - iters;
 
-        // ---- Alg. 1 line 1: z^(k)_0 := u_0 := r_0 / ||r_0|| for every k; g_00 := 1
+        // ---- Algorithm 1, initialization: z^(k)_0 := u_0 := r_0 / ||r_0|| for every k; g_00 := 1
         {
             const double inv = 1.0 / rn;
             for (int64_t u = grp.unit0(); u < nunits; u += grp.ustep()) {
@@ -1074,7 +1074,7 @@ __device__ void plcg_body(const SolveArgs<T> &a, Smem<T> &s, Grp &grp)
                         for (int v = 0; v < VEC; ++v) un[v] = fma(kc - C.sig, c[r][v], kn * nb[r][v]);
                     } else {
                         // K4: z^(l)_{i+1} = (A z^(l)_i - gamma z^(l)_i - delta' z^(l)_{i-1}) / delta
-                        // and z^(k)_{i-l+k+1}, k < l (Alg. 1 lines 19-21)
+                        // and z^(k)_{i-l+k+1}, k < l (Algorithm 1, K4)
                         const T uc = fma(kc, C.invd, C.al), un_nb = kn * C.invd;
 #pragma unroll
                         for (int v = 0; v < VEC; ++v)
@@ -1087,7 +1087,7 @@ __device__ void plcg_body(const SolveArgs<T> &a, Smem<T> &s, Grp &grp)
                                 nw[k][v] = fma(up, C.invd, fma(C.ak[k], cur[r][k][v], C.bm * pk[r][k][v]));
                             }
                     }
-                    // K6: p and the iterate (Alg. 1 lines 26-31)
+                    // K6: p and the iterate (Algorithm 1, K6)
                     if (C.k6 == 1) {
 #pragma unroll
                         for (int v = 0; v < VEC; ++v) pv[r][v] = C.pv * cur[r][0][v];

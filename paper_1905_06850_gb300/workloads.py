@@ -85,6 +85,23 @@ def shift_interval(op: dict) -> tuple[float, float]:
     return (0.0, float(rowsum.max()))
 
 
+def jacobi_shift_interval(op: dict) -> tuple[float, float]:
+    """The shift interval for the Jacobi-preconditioned operator diag(A)^{-1} A:
+    [0, max_i sum_j |a_ij| / a_ii] (Gershgorin; <= 2 for a diagonally
+    dominant A, the [0, 2] of the paper's preconditioned experiments).
+    Constant-coefficient stencils: shift_interval divided by the center."""
+    if op["kind"] == "stencil":
+        lo, hi = shift_interval(op)
+        return lo / op["center"], hi / op["center"]
+    val, rowptr = op["val"], op["rowptr"]
+    n = op["n"]
+    rows = np.repeat(np.arange(n), np.diff(rowptr))
+    diag = np.zeros(n)
+    np.add.at(diag, rows[op["col"] == rows], val[op["col"] == rows])
+    rowsum = np.add.reduceat(np.abs(val), rowptr[:-1]) if val.size else np.zeros(n)
+    return 0.0, float((rowsum / diag).max())
+
+
 def hetero27_csr(nx: int, ny: int, nz: int, seed: int = 3, sigma: float = 1.0) -> dict:
     """27-point heterogeneous-diffusion SPD operator in CSR.
 

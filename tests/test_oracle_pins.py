@@ -205,7 +205,7 @@ def test_p7_finite_termination_in_high_precision():
 @pytest.mark.parametrize("nx,ny", [(3, 3), (3, 5), (4, 4), (5, 5), (6, 4), (6, 6)])
 @pytest.mark.parametrize("l", [1, 2, 3, 4, 5])
 def test_p7_lucky_breakdown_terminates_in_fp64(nx, ny, l):
-    """Near exact termination the square-root argument of Alg. 1 line 10 goes
+    """Near exact termination the square-root argument of K2 (Algorithm 1) goes
     to zero; the oracle's breakdown handling (R4) must still deliver the
     solution to rtol 1e-12."""
     op = W.stencil2d(nx, ny)
@@ -417,7 +417,7 @@ def test_maxit_and_degenerate_inputs():
 
 
 def test_dot_variants_agree():
-    """The l+1-dot variant (symmetry of G) and the 2l+1 dots of line 23 give
+    """The l+1-dot variant (symmetry of G) and the 2l+1 dots of K5 (Algorithm 1) give
     the same iteration counts and nearly the same x."""
     c = W.config_2d()
     for l in (1, 2, 3, 4):
@@ -426,3 +426,171 @@ def test_dot_variants_agree():
         b = O.plcg(c["op"], c["b"], l=l, sigma=s, rtol=1e-8, dots_2l1=False)
         assert a.iters == b.iters
         assert np.linalg.norm(a.x - b.x) <= 1e-10 * np.linalg.norm(a.x)
+
+
+# ------------------------------------------------- Jacobi preconditioning --
+# Sec. 2.2 "Preconditioned p(l)-CG": Algorithm 1 with M = diag(A), u_i and
+# z^(l)_i kept apart, dots taken with u, the stop test in the natural norm.
+
+def _jacobi_scaled(op):
+    """S A S and S = diag(A)^{-1/2}, formed with scipy.sparse (library)."""
+    import scipy.sparse as sp
+    A = W.to_scipy(op).tocsr()
+    s = 1.0 / np.sqrt(A.diagonal())
+    Ah = (sp.diags(s) @ A @ sp.diags(s)).tocsr()
+    Ah.sort_indices()
+    return {"kind": "csr", "n": A.shape[0], "rowptr": Ah.indptr.astype(np.int64),
+            "col": Ah.indices.astype(np.int32), "val": Ah.data.astype(np.float64)}, s
+
+
+def _jacobi_interval(op):
+    A = W.to_scipy(op).tocsr()
+    return 0.0, float((np.asarray(abs(A).sum(axis=1)).ravel() / A.diagonal()).max())
+
+
+@pytest.mark.parametrize("op", [W.hetero27_csr(5, 5, 5, seed=11), W.random_spd_csr(300, seed=12)],
+                         ids=["h27_5", "rand300"])
+@pytest.mark.parametrize("method", ["cg", "plcg1", "plcg2", "plcg3"])
+def test_j1_jacobi_is_cg_on_the_symmetrically_scaled_system(op, method):
+    """With M = diag(A) = S^{-2}, preconditioned CG / p(l)-CG on (A, b) is
+    the unpreconditioned method on (S A S, S b) with x = S x_hat: the same
+    iteration count, iterates x_k = S x_hat_k and |zeta_k| (the natural norm
+    of the residual equals ||S r||).  The unpreconditioned path is pinned by
+    P1-P13; a dropped M^{-1}, a u/z mix-up in K1, K4 or K5, or a 2-norm stop
+    test breaks this identity."""
+    n = op["n"]
+    b = np.random.default_rng(5).standard_normal(n)
+    oph, s = _jacobi_scaled(op)
+    if method == "cg":
+        r1 = O.cg(op, b, rtol=1e-10, trace_cap=400, precond="jacobi")
+        r2 = O.cg(oph, s * b, rtol=1e-10, trace_cap=400)
+        tol_x = 1e-10
+    else:
+        l = int(method[-1])
+        sig = O.chebyshev_shifts(l, *_jacobi_interval(op))
+        r1 = O.plcg(op, b, l=l, sigma=sig, rtol=1e-10, trace_cap=400, precond="jacobi")
+        r2 = O.plcg(oph, s * b, l=l, sigma=sig, rtol=1e-10, trace_cap=400)
+        tol_x = 1e-6 if l >= 2 else 1e-10
+    assert r1.status == O.ORC_OK and r2.status == O.ORC_OK
+    # near termination a rounding-level difference can turn a lucky breakdown
+    # into a restart; the first segments are compared iterate by iterate
+    assert abs(r1.iters - r2.iters) <= 2
+    xs = np.linalg.norm(r1.x)
+    k = min(r1.trace["len"], r2.trace["len"])
+    assert k >= 10
+    for j in range(k):
+        assert np.linalg.norm(r1.trace["x"][j] - s * r2.trace["x"][j]) <= tol_x * xs, j
+    z1, z2 = np.abs(r1.trace["zeta"][:k]), np.abs(r2.trace["zeta"][:k])
+    # rounding grows along the p(l)-CG recurrences (Sec. 2.2); it is bounded
+    # relative to the initial residual, not to each small late |zeta_k|
+    assert np.all(np.abs(z1 - z2) <= 1e-6 * z1 + 10 * tol_x * z1[0])
+    # both converged to 1e-10 in the same natural norm
+    assert np.linalg.norm(r1.x - s * r2.x) <= 1e-7 * xs
+
+
+@pytest.mark.parametrize("l", [1, 2, 3])
+def test_j2_zeta_is_the_natural_residual_norm(l):
+    """Sec. 2.2 "Residual norm": with a preconditioner, |zeta_j| is
+    sqrt(r_j^T M^{-1} r_j) of the true residual r_j = b - A x_j."""
+    op = W.hetero27_csr(5, 5, 5, seed=21)
+    A = W.to_scipy(op)
+    minv = 1.0 / A.diagonal()
+    b = np.random.default_rng(22).standard_normal(op["n"])
+    sig = O.chebyshev_shifts(l, *_jacobi_interval(op))
+    r = O.plcg(op, b, l=l, sigma=sig, rtol=1e-10, trace_cap=400, precond="jacobi")
+    assert r.status == O.ORC_OK
+    # early iterates: with l >= 2 rounding errors grow along the recurrences
+    # (on this operator by ~8x per iteration for l = 3)
+    for j in range(0, 5):
+        rj = b - A @ r.trace["x"][j]
+        nat = math.sqrt(rj @ (minv * rj))
+        assert abs(abs(r.trace["zeta"][j]) - nat) <= 1e-8 * nat + 1e-10 * abs(r.trace["zeta"][0]), j
+        # and it is not the 2-norm (the operator's diagonal varies)
+        assert abs(nat - np.linalg.norm(rj)) > 1e-3 * nat
+
+
+def test_j3_finite_termination_counts_eigenvalues_of_minv_a():
+    """A = T L T (T diagonal, L the 4x4-grid Laplacian) has distinct
+    eigenvalues, but diag(A)^{-1} A = T^{-1} (L / 4) T has L's 9: the
+    preconditioned methods end in about 9 steps, the plain ones need far
+    more (Saad, Sec. 9.2: PCG minimises over the Krylov space of M^{-1}A)."""
+    import scipy.sparse as sp
+    N = 4
+    Lm = dense(W.stencil2d(N, N))
+    t = np.exp(np.random.default_rng(3).standard_normal(N * N))
+    A = sp.csr_matrix(np.diag(t) @ Lm @ np.diag(t))
+    A.sort_indices()
+    op = {"kind": "csr", "n": N * N, "rowptr": A.indptr.astype(np.int64),
+          "col": A.indices.astype(np.int32), "val": A.data}
+    ev = np.linalg.eigvals(np.diag(1.0 / A.diagonal()) @ A.toarray()).real
+    assert len(np.unique(np.round(ev, 8))) == 9
+    b = np.random.default_rng(4).standard_normal(N * N)
+    rc = O.cg(op, b, rtol=1e-12, precond="jacobi")
+    assert rc.status == O.ORC_OK and rc.iters <= 9
+    assert O.cg(op, b, rtol=1e-12).iters >= 16
+    for l in (1, 2):
+        r = O.plcg(op, b, l=l, sigma=O.chebyshev_shifts(l, 0.0, 2.0), rtol=1e-12, precond="jacobi")
+        assert r.status == O.ORC_OK and r.iters <= 10 and r.true_relres < 1e-12, l
+        ru = O.plcg(op, b, l=l, sigma=O.chebyshev_shifts(l, *W.shift_interval(op)), rtol=1e-12)
+        assert ru.iters >= 16
+
+
+@pytest.mark.parametrize("l", [1, 2, 3])
+def test_j4_diagonal_matrix_is_solved_exactly(l):
+    """M = A for a diagonal A: M^{-1}A = I, the Krylov space has dimension 1
+    and the preconditioned methods return b / diag(A) at once."""
+    n = 50
+    d = np.random.default_rng(9).uniform(0.5, 3.0, n)
+    op = {"kind": "csr", "n": n, "rowptr": np.arange(n + 1, dtype=np.int64),
+          "col": np.arange(n, dtype=np.int32), "val": d}
+    b = np.random.default_rng(10).standard_normal(n)
+    r = O.plcg(op, b, l=l, sigma=O.chebyshev_shifts(l, 0.0, 2.0), rtol=1e-12, precond="jacobi")
+    assert r.status == O.ORC_OK and r.iters <= 2
+    assert np.abs(r.x - b / d).max() <= 1e-14 * np.abs(b / d).max()
+    rc = O.cg(op, b, rtol=1e-12, precond="jacobi")
+    assert rc.status == O.ORC_OK and rc.iters == 1
+    assert np.abs(rc.x - b / d).max() <= 1e-14 * np.abs(b / d).max()
+
+
+@pytest.mark.parametrize("op", [W.hetero27_csr(5, 5, 5, seed=11), W.random_spd_csr(300, seed=12)],
+                         ids=["h27_5", "rand300"])
+def test_j5_jacobi_final_x_vs_dense_cholesky(op):
+    """Final x against scipy's Cholesky solve.  A natural-norm relative
+    residual rho bounds the 2-norm one by sqrt(max d / min d) rho, hence
+    ||x - x*|| / ||x*|| <= kappa sqrt(max d / min d) rho."""
+    A = dense(op)
+    d = np.diag(A)
+    b = np.random.default_rng(5).standard_normal(op["n"])
+    x_chol = scipy.linalg.cho_solve(scipy.linalg.cho_factor(A), b)
+    ev = np.linalg.eigvalsh(A)
+    rtol = 1e-10
+    bound = 1.01 * (ev[-1] / ev[0]) * math.sqrt(d.max() / d.min()) * rtol + 1e-13
+    rc = O.cg(op, b, rtol=rtol, precond="jacobi")
+    assert rc.status == O.ORC_OK
+    assert np.linalg.norm(rc.x - x_chol) / np.linalg.norm(x_chol) <= bound
+    for l in range(1, 5):
+        r = O.plcg(op, b, l=l, sigma=O.chebyshev_shifts(l, *_jacobi_interval(op)), rtol=rtol,
+                   precond="jacobi")
+        assert r.status == O.ORC_OK and r.true_relres < rtol, l
+        assert np.linalg.norm(r.x - x_chol) / np.linalg.norm(x_chol) <= bound, l
+
+
+@pytest.mark.parametrize("l", [1, 3])
+def test_j6_constant_diagonal_changes_nothing(l):
+    """For a constant-coefficient stencil M = c I: every scalar of
+    Algorithm 1 and every iterate equal the unpreconditioned ones."""
+    op = W.stencil2d(15, 11)
+    b = np.random.default_rng(23).standard_normal(op["nx"] * op["ny"])
+    sig = shifts(l, op)
+    r0 = O.plcg(op, b, l=l, sigma=sig, rtol=1e-9)
+    # the spectrum of M^{-1} A is the operator's divided by c = 4
+    r1 = O.plcg(op, b, l=l, sigma=sig / 4.0, rtol=1e-9, precond="jacobi")
+    assert r0.iters == r1.iters
+    assert np.linalg.norm(r0.x - r1.x) <= 1e-11 * np.linalg.norm(r0.x)
+
+
+def test_j7_jacobi_rejects_a_nonpositive_diagonal():
+    op = {"kind": "csr", "n": 2, "rowptr": np.array([0, 1, 2], dtype=np.int64),
+          "col": np.array([0, 1], dtype=np.int32), "val": np.array([1.0, -2.0])}
+    assert O.cg(op, np.ones(2), precond="jacobi").status == O.ORC_ERR_INVALID
+    assert O.plcg(op, np.ones(2), l=1, sigma=[0.5], precond="jacobi").status == O.ORC_ERR_INVALID
