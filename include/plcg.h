@@ -5,8 +5,9 @@
  * Method: Cools, Cornelis, Ghysels, Vanroose, "Improving strong scaling of
  * the Conjugate Gradient method for solving large linear systems using global
  * reduction pipelining", EuroMPI'19 (arXiv:1905.06850), Algorithm 1 with
- * M = I, and classic Hestenes-Stiefel CG (cited and costed in Sec. 1 and
- * Table 1) for comparison.  The problem is A x = b with A sparse symmetric
+ * M = I or the Jacobi preconditioner M = diag(A) (Sec. 2.2, "Preconditioned
+ * p(l)-CG"), and classic Hestenes-Stiefel CG (cited and costed in Sec. 1 and
+ * Table 1; preconditioned alike) for comparison.  The problem is A x = b with A sparse symmetric
  * positive definite (Sec. 2.1).
  *
  * Conventions
@@ -60,6 +61,17 @@ typedef enum {
     PLCG_METHOD_CG = 1          /* classic Hestenes-Stiefel CG                  */
 } plcg_method;
 
+typedef enum {
+    PLCG_PRECOND_NONE = 0,      /* M = I                                         */
+    PLCG_PRECOND_JACOBI = 1     /* M = diag(A); every diagonal entry must be
+                                   positive.  Tolerances then apply to natural
+                                   norms ||v||_{M^{-1}} = sqrt(v^T M^{-1} v)
+                                   (Sec. 2.2, "Residual norm in p(l)-CG"), and
+                                   shifts / [lmin, lmax] describe the spectrum
+                                   of M^{-1} A (inside [0, 2] for a diagonally
+                                   dominant A)                                    */
+} plcg_precond;
+
 /* Opaque matrix handle: operator + its device data + cached workspaces. */
 typedef struct plcg_matrix plcg_matrix;
 
@@ -86,7 +98,8 @@ typedef struct {
                                    or NULL: Chebyshev shifts on [lmin, lmax],
                                    Sec. 2.2 Eq. (chebyshev) (NULL)               */
     double lmin, lmax;          /* spectrum interval for the shifts (0, 8)      */
-    double rtol;                /* stop when ||b - A x|| < rtol ||b|| (1e-8)      */
+    double rtol;                /* stop when ||b - A x|| < rtol ||b|| (1e-8);
+                                   Jacobi: in the natural norm                   */
     int64_t maxit;              /* budget on the iterate index k (100000)        */
     int prec;                   /* plcg_precision (PLCG_FP64)                    */
     int dots_2l1;               /* 1: the 2l+1 dot products of Algorithm 1, K5;
@@ -95,6 +108,7 @@ typedef struct {
     double inner_rtol_floor;    /* FP32 path: floor of the inner relative tolerance
                                    of each refinement step (1e-4) */
     int grid_ctas;              /* 0: choose; else the number of CTAs (tuning)   */
+    int precond;                /* plcg_precond (PLCG_PRECOND_NONE)              */
 } plcg_params;
 
 typedef struct {
@@ -104,7 +118,8 @@ typedef struct {
     int64_t restarts;           /* segments started after the first              */
     int64_t refinements;        /* FP64 outer refinement steps (FP32 path)        */
     double recursive_relres;    /* |zeta_k| / ||b|| at the end of the last segment */
-    double true_relres;         /* ||b - A x|| / ||b||, FP64, at return           */
+    double true_relres;         /* ||b - A x|| / ||b||, FP64, at return (Jacobi:
+                                   both in the natural norm)                      */
     double seconds;             /* device time of the solve (CUDA events)        */
     double latency;             /* serving: seconds from plcg_submit to completion;
                                    other entry points: = seconds                 */
@@ -125,7 +140,10 @@ plcg_status plcg_create_stencil(const plcg_stencil_desc *desc, void *stream,
  * pointers, else host pointers.  prec fixes the stored value type: PLCG_FP64
  * keeps FP64 values; PLCG_FP32_FP64DOT rounds them to FP32 once, and all
  * solves of this matrix (including the FP64 residuals) use those rounded
- * values.  The arrays are copied; the caller may free them on return.
+ * values.  The arrays are copied; the caller may free them on return.  The
+ * diagonal (the sum of a row's entries in column r, in FP64 from the stored
+ * values) and its inverse are formed here for PLCG_PRECOND_JACOBI solves,
+ * which return PLCG_ERR_INVALID if an entry is not positive.
  * Errors: PLCG_ERR_INVALID (n <= 0, n >= 2^31, bad rowptr or col, checked on
  * the host when on_device = 0), PLCG_ERR_NOMEM, PLCG_ERR_CUDA. */
 plcg_status plcg_create_csr(int64_t n, int64_t nnz, const int64_t *rowptr,

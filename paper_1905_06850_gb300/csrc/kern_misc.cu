@@ -8,9 +8,11 @@ const void *kernel_ptr(bool f32, int op, int vec, int l, bool cg)
 {
     if (!f32) {
         if (op == kOpCsr) return kptr_f64_csr(l, cg);
+        if (op == kOpCsrJacobi) return kptr_f64_csrj(l, cg);
         return vec == 2 ? kptr_f64_st2(l, cg) : kptr_f64_st1(l, cg);
     }
     if (op == kOpCsr) return kptr_f32_csr(l, cg);
+    if (op == kOpCsrJacobi) return kptr_f32_csrj(l, cg);
     return vec == 4 ? kptr_f32_st4(l, cg) : kptr_f32_st1(l, cg);
 }
 
@@ -25,6 +27,46 @@ cudaError_t launch_round_to_f32(const double *src, float *dst, int64_t n, cudaSt
 {
     const int64_t blocks = (n + 255) / 256;
     round_to_f32_kernel<<<(unsigned)(blocks < 65535 ? (blocks > 0 ? blocks : 1) : 65535), 256, 0, s>>>(src, dst, n);
+    return cudaGetLastError();
+}
+
+// Jacobi preconditioner data of a CSR matrix (values of type V): d_r = the
+// sum of row r's entries in column r (FP64, in row order), dinv64 = 1 / d_r,
+// and copies of both in V.  *bad is set when some d_r is not positive.
+template <typename V>
+__global__ void jacobi_setup_kernel(const int64_t *rowptr, const int32_t *col, const V *val,
+                                    int64_t n, double *dinv64, V *dinv, V *diag, int *bad)
+{
+    for (int64_t r = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; r < n;
+         r += (int64_t)gridDim.x * blockDim.x) {
+        double d = 0.0;
+        for (int64_t e = rowptr[r]; e < rowptr[r + 1]; ++e)
+            if (col[e] == r) d += (double)val[e];
+        if (!(d > 0.0) || !isfinite(d)) {
+            atomicExch(bad, 1);
+            d = 1.0;
+        }
+        const double di = 1.0 / d;
+        dinv64[r] = di;
+        dinv[r] = (V)di;
+        diag[r] = (V)d;
+    }
+}
+
+cudaError_t launch_jacobi_setup(bool f32, const int64_t *rowptr, const int32_t *col,
+                                const void *val, int64_t n, double *dinv64, void *dinv,
+                                void *diag, int *bad, cudaStream_t s)
+{
+    const int64_t blocks = (n + 255) / 256;
+    const unsigned g = (unsigned)(blocks < 65535 ? (blocks > 0 ? blocks : 1) : 65535);
+    if (f32)
+        jacobi_setup_kernel<float><<<g, 256, 0, s>>>(rowptr, col, static_cast<const float *>(val), n,
+                                                     dinv64, static_cast<float *>(dinv),
+                                                     static_cast<float *>(diag), bad);
+    else
+        jacobi_setup_kernel<double><<<g, 256, 0, s>>>(rowptr, col, static_cast<const double *>(val), n,
+                                                      dinv64, static_cast<double *>(dinv),
+                                                      static_cast<double *>(diag), bad);
     return cudaGetLastError();
 }
 

@@ -78,6 +78,11 @@ struct plcg_matrix {
     int64_t *rowptr = nullptr;
     int32_t *col = nullptr;
     void *val = nullptr;
+    // Jacobi data (CSR): 1 / a_rr in FP64, 1 / a_rr and a_rr in the stored type
+    double *jdinv64 = nullptr;
+    void *jdinv = nullptr;
+    void *jdiag = nullptr;
+    bool jacobi_ok = false;
     cudaStream_t stream = nullptr;
     int device = 0;
     int num_sms = 0;
@@ -104,6 +109,7 @@ extern "C" void plcg_params_default(plcg_params *p)
     p->max_restarts = 8;
     p->inner_rtol_floor = 1e-4;
     p->grid_ctas = 0;
+    p->precond = PLCG_PRECOND_NONE;
 }
 
 static plcg_status matrix_common_init(plcg_matrix *A, void *stream)
@@ -206,6 +212,23 @@ extern "C" plcg_status plcg_create_csr(int64_t n, int64_t nnz, const int64_t *ro
             if (tmp) cudaFree(tmp);
         }
     }
+    // Jacobi preconditioner data (Sec. 2.2): the diagonal and its inverse
+    int *bad = nullptr;
+    if (e == cudaSuccess) e = cudaMalloc(&A->jdinv64, n * sizeof(double));
+    if (e == cudaSuccess) e = cudaMalloc(&A->jdiag, n * vsz);
+    if (e == cudaSuccess) {
+        if (prec == PLCG_FP64) A->jdinv = A->jdinv64;
+        else e = cudaMalloc(&A->jdinv, n * vsz);
+    }
+    if (e == cudaSuccess) e = cudaMalloc(&bad, sizeof(int));
+    if (e == cudaSuccess) e = cudaMemset(bad, 0, sizeof(int));
+    if (e == cudaSuccess)
+        e = launch_jacobi_setup(prec != PLCG_FP64, A->rowptr, A->col, A->val, n, A->jdinv64,
+                                A->jdinv, A->jdiag, bad, nullptr);
+    int hbad = 1;
+    if (e == cudaSuccess) e = cudaMemcpy(&hbad, bad, sizeof(int), cudaMemcpyDeviceToHost);
+    if (bad) cudaFree(bad);
+    A->jacobi_ok = (e == cudaSuccess && hbad == 0);
     if (e != cudaSuccess) {
         plcg_status s2 = fail(e == cudaErrorMemoryAllocation ? PLCG_ERR_NOMEM : PLCG_ERR_CUDA,
                               "csr upload: %s", cudaGetErrorString(e));
@@ -224,6 +247,9 @@ extern "C" void plcg_destroy(plcg_matrix *A)
     cudaFree(A->rowptr);
     cudaFree(A->col);
     cudaFree(A->val);
+    if (A->jdinv != A->jdinv64) cudaFree(A->jdinv);
+    cudaFree(A->jdinv64);
+    cudaFree(A->jdiag);
     cudaFree(A->ws.mem);
     cudaFree(A->b_dev);
     cudaFree(A->x_dev);
@@ -240,6 +266,21 @@ static void chebyshev_shifts(int l, double lmin, double lmax, double *sig)
     const double pi = 3.14159265358979323846;
     for (int i = 0; i < l; ++i)
         sig[i] = 0.5 * (lmax + lmin) + 0.5 * (lmax - lmin) * std::cos((2 * i + 1) * pi / (2.0 * l));
+}
+
+// The shifts of a p(l)-CG solve: prm->shifts, else Chebyshev shifts on
+// [lmin, lmax].  With the Jacobi preconditioner they describe M^{-1} A; for
+// a constant-coefficient stencil M = c I, and the solve runs the
+// unpreconditioned recurrences on A with the shifts scaled by c -- the same
+// iterates and scalars in exact arithmetic, with natural norms that are the
+// 2-norms divided by sqrt(c) on both sides of the stop test.
+static void resolve_shifts(const plcg_matrix *A, const plcg_params *prm, double lmin, double lmax,
+                           double *sigma)
+{
+    if (prm->shifts) std::memcpy(sigma, prm->shifts, prm->l * sizeof(double));
+    else chebyshev_shifts(prm->l, lmin, lmax, sigma);
+    if (prm->precond == PLCG_PRECOND_JACOBI && A->kind == kOpStencil)
+        for (int k = 0; k < prm->l; ++k) sigma[k] *= A->st.center;
 }
 
 static plcg_status ensure_ws(plcg_matrix *A, size_t bytes)
@@ -270,7 +311,8 @@ static plcg_status build_solve(const plcg_matrix *A, const double *b, double *x,
     const int64_t n = A->n;
     const int l = prm->l;
     const bool cg = prm->method == PLCG_METHOD_CG;
-    const int op = A->kind;
+    const bool jac = prm->precond == PLCG_PRECOND_JACOBI && A->kind == kOpCsr;
+    const int op = jac ? (int)kOpCsrJacobi : A->kind;
     const bool f32 = sizeof(T) == 4;
     int vec = 1;
     if (op == kOpStencil) {
@@ -330,6 +372,11 @@ static plcg_status build_solve(const plcg_matrix *A, const double *b, double *x,
     a.csr.rowptr = A->rowptr;
     a.csr.col = A->col;
     a.csr.val = A->val;
+    if (jac) {
+        a.csr.dinv = A->jdinv;
+        a.csr.diag = A->jdiag;
+        a.dinv64 = A->jdinv64;
+    }
     a.b = b;
     a.x = x;
     a.r = reinterpret_cast<double *>(base + o_r);
@@ -441,6 +488,14 @@ static plcg_status check_params(const plcg_matrix *A, const plcg_params *p)
         return fail(PLCG_ERR_INVALID, "CSR matrix was created for precision %d", A->csr_prec);
     if (p->prec == PLCG_FP32_FP64DOT && !(p->inner_rtol_floor > 0.0 && p->inner_rtol_floor < 1.0))
         return fail(PLCG_ERR_INVALID, "inner_rtol_floor must be in (0, 1)");
+    if (p->precond != PLCG_PRECOND_NONE && p->precond != PLCG_PRECOND_JACOBI)
+        return fail(PLCG_ERR_INVALID, "unknown preconditioner %d", p->precond);
+    if (p->precond == PLCG_PRECOND_JACOBI) {
+        if (A->kind == kOpCsr && !A->jacobi_ok)
+            return fail(PLCG_ERR_INVALID, "Jacobi preconditioner: a diagonal entry is not positive");
+        if (A->kind == kOpStencil && !(A->st.center > 0.0))
+            return fail(PLCG_ERR_INVALID, "Jacobi preconditioner: the stencil center is not positive");
+    }
     if (p->method == PLCG_METHOD_PLCG) {
         if (p->shifts) {
             for (int k = 0; k < p->l; ++k)
@@ -461,10 +516,7 @@ extern "C" plcg_status plcg_solve(plcg_matrix *A, const double *b, double *x,
     if ((reinterpret_cast<uintptr_t>(b) | reinterpret_cast<uintptr_t>(x)) & 15)
         return fail(PLCG_ERR_INVALID, "b and x must be 16-byte aligned");
     double sigma[kMaxL] = {0};
-    if (prm->method == PLCG_METHOD_PLCG) {
-        if (prm->shifts) std::memcpy(sigma, prm->shifts, prm->l * sizeof(double));
-        else chebyshev_shifts(prm->l, prm->lmin, prm->lmax, sigma);
-    }
+    if (prm->method == PLCG_METHOD_PLCG) resolve_shifts(A, prm, prm->lmin, prm->lmax, sigma);
     std::lock_guard<std::mutex> lock(A->mu);
     CUDA_TRY(cudaSetDevice(A->device));
     if (prm->prec == PLCG_FP64) return run_solve<double>(A, b, x, prm, sigma, res);
@@ -584,14 +636,10 @@ static plcg_status run_batched(int count, plcg_matrix *const *A, const double *c
         y.out = nullptr;
         std::memset(y.sigma, 0, sizeof(y.sigma));
         if (!cg) {
-            if (prm->shifts) {
-                for (int k = 0; k < l; ++k) y.sigma[k] = prm->shifts[k];
-            } else {
-                const double lo = lmin ? lmin[i] : prm->lmin, hi = lmax ? lmax[i] : prm->lmax;
-                if (!std::isfinite(lo) || !std::isfinite(hi) || hi < lo)
-                    return fail(PLCG_ERR_INVALID, "system %d: need lmin <= lmax", i);
-                chebyshev_shifts(l, lo, hi, y.sigma);
-            }
+            const double lo = lmin ? lmin[i] : prm->lmin, hi = lmax ? lmax[i] : prm->lmax;
+            if (!prm->shifts && (!std::isfinite(lo) || !std::isfinite(hi) || hi < lo))
+                return fail(PLCG_ERR_INVALID, "system %d: need lmin <= lmax", i);
+            resolve_shifts(M, prm, lo, hi, y.sigma);
         }
         work[i] = stencil_work(M);
         wsum += work[i];
@@ -751,6 +799,8 @@ extern "C" plcg_status plcg_solve_batched(int count, plcg_matrix *const *A, cons
             return fail(PLCG_ERR_UNIMPL, "plcg_solve_batched: system %d is not a stencil operator", i);
         if (A[i]->device != A[0]->device)
             return fail(PLCG_ERR_INVALID, "plcg_solve_batched: systems on different devices");
+        if (prm && prm->precond == PLCG_PRECOND_JACOBI && !(A[i]->st.center > 0.0))
+            return fail(PLCG_ERR_INVALID, "system %d: Jacobi needs a positive stencil center", i);
     }
     plcg_status st = check_params(A[0], prm);
     if (st != PLCG_OK) return st;
@@ -963,10 +1013,8 @@ extern "C" plcg_status plcg_submit(plcg_server *S, plcg_matrix *A, const double 
         if (prm->shifts) {
             std::memcpy(q->shifts, prm->shifts, prm->l * sizeof(double));
             q->prm.shifts = q->shifts;
-            std::memcpy(q->sigma, prm->shifts, prm->l * sizeof(double));
-        } else {
-            chebyshev_shifts(prm->l, prm->lmin, prm->lmax, q->sigma);
         }
+        resolve_shifts(A, &q->prm, prm->lmin, prm->lmax, q->sigma);
     }
     // per-request grid cap: at most half of the GPU's resident CTAs, so large
     // requests never lock small ones out

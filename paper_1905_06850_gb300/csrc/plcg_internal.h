@@ -11,7 +11,8 @@ constexpr int kMaxDots = 2 * kMaxL + 1;   // dot products per iteration (Algorit
 constexpr int kBlock = 256;               // threads per CTA of the persistent solver
 constexpr int kNormSlots = 2;             // doubles per CTA in the norm partials
 
-enum OpKind : int { kOpStencil = 0, kOpCsr = 1 };
+// kOpCsrJacobi: CSR with the Jacobi preconditioner M = diag(A) (Sec. 2.2).
+enum OpKind : int { kOpStencil = 0, kOpCsr = 1, kOpCsrJacobi = 2 };
 
 // End reasons of one segment (a run of Algorithm 1 from a residual).
 enum SegEnd : int { kSegConverged = 0, kSegMaxit = 1, kSegBreakdown = 2, kSegLucky = 3,
@@ -56,11 +57,14 @@ struct StencilDesc {
     FastDivU32 dnx, dny;   // division by nx and by ny
 };
 
-// CSR arrays in device memory; val is float or double (see the kernel's T).
+// CSR arrays in device memory; val, dinv and diag are float or double (the
+// kernel's T).  dinv / diag (1 / a_rr and a_rr) are set for kOpCsrJacobi.
 struct CsrDesc {
     const int64_t *rowptr;
     const int32_t *col;
     const void *val;
+    const void *dinv;
+    const void *diag;
 };
 
 // Everything one persistent solve needs (passed by value to the kernel).
@@ -71,6 +75,7 @@ struct SolveArgs {
     CsrDesc csr;
     const double *b;          // FP64 right-hand side
     double *x;                // FP64 iterate (in: x0)
+    const double *dinv64;     // kOpCsrJacobi: FP64 1 / a_rr (natural norms, M^{-1} r)
     double *r;                // FP64 residual b - A x
     T *zring;                 // ring storage of the l+1 bases (p(l)-CG) / p ring (CG)
     int depth[kMaxL + 1];     // ring depth of basis k

@@ -23,9 +23,18 @@ const void *kptr_f64_csr(int l, bool cg);
 const void *kptr_f32_st4(int l, bool cg);
 const void *kptr_f32_st1(int l, bool cg);
 const void *kptr_f32_csr(int l, bool cg);
+const void *kptr_f64_csrj(int l, bool cg);
+const void *kptr_f32_csrj(int l, bool cg);
 
 // Sets the thread-local message returned by plcg_last_error().
 void set_last_error(const std::string &msg);
+
+// Jacobi data of a CSR matrix: dinv64 = 1 / diag (FP64), dinv and diag in
+// the stored value type (float if f32); *bad = 1 if a diagonal entry is not
+// positive.
+cudaError_t launch_jacobi_setup(bool f32, const int64_t *rowptr, const int32_t *col,
+                                const void *val, int64_t n, double *dinv64, void *dinv,
+                                void *diag, int *bad, cudaStream_t s);
 
 // dst[i] = (float) src[i] on the device.
 cudaError_t launch_round_to_f32(const double *src, float *dst, int64_t n, cudaStream_t s);

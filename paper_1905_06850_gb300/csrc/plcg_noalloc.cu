@@ -183,6 +183,10 @@ extern "C" plcg_status plcg_solve_stencil_noalloc(const plcg_stencil_desc *d, co
         return nafail(PLCG_ERR_INVALID, "unknown precision");
     if (prm->prec == PLCG_FP32_FP64DOT && !(prm->inner_rtol_floor > 0.0 && prm->inner_rtol_floor < 1.0))
         return nafail(PLCG_ERR_INVALID, "inner_rtol_floor must be in (0, 1)");
+    if (prm->precond != PLCG_PRECOND_NONE && prm->precond != PLCG_PRECOND_JACOBI)
+        return nafail(PLCG_ERR_INVALID, "unknown preconditioner");
+    if (prm->precond == PLCG_PRECOND_JACOBI && !(d->center + d->diag_shift > 0.0))
+        return nafail(PLCG_ERR_INVALID, "Jacobi preconditioner: the stencil center is not positive");
     if ((reinterpret_cast<uintptr_t>(b) | reinterpret_cast<uintptr_t>(x)) & 15)
         return nafail(PLCG_ERR_INVALID, "b and x must be 16-byte aligned");
     double sigma[kMaxL] = {0};
@@ -200,6 +204,10 @@ extern "C" plcg_status plcg_solve_stencil_noalloc(const plcg_stencil_desc *d, co
                 sigma[i] = 0.5 * (prm->lmax + prm->lmin) +
                            0.5 * (prm->lmax - prm->lmin) * std::cos((2 * i + 1) * pi / (2.0 * prm->l));
         }
+        // Jacobi on a constant-coefficient stencil: M = c I, so the shifts of
+        // M^{-1} A become shifts of A scaled by c (same iterates)
+        if (prm->precond == PLCG_PRECOND_JACOBI)
+            for (int k = 0; k < prm->l; ++k) sigma[k] *= d->center + d->diag_shift;
     }
     int dev = 0;
     cudaError_t e = cudaGetDevice(&dev);

@@ -789,7 +789,9 @@ struct DotAcc {
 
 // ------------------------------------------------------------------------
 // Residual sweep: r = b - A x (FP64; the stored operator values widened),
-// this CTA's ||r||^2 and ||b||^2 in s.out[0..1].  Units of kBlock * V64 rows.
+// this CTA's ||r||^2 and ||b||^2 in s.out[0..1] -- with the Jacobi
+// preconditioner the natural norms r^T M^{-1} r and b^T M^{-1} b (Sec. 2.2,
+// "Residual norm in p(l)-CG").  Units of kBlock * V64 rows.
 // ------------------------------------------------------------------------
 template <typename T, int VEC, int OP, class Grp>
 __device__ void residual_sweep(const SolveArgs<T> &a, Smem<T> &s, const Grp &grp)
@@ -816,8 +818,14 @@ __device__ void residual_sweep(const SolveArgs<T> &a, Smem<T> &s, const Grp &grp
 #pragma unroll
         for (int v = 0; v < V64; ++v) {
             rv[v] = bv[v] - w[v];
-            acc[0] = fma(bv[v], bv[v], acc[0]);
-            acc[1] = fma(rv[v], rv[v], acc[1]);
+            if constexpr (OP == kOpCsrJacobi) {
+                const double mi = __ldg(a.dinv64 + g0 + v);
+                acc[0] = fma(bv[v] * mi, bv[v], acc[0]);
+                acc[1] = fma(rv[v] * mi, rv[v], acc[1]);
+            } else {
+                acc[0] = fma(bv[v], bv[v], acc[0]);
+                acc[1] = fma(rv[v], rv[v], acc[1]);
+            }
         }
         vst<double, V64>(a.r + g0, rv);
     }
@@ -907,7 +915,8 @@ __device__ void plcg_body(const SolveArgs<T> &a, Smem<T> &s, Grp &grp)
         const double tau = kF32 ? fmax(a.inner_floor * rn, 0.5 * a.rtol * normb) : a.rtol * normb;
         const long long budget = a.maxit - iters;
 
-        // ---- Algorithm 1, initialization: z^(k)_0 := u_0 := r_0 / ||r_0|| for every k; g_00 := 1
+        // ---- Algorithm 1, initialization: z^(k)_0 := M^{-1} r_0 / nu for every
+        // k, nu = sqrt((r_0, M^{-1} r_0)); u_0 = M z^(l)_0 is never stored; g_00 := 1
         {
             const double inv = 1.0 / rn;
             for (int64_t u = grp.unit0(); u < nunits; u += grp.ustep()) {
@@ -915,7 +924,12 @@ __device__ void plcg_body(const SolveArgs<T> &a, Smem<T> &s, Grp &grp)
                 if (g0 >= n) continue;
                 T z[VEC];
 #pragma unroll
-                for (int v = 0; v < VEC; ++v) z[v] = (T)(a.r[g0 + v] * inv);
+                for (int v = 0; v < VEC; ++v) {
+                    if constexpr (OP == kOpCsrJacobi)
+                        z[v] = (T)(a.r[g0 + v] * __ldg(a.dinv64 + g0 + v) * inv);
+                    else
+                        z[v] = (T)(a.r[g0 + v] * inv);
+                }
 #pragma unroll
                 for (int k = 0; k <= L; ++k) vst<T, VEC>(ring(a, k, 0) + g0, z);
                 if constexpr (kF32) {
@@ -1038,12 +1052,19 @@ __device__ void plcg_body(const SolveArgs<T> &a, Smem<T> &s, Grp &grp)
                 // -- loads
                 T c[RPT][VEC], nb[RPT][VEC], zp[RPT][VEC], cur[RPT][L][VEC], pk[RPT][L][VEC];
                 T pv[RPT][VEC], xv[RPT][VEC];
+                T dg[RPT];   // Jacobi: a_gg, for u_{i+1} = M z^(l)_{i+1}
 #pragma unroll
                 for (int r = 0; r < RPT; ++r) {
 #pragma unroll
                     for (int v = 0; v < VEC; ++v) zp[r][v] = T(0);
+                    dg[r] = T(1);
                     if (!ok[r]) continue;
                     op_parts<T, T, VEC, OP>(st, csr, Ld1<T>{C.zl_cur}, g0[r], c[r], nb[r]);   // K1 operands
+                    if constexpr (OP == kOpCsrJacobi) {
+                        // K1 with M = diag(A): z^(l)_{i+1} is built from M^{-1} A z^(l)_i
+                        nb[r][0] *= __ldg(static_cast<const T *>(csr.dinv) + g0[r]);
+                        dg[r] = __ldg(static_cast<const T *>(csr.diag) + g0[r]);
+                    }
                     if (rec) {
                         vld<T, VEC>(C.zl_prev + g0[r], zp[r]);
 #pragma unroll
@@ -1108,7 +1129,11 @@ __device__ void plcg_body(const SolveArgs<T> &a, Smem<T> &s, Grp &grp)
                     }
                     if (C.k6 >= 1) vst<T, VEC>(pvec + g0[r], pv[r]);
                     if (C.k6 == 2) vst<T, VEC>(xi + g0[r], xv[r]);
-                    // -- K5: partial dot products with u_{i+1} = z^(l)_{i+1}
+                    // -- K5: partial dot products with u_{i+1} = M z^(l)_{i+1}
+                    // (M = I: z^(l)_{i+1} itself)
+                    T uM[VEC];
+#pragma unroll
+                    for (int v = 0; v < VEC; ++v) uM[v] = (OP == kOpCsrJacobi) ? un[v] * dg[r] : un[v];
 #pragma unroll
                     for (int q = 0; q <= 2 * L; ++q) {
                         const int src = C.dsrc[q];
@@ -1122,7 +1147,7 @@ __device__ void plcg_body(const SolveArgs<T> &a, Smem<T> &s, Grp &grp)
                                 o[v] = (src == 2) ? un[v] : (src == 3) ? nw[0][v] : (src == 4) ? c[r][v]
                                      : zp[r][v];
                         }
-                        dac[q].add(un, o);
+                        dac[q].add(uM, o);
                     }
                 }
                 if (++since_flush == kFlushUnits) {
@@ -1162,7 +1187,9 @@ finish:
 
 // ------------------------------------------------------------------------
 // Classic CG (Hestenes-Stiefel) on one group: two synchronisations per
-// iteration (after (p, Ap) and after (r, r)).  p lives in a ring of two
+// iteration (after (p, Ap) and after (r, r)).  With the Jacobi preconditioner
+// (kOpCsrJacobi) the recursive vector is z = M^{-1} r instead of r: q holds
+// M^{-1} A p, z -= alpha q, and rho = (r, z) = sum a_gg z_g^2.  p lives in a ring of two
 // vectors because the SpMV of step k reads neighbours of p_{k-1} while p_k is
 // written.  q = A p is in a.p; the recursive residual is r itself on the FP64
 // path and a.rc (FP32) on the FP32 path, whose inner iterate is the ring's
@@ -1233,18 +1260,25 @@ __device__ void cg_body(const SolveArgs<T> &a, Smem<T> &s, Grp &grp)
         const long long budget = a.maxit - iters;
         double rr = rn * rn;
         if constexpr (kF32) {
-            // rc = (float) r, d = 0, rr from the rounded values
+            // rc = (float) r (Jacobi: (float) M^{-1} r), d = 0, rr from the
+            // rounded values
             DotAcc<T, VEC> d0;
             for (int64_t u = grp.unit0(); u < nunits; u += grp.ustep()) {
                 const int64_t g0 = u * UNIT + (int64_t)tid * VEC;
                 if (g0 >= n) continue;
-                T z[VEC], zero[VEC];
+                T z[VEC], zero[VEC], zm[VEC];
 #pragma unroll
                 for (int v = 0; v < VEC; ++v) {
-                    z[v] = (T)a.r[g0 + v];
+                    if constexpr (OP == kOpCsrJacobi) {
+                        z[v] = (T)(a.r[g0 + v] * __ldg(a.dinv64 + g0 + v));
+                        zm[v] = z[v] * __ldg(static_cast<const T *>(csr.diag) + g0 + v);
+                    } else {
+                        z[v] = (T)a.r[g0 + v];
+                        zm[v] = z[v];
+                    }
                     zero[v] = T(0);
                 }
-                d0.add(z, z);
+                d0.add(zm, z);
                 d0.flush();
                 vst<T, VEC>(rc + g0, z);
                 vst<T, VEC>(xi + g0, zero);
@@ -1255,6 +1289,13 @@ __device__ void cg_body(const SolveArgs<T> &a, Smem<T> &s, Grp &grp)
             CG_SYNC();
             grp.template get_dots<1>(a, s, 0, s.raw);
             rr = s.raw[0];
+        } else if constexpr (OP == kOpCsrJacobi) {
+            // FP64 path: z = M^{-1} r in r's place; rr = (r, M^{-1} r) = rn^2
+            for (int64_t u = grp.unit0(); u < nunits; u += grp.ustep()) {
+                const int64_t g = u * UNIT + (int64_t)tid;
+                if (g < n) a.r[g] *= __ldg(a.dinv64 + g);
+            }
+            CG_SYNC();
         }
         long long k = 0;
         int end;
@@ -1270,7 +1311,7 @@ __device__ void cg_body(const SolveArgs<T> &a, Smem<T> &s, Grp &grp)
             int since_flush = 0;
             const int64_t nunits_s = (n + USWEEP - 1) / USWEEP;
             for (int64_t u = grp.unit0(); u < nunits_s; u += grp.ustep()) {
-                T c[RPT][VEC], w[RPT][VEC];
+                T c[RPT][VEC], w[RPT][VEC], mi[RPT];
                 int64_t g0[RPT];
 #pragma unroll
                 for (int r = 0; r < RPT; ++r) {
@@ -1280,13 +1321,16 @@ __device__ void cg_body(const SolveArgs<T> &a, Smem<T> &s, Grp &grp)
                         op_apply<T, T, VEC, OP>(st, csr, cC, cO, LdFirst<T>{rc}, g0[r], c[r], w[r]);
                     else
                         op_apply<T, T, VEC, OP>(st, csr, cC, cO, LdAxpy<T>{rc, po, (T)beta}, g0[r], c[r], w[r]);
+                    if constexpr (OP == kOpCsrJacobi)
+                        mi[r] = __ldg(static_cast<const T *>(csr.dinv) + g0[r]);
                 }
 #pragma unroll
                 for (int r = 0; r < RPT; ++r) {
                     if (g0[r] >= n) continue;
                     vst<T, VEC>(pn + g0[r], c[r]);
-                    vst<T, VEC>(q + g0[r], w[r]);
                     d1.add(c[r], w[r]);
+                    if constexpr (OP == kOpCsrJacobi) w[r][0] *= mi[r];   // q = M^{-1} A p
+                    vst<T, VEC>(q + g0[r], w[r]);
                 }
                 if (++since_flush == kFlushUnits) { d1.flush(); since_flush = 0; }
             }
@@ -1305,7 +1349,7 @@ __device__ void cg_body(const SolveArgs<T> &a, Smem<T> &s, Grp &grp)
             DotAcc<T, VEC> d2;
             since_flush = 0;
             for (int64_t u = grp.unit0(); u < nunits_s; u += grp.ustep()) {
-                T pv[RPT][VEC], qv[RPT][VEC], xv[RPT][VEC], rv[RPT][VEC];
+                T pv[RPT][VEC], qv[RPT][VEC], xv[RPT][VEC], rv[RPT][VEC], dv[RPT][VEC];
                 int64_t g0[RPT];
 #pragma unroll
                 for (int r = 0; r < RPT; ++r) {
@@ -1315,6 +1359,8 @@ __device__ void cg_body(const SolveArgs<T> &a, Smem<T> &s, Grp &grp)
                     vld<T, VEC>(q + g0[r], qv[r]);
                     vld<T, VEC>(xi + g0[r], xv[r]);
                     vld<T, VEC>(rc + g0[r], rv[r]);
+                    if constexpr (OP == kOpCsrJacobi)
+                        vldg<T, VEC>(static_cast<const T *>(csr.diag) + g0[r], dv[r]);
                 }
 #pragma unroll
                 for (int r = 0; r < RPT; ++r) {
@@ -1326,7 +1372,13 @@ __device__ void cg_body(const SolveArgs<T> &a, Smem<T> &s, Grp &grp)
                     }
                     vst<T, VEC>(xi + g0[r], xv[r]);
                     vst<T, VEC>(rc + g0[r], rv[r]);
-                    d2.add(rv[r], rv[r]);
+                    if constexpr (OP == kOpCsrJacobi) {   // rho = (r, z) = sum a_gg z_g^2
+#pragma unroll
+                        for (int v = 0; v < VEC; ++v) dv[r][v] *= rv[r][v];
+                        d2.add(dv[r], rv[r]);
+                    } else {
+                        d2.add(rv[r], rv[r]);
+                    }
                 }
                 if (++since_flush == kFlushUnits) { d2.flush(); since_flush = 0; }
             }

@@ -38,6 +38,8 @@ PLCG_FP64 = 0
 PLCG_FP32_FP64DOT = 1
 PLCG_METHOD_PLCG = 0
 PLCG_METHOD_CG = 1
+PLCG_PRECOND_NONE = 0
+PLCG_PRECOND_JACOBI = 1
 
 
 class plcg_stencil_desc(C.Structure):
@@ -51,7 +53,7 @@ class plcg_params(C.Structure):
                 ("lmin", C.c_double), ("lmax", C.c_double), ("rtol", C.c_double),
                 ("maxit", C.c_int64), ("prec", C.c_int), ("dots_2l1", C.c_int),
                 ("max_restarts", C.c_int), ("inner_rtol_floor", C.c_double),
-                ("grid_ctas", C.c_int)]
+                ("grid_ctas", C.c_int), ("precond", C.c_int)]
 
 
 class plcg_result(C.Structure):
@@ -153,7 +155,7 @@ def _result(r: plcg_result) -> Result:
 
 def make_params(method="plcg", l=1, shifts=None, interval=(0.0, 8.0), rtol=1e-8, maxit=100000,
                 prec="fp64", dots_2l1=False, max_restarts=8, inner_rtol_floor=1e-4,
-                grid_ctas=0):
+                grid_ctas=0, precond=None):
     p = plcg_params()
     load().plcg_params_default(C.byref(p))
     p.method = PLCG_METHOD_CG if method == "cg" else PLCG_METHOD_PLCG
@@ -170,6 +172,9 @@ def make_params(method="plcg", l=1, shifts=None, interval=(0.0, 8.0), rtol=1e-8,
     p.max_restarts = int(max_restarts)
     p.inner_rtol_floor = float(inner_rtol_floor)
     p.grid_ctas = int(grid_ctas)
+    if precond not in (None, "none", "jacobi"):
+        raise ValueError(f"unknown preconditioner {precond!r}")
+    p.precond = PLCG_PRECOND_JACOBI if precond == "jacobi" else PLCG_PRECOND_NONE
     return p, keep
 
 

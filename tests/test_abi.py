@@ -40,6 +40,37 @@ def test_params_default(lib):
     lib.plcg_params_default(C.byref(p))
     assert p.l == 1 and p.rtol == 1e-8 and p.maxit == 100000 and p.max_restarts == 8
     assert p.prec == plcg.PLCG_FP64 and p.dots_2l1 == 0 and abs(p.inner_rtol_floor - 1e-4) < 1e-20
+    assert p.precond == plcg.PLCG_PRECOND_NONE and p.grid_ctas == 0
+
+
+def test_struct_layouts_match_header(tmp_path):
+    """The ctypes structs have the sizes and field offsets gcc gives the
+    header's structs."""
+    import shutil
+    import subprocess
+    if not shutil.which("gcc"):
+        pytest.skip("gcc not available")
+    structs = {"plcg_params": plcg.plcg_params, "plcg_result": plcg.plcg_result,
+               "plcg_stencil_desc": plcg.plcg_stencil_desc}
+    lines = ['#include <stdio.h>', '#include <stddef.h>', '#include "plcg.h"', 'int main(void) {']
+    for name, st in structs.items():
+        lines.append(f'printf("{name} %zu\\n", sizeof({name}));')
+        for fname, _ in st._fields_:
+            lines.append(f'printf("{name}.{fname} %zu\\n", offsetof({name}, {fname}));')
+    lines.append("return 0; }")
+    src = tmp_path / "layout.c"
+    src.write_text("\n".join(lines))
+    exe = tmp_path / "layout"
+    inc = os.path.join(os.path.dirname(os.path.dirname(os.path.abspath(__file__))), "include")
+    subprocess.run(["gcc", "-I", inc, str(src), "-o", str(exe)], check=True)
+    got = dict(line.split() for line in subprocess.run([str(exe)], capture_output=True, text=True,
+                                                       check=True).stdout.splitlines())
+    for name, st in structs.items():
+        assert int(got[name]) == C.sizeof(st), name
+        for fname, _ in st._fields_:
+            assert int(got[f"{name}.{fname}"]) == getattr(st, fname).offset, (name, fname)
+    with pytest.raises(ValueError):
+        plcg.make_params(precond="ilu")
 
 
 @pytest.mark.parametrize("dim,points,nx,ny,nz", [(2, 7, 4, 4, 1), (3, 5, 4, 4, 4), (2, 5, 0, 4, 1),
