@@ -336,8 +336,8 @@ def run_ours(args):
 
 def other_configs(plcg, W, dev, hbm_peak):
     """Time-to-rtol on the other workloads: the 2D 100^2 Laplacian (FP64,
-    latency-bound), the 27-point heterogeneous CSR on 128^3 (FP32 with FP64
-    correction) and the batch of 4096 shifted 2D Poisson systems (FP32 with
+    latency-bound), the diagonal toy of Sec. 4 (100^2 and 2000^2), the 27-point heterogeneous CSR on 128^3 (FP32 with FP64
+    correction; unpreconditioned and with Jacobi) and the batch of 4096 shifted 2D Poisson systems (FP32 with
     FP64 correction, one persistent launch), each against classic CG."""
     import torch
     out = {}
@@ -357,6 +357,25 @@ def other_configs(plcg, W, dev, hbm_peak):
                    "us_per_iter": round(min(ts) / r.iters * 1e6, 2)}
     A.close()
     out["2d_100_fp64_rtol1e-6"] = d
+    # ---- the paper's communication-bound toy: diagonal operator with the 2D
+    # Laplacian's eigenvalues (Sec. 4), 100^2 (barrier-latency bound) and the
+    # paper's 2000^2 = 4M unknowns, FP64, rtol 1e-6
+    for N in (100, 2000):
+        e = W.e3_diagonal(N)
+        A = plcg.Matrix(e["op"])
+        b = torch.tensor(e["b"], device=dev)
+        d = {"n": N * N}
+        for name, kw in (("plcg_l1", {"l": 1}), ("plcg_l2", {"l": 2}), ("plcg_l3", {"l": 3}),
+                         ("classic_cg", {"method": "cg"})):
+            ts = []
+            for _ in range(3 if N == 100 else 2):
+                x = torch.zeros_like(b)
+                r = A.solve(b, x, interval=e["interval"], rtol=e["rtol"], **kw)
+                ts.append(r.seconds)
+            d[name] = {"iters": r.iters, "time_to_rtol_us": round(min(ts) * 1e6, 1),
+                       "us_per_iter": round(min(ts) / r.iters * 1e6, 2)}
+        A.close()
+        out[f"e3_diag_{N}_fp64_rtol1e-6"] = d
     # ---- 27-point heterogeneous CSR 128^3, FP32 vectors/values, FP64 correction
     c = W.config_hetero27(nx=128)
     op = c["op"]
@@ -364,16 +383,22 @@ def other_configs(plcg, W, dev, hbm_peak):
     A = plcg.Matrix(op, prec="fp32")
     b = torch.tensor(c["b"], device=dev)
     d = {"n": n, "nnz": nnz}
+    jac = {"precond": "jacobi"}
     for name, kw in (("plcg_l1", {"l": 1}), ("plcg_l2", {"l": 2}), ("plcg_l3", {"l": 3}),
-                     ("classic_cg", {"method": "cg"})):
+                     ("classic_cg", {"method": "cg"}),
+                     ("jacobi_plcg_l1", {"l": 1, **jac}), ("jacobi_plcg_l2", {"l": 2, **jac}),
+                     ("jacobi_plcg_l3", {"l": 3, **jac}), ("jacobi_classic_cg", {"method": "cg", **jac})):
+        # Jacobi: shifts on the spectrum of diag(A)^{-1} A; natural-norm rtol
+        interval = W.jacobi_shift_interval(op) if "precond" in kw else c["interval"]
         ts = []
         for _ in range(2):
             x = torch.zeros_like(b)
-            r = A.solve(b, x, interval=c["interval"], rtol=1e-8, prec="fp32", max_restarts=64,
+            r = A.solve(b, x, interval=interval, rtol=1e-8, prec="fp32", max_restarts=64,
                         check=False, **kw)
             ts.append(r.seconds)
         ll = kw.get("l", 1)
         vec_passes = 10 if "method" in kw else 3 * (ll + 1) + 4
+        vec_passes += 2 if "precond" in kw else 0   # 1/a_gg and a_gg
         byt = r.iters * (vec_passes * 4 * n + 8 * nnz + 8 * n)
         d[name] = {"status": r.status, "iters": r.iters, "restarts": r.restarts,
                    "refinements": r.refinements, "time_to_rtol_s": round(min(ts), 5),

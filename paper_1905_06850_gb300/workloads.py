@@ -258,6 +258,29 @@ def config_hetero27(nx: int = 128, seed: int = 3) -> dict:
             "rtol": 1e-8}
 
 
+def e3_diagonal(nx: int = 100, seed: int = 1) -> dict:
+    """The paper's communication-bound toy (Sec. 4, Fig. "lapl", right): a
+    diagonal ("one-point stencil") operator carrying the nx^2 eigenvalues of
+    the 2D 5-point Laplacian, lambda_jk = 4 - 2 cos(j pi/(nx+1)) -
+    2 cos(k pi/(nx+1)) in (k, j) = (y, x) order, with the right-hand side
+    rotated into that eigenbasis: b_diag = Q^T b where Q is the orthonormal
+    DST-I basis (scipy.fft.dstn, norm "ortho") and b = A x* of config_2d.  It
+    has the Laplacian's spectrum and residual history, with an SpMV that is
+    one multiply per row.  Returns op (CSR, one entry per row), b, the
+    Laplacian's b, interval."""
+    import scipy.fft
+    lap = config_2d(nx=nx, seed=seed)
+    j = np.arange(1, nx + 1)
+    lam1 = 2.0 - 2.0 * np.cos(j * np.pi / (nx + 1))
+    lam = (lam1[:, None] + lam1[None, :]).ravel()
+    n = nx * nx
+    op = {"kind": "csr", "n": n, "rowptr": np.arange(n + 1, dtype=np.int64),
+          "col": np.arange(n, dtype=np.int32), "val": lam}
+    bt = scipy.fft.dstn(lap["b"].reshape(nx, nx), type=1, norm="ortho").ravel()
+    return {"op": op, "b": bt, "b_laplacian": lap["b"], "interval": (0.0, 8.0),
+            "rtol": 1e-6}
+
+
 def batched_systems(count: int = 4096, s_lo: int = 16, s_hi: int = 256, seed: int = 4):
     """The batched workload: ``count`` shifted 2D Poisson systems.  Returns a
     list of dicts with op (FP32-rounded coefficients), b, interval, side, c."""

@@ -594,3 +594,23 @@ def test_j7_jacobi_rejects_a_nonpositive_diagonal():
           "col": np.array([0, 1], dtype=np.int32), "val": np.array([1.0, -2.0])}
     assert O.cg(op, np.ones(2), precond="jacobi").status == O.ORC_ERR_INVALID
     assert O.plcg(op, np.ones(2), l=1, sigma=[0.5], precond="jacobi").status == O.ORC_ERR_INVALID
+
+
+@pytest.mark.parametrize("l", [0, 1, 2])
+def test_p10_e3_workload_generator(l):
+    """The diagonal-toy workload generator builds what P10 pins: the oracle on
+    it has the 2D Laplacian's iteration count, and rotating its x back
+    (inverse DST-I) gives the Laplacian solve's x."""
+    N = 30
+    e = W.e3_diagonal(N)
+    lap = W.config_2d(nx=N)
+    if l == 0:
+        a, b = O.cg(e["op"], e["b"], rtol=1e-8), O.cg(lap["op"], lap["b"], rtol=1e-8)
+    else:
+        s = O.chebyshev_shifts(l, *e["interval"])
+        a = O.plcg(e["op"], e["b"], l=l, sigma=s, rtol=1e-8)
+        b = O.plcg(lap["op"], lap["b"], l=l, sigma=s, rtol=1e-8)
+    assert a.status == b.status == O.ORC_OK and a.iters == b.iters
+    xa = scipy.fft.idstn(a.x.reshape(N, N), type=1, norm="ortho").ravel()
+    assert np.linalg.norm(xa - b.x) <= 1e-12 * np.linalg.norm(b.x)
+    assert np.array_equal(e["b_laplacian"], lap["b"])
