@@ -223,8 +223,8 @@ template <typename V>
 struct Ld1 {
     const V *z;
     template <int VEC>
-    __device__ __forceinline__ void vec(int64_t g, V (&o)[VEC]) const { vld<V, VEC>(z + g, o); }
-    __device__ __forceinline__ V one(int64_t g) const { return z[g]; }
+    __device__ __forceinline__ void vec(uint32_t g, V (&o)[VEC]) const { vld<V, VEC>(z + g, o); }
+    __device__ __forceinline__ V one(uint32_t g) const { return z[g]; }
 };
 
 template <typename V>
@@ -233,7 +233,7 @@ struct LdAxpy {           // value = a[g] + beta * b[g]
     const V *b;
     V beta;
     template <int VEC>
-    __device__ __forceinline__ void vec(int64_t g, V (&o)[VEC]) const
+    __device__ __forceinline__ void vec(uint32_t g, V (&o)[VEC]) const
     {
         V t[VEC];
         vld<V, VEC>(a + g, o);
@@ -241,15 +241,15 @@ struct LdAxpy {           // value = a[g] + beta * b[g]
 #pragma unroll
         for (int v = 0; v < VEC; ++v) o[v] = fma(beta, t[v], o[v]);
     }
-    __device__ __forceinline__ V one(int64_t g) const { return fma(beta, b[g], a[g]); }
+    __device__ __forceinline__ V one(uint32_t g) const { return fma(beta, b[g], a[g]); }
 };
 
 template <typename V>
 struct LdFirst {          // value = a[g] (CG first step, p_0 = r_0)
     const V *a;
     template <int VEC>
-    __device__ __forceinline__ void vec(int64_t g, V (&o)[VEC]) const { vld<V, VEC>(a + g, o); }
-    __device__ __forceinline__ V one(int64_t g) const { return a[g]; }
+    __device__ __forceinline__ void vec(uint32_t g, V (&o)[VEC]) const { vld<V, VEC>(a + g, o); }
+    __device__ __forceinline__ V one(uint32_t g) const { return a[g]; }
 };
 
 // ------------------------------------------------------------------------
@@ -257,18 +257,18 @@ struct LdFirst {          // value = a[g] (CG first step, p_0 = r_0)
 // rows g0 .. g0+VEC-1 (stencil: nx % VEC == 0, so they share y and z).
 // ------------------------------------------------------------------------
 // Centre values c and neighbour sums nb of the VEC rows g0 .. g0+VEC-1, so
-// that (A z)_g = center * c + off * nb.
+// that (A z)_g = center * c + off * nb.  Row indices are 32-bit (n < 2^31):
+// one multiply-add forms each address.
 template <typename V, int VEC, class Ld>
-__device__ __forceinline__ void stencil_parts(const StencilDesc &st, const Ld &ld, int64_t g0,
+__device__ __forceinline__ void stencil_parts(const StencilDesc &st, const Ld &ld, uint32_t g0,
                                               V (&c)[VEC], V (&nb)[VEC])
 {
-    const int nx = st.nx, ny = st.ny;
-    // coordinates of row g0 (n < 2^31): x fastest, then y, then z
-    const uint32_t gu = (uint32_t)g0;
-    const uint32_t line = (__umulhi(gu, st.dnx.m) + gu) >> st.dnx.s;
-    const int x0 = (int)(gu - line * (uint32_t)nx);
+    const uint32_t nx = (uint32_t)st.nx, ny = (uint32_t)st.ny;
+    // coordinates of row g0: x fastest, then y, then z
+    const uint32_t line = (__umulhi(g0, st.dnx.m) + g0) >> st.dnx.s;
+    const uint32_t x0 = g0 - line * nx;
     const uint32_t zc = (__umulhi(line, st.dny.m) + line) >> st.dny.s;
-    const int y = (int)(line - zc * (uint32_t)ny);
+    const uint32_t y = line - zc * ny;
     ld.template vec<VEC>(g0, c);
     const V left = (x0 > 0) ? ld.one(g0 - 1) : V(0);
     const V right = (x0 + VEC < nx) ? ld.one(g0 + VEC) : V(0);
@@ -281,19 +281,19 @@ __device__ __forceinline__ void stencil_parts(const StencilDesc &st, const Ld &l
 #pragma unroll
         for (int v = 0; v < VEC; ++v) nb[v] += t[v];
     }
-    if (y < ny - 1) {
+    if (y + 1 < ny) {
         ld.template vec<VEC>(g0 + nx, t);
 #pragma unroll
         for (int v = 0; v < VEC; ++v) nb[v] += t[v];
     }
     if (st.dim == 3) {
-        const int64_t nxy = (int64_t)nx * ny;
+        const uint32_t nxy = nx * ny;
         if (zc > 0) {
             ld.template vec<VEC>(g0 - nxy, t);
 #pragma unroll
             for (int v = 0; v < VEC; ++v) nb[v] += t[v];
         }
-        if ((int)zc < st.nz - 1) {
+        if (zc + 1 < (uint32_t)st.nz) {
             ld.template vec<VEC>(g0 + nxy, t);
 #pragma unroll
             for (int v = 0; v < VEC; ++v) nb[v] += t[v];
@@ -303,7 +303,7 @@ __device__ __forceinline__ void stencil_parts(const StencilDesc &st, const Ld &l
 
 template <typename V, int VEC, class Ld>
 __device__ __forceinline__ void stencil_apply(const StencilDesc &st, V cC, V cO, const Ld &ld,
-                                              int64_t g0, V (&c)[VEC], V (&w)[VEC])
+                                              uint32_t g0, V (&c)[VEC], V (&w)[VEC])
 {
     V nb[VEC];
     stencil_parts<V, VEC>(st, ld, g0, c, nb);
@@ -313,7 +313,7 @@ __device__ __forceinline__ void stencil_apply(const StencilDesc &st, V cC, V cO,
 
 // CSR row (VEC = 1).  C is the stored value type (float or double).
 template <typename V, typename C, class Ld>
-__device__ __forceinline__ V csr_row(const CsrDesc &A, const Ld &ld, int64_t row)
+__device__ __forceinline__ V csr_row(const CsrDesc &A, const Ld &ld, uint32_t row)
 {
     const C *val = static_cast<const C *>(A.val);
     const int64_t e0 = __ldg(A.rowptr + row), e1 = __ldg(A.rowptr + row + 1);
@@ -325,7 +325,7 @@ __device__ __forceinline__ V csr_row(const CsrDesc &A, const Ld &ld, int64_t row
 // (c, nb) with (A z)_g = kc * c + kn * nb: stencil (center, off), CSR (0, 1).
 template <typename V, typename C, int VEC, int OP, class Ld>
 __device__ __forceinline__ void op_parts(const StencilDesc &st, const CsrDesc &csr, const Ld &ld,
-                                         int64_t g0, V (&c)[VEC], V (&nb)[VEC])
+                                         uint32_t g0, V (&c)[VEC], V (&nb)[VEC])
 {
     if constexpr (OP == kOpStencil) {
         stencil_parts<V, VEC>(st, ld, g0, c, nb);
@@ -338,7 +338,7 @@ __device__ __forceinline__ void op_parts(const StencilDesc &st, const CsrDesc &c
 
 template <typename V, typename C, int VEC, int OP, class Ld>
 __device__ __forceinline__ void op_apply(const StencilDesc &st, const CsrDesc &csr, V cC, V cO,
-                                         const Ld &ld, int64_t g0, V (&c)[VEC], V (&w)[VEC])
+                                         const Ld &ld, uint32_t g0, V (&c)[VEC], V (&w)[VEC])
 {
     if constexpr (OP == kOpStencil) {
         stencil_apply<V, VEC>(st, cC, cO, ld, g0, c, w);
@@ -804,8 +804,8 @@ __device__ void residual_sweep(const SolveArgs<T> &a, Smem<T> &s, const Grp &grp
     double acc[2] = {0.0, 0.0};
     Ld1<double> ld{a.x};
     for (int64_t u = grp.unit0(); u < nunits; u += grp.ustep()) {
-        const int64_t g0 = u * UNIT + (int64_t)threadIdx.x * V64;
-        if (g0 >= n) continue;
+        const uint32_t g0 = (uint32_t)(u * UNIT + (int64_t)threadIdx.x * V64);
+        if (g0 >= (uint32_t)n) continue;
         double c[V64], w[V64], bv[V64];
         if constexpr (OP == kOpStencil) {
             stencil_apply<double, V64>(a.st, cC, cO, ld, g0, c, w);
@@ -846,6 +846,16 @@ __device__ __forceinline__ void write_result(const SolveArgs<T> &a, int status, 
     o->refinements = refinements;
     o->recursive_relres = (normb > 0.0) ? recres / normb : 0.0;
     o->true_relres = (normb > 0.0) ? last_rn / normb : 0.0;
+}
+
+// K5 operand of dot q in the steady state (l+1 dots, i >= l+1): the same
+// choice scalar_step makes, as a compile-time function of q: 0 no dot,
+// 1 ring vector z^(l)_j from memory, 2 the new z^(l)_{i+1}, 3 the new
+// z^(0)_{i-l+1}, 4 z^(l)_i, 5 z^(l)_{i-1}.
+template <int L>
+__device__ __forceinline__ constexpr int steady_dot_src(int q)
+{
+    return q < L ? 0 : q == L ? 3 : q == 2 * L ? 2 : q == 2 * L - 1 ? 4 : q == 2 * L - 2 ? 5 : 1;
 }
 
 // ------------------------------------------------------------------------
@@ -1036,126 +1046,139 @@ __device__ void plcg_body(const SolveArgs<T> &a, Smem<T> &s, Grp &grp)
             StRef st = a.st;
             const CsrDesc &csr = a.csr;
             T *const pvec = a.p;
-            const bool rec = C.mode == 1;
             DotAcc<T, VEC> dac[2 * L + 1];
-            int since_flush = 0;
-            const int64_t usw = (int64_t)nsw * VEC * RPT;   // rows per sweep unit
-            const int64_t nunits_s = (tid < nsw) ? (n + usw - 1) / usw : 0;
-            for (int64_t u = grp.unit0(); u < nunits_s; u += grp.ustep()) {
-                int64_t g0[RPT];
-                bool ok[RPT];
+            const uint32_t nn = (uint32_t)n;                      // n < 2^31
+            const uint32_t usw = (uint32_t)(nsw * VEC * RPT);      // rows per sweep unit
+            const uint32_t nunits_s = (tid < nsw) ? (nn + usw - 1) / usw : 0u;
+            // Steady state -- every iteration of a segment after the first l + 1:
+            // the recurrences run, K6 updates p and x, z^(0)_{m-1} exists and the
+            // K5 operands follow a fixed pattern.  That case gets its own loop
+            // with those tests and the operand selection resolved at compile time.
+            const bool steady = C.mode == 1 && C.k6 == 2 && C.prev0 && !a.dots_2l1;
+            auto sweep = [&](auto steady_tag) {
+                constexpr bool S = decltype(steady_tag)::value;
+                const bool rec = S || C.mode == 1;
+                const int k6 = S ? 2 : C.k6;
+                const bool prev0 = S || C.prev0;
+                int since_flush = 0;
+                for (uint32_t u = (uint32_t)grp.unit0(); u < nunits_s; u += (uint32_t)grp.ustep()) {
+                    uint32_t g0[RPT];
+                    bool ok[RPT];
 #pragma unroll
-                for (int r = 0; r < RPT; ++r) {
-                    g0[r] = u * usw + ((int64_t)r * nsw + tid) * VEC;
-                    ok[r] = g0[r] < n;
-                }
-                // -- loads
-                T c[RPT][VEC], nb[RPT][VEC], zp[RPT][VEC], cur[RPT][L][VEC], pk[RPT][L][VEC];
-                T pv[RPT][VEC], xv[RPT][VEC];
-                T dg[RPT];   // Jacobi: a_gg, for u_{i+1} = M z^(l)_{i+1}
-#pragma unroll
-                for (int r = 0; r < RPT; ++r) {
-#pragma unroll
-                    for (int v = 0; v < VEC; ++v) zp[r][v] = T(0);
-                    dg[r] = T(1);
-                    if (!ok[r]) continue;
-                    op_parts<T, T, VEC, OP>(st, csr, Ld1<T>{C.zl_cur}, g0[r], c[r], nb[r]);   // K1 operands
-                    if constexpr (OP == kOpCsrJacobi) {
-                        // K1 with M = diag(A): z^(l)_{i+1} is built from M^{-1} A z^(l)_i
-                        nb[r][0] *= __ldg(static_cast<const T *>(csr.dinv) + g0[r]);
-                        dg[r] = __ldg(static_cast<const T *>(csr.diag) + g0[r]);
+                    for (int r = 0; r < RPT; ++r) {
+                        g0[r] = u * usw + ((uint32_t)r * nsw + tid) * VEC;
+                        ok[r] = g0[r] < nn;
                     }
-                    if (rec) {
-                        vld<T, VEC>(C.zl_prev + g0[r], zp[r]);
+                    // -- loads
+                    T c[RPT][VEC], nb[RPT][VEC], zp[RPT][VEC], cur[RPT][L][VEC], pk[RPT][L][VEC];
+                    T pv[RPT][VEC], xv[RPT][VEC];
+                    T dg[RPT];   // Jacobi: a_gg, for u_{i+1} = M z^(l)_{i+1}
 #pragma unroll
-                        for (int k = 0; k < L; ++k) vld<T, VEC>(C.cur[k] + g0[r], cur[r][k]);
+                    for (int r = 0; r < RPT; ++r) {
 #pragma unroll
-                        for (int k = 0; k < L; ++k) {
-                            if (k > 0 || C.prev0) {
-                                vld<T, VEC>(C.prv[k] + g0[r], pk[r][k]);
-                            } else {
+                        for (int v = 0; v < VEC; ++v) zp[r][v] = T(0);
+                        dg[r] = T(1);
+                        if (!ok[r]) continue;
+                        op_parts<T, T, VEC, OP>(st, csr, Ld1<T>{C.zl_cur}, g0[r], c[r], nb[r]);   // K1 operands
+                        if constexpr (OP == kOpCsrJacobi) {
+                            // K1 with M = diag(A): z^(l)_{i+1} is built from M^{-1} A z^(l)_i
+                            nb[r][0] *= __ldg(static_cast<const T *>(csr.dinv) + g0[r]);
+                            dg[r] = __ldg(static_cast<const T *>(csr.diag) + g0[r]);
+                        }
+                        if (rec) {
+                            vld<T, VEC>(C.zl_prev + g0[r], zp[r]);
 #pragma unroll
-                                for (int v = 0; v < VEC; ++v) pk[r][k][v] = T(0);
+                            for (int k = 0; k < L; ++k) vld<T, VEC>(C.cur[k] + g0[r], cur[r][k]);
+#pragma unroll
+                            for (int k = 0; k < L; ++k) {
+                                if (k > 0 || prev0) {
+                                    vld<T, VEC>(C.prv[k] + g0[r], pk[r][k]);
+                                } else {
+#pragma unroll
+                                    for (int v = 0; v < VEC; ++v) pk[r][k][v] = T(0);
+                                }
                             }
                         }
-                    }
-                    if (C.k6 == 2) {
-                        vld<T, VEC>(pvec + g0[r], pv[r]);
-                        vld<T, VEC>(xi + g0[r], xv[r]);
-                    }
-                }
-#pragma unroll
-                for (int r = 0; r < RPT; ++r) {
-                    if (!ok[r]) continue;
-                    // -- compute
-                    T un[VEC], nw[L][VEC];
-                    if (!rec) {
-                        // u_{i+1} = A z^(l)_i - sigma_i z^(l)_i
-#pragma unroll
-                        for (int v = 0; v < VEC; ++v) un[v] = fma(kc - C.sig, c[r][v], kn * nb[r][v]);
-                    } else {
-                        // K4: z^(l)_{i+1} = (A z^(l)_i - gamma z^(l)_i - delta' z^(l)_{i-1}) / delta
-                        // and z^(k)_{i-l+k+1}, k < l (Algorithm 1, K4)
-                        const T uc = fma(kc, C.invd, C.al), un_nb = kn * C.invd;
-#pragma unroll
-                        for (int v = 0; v < VEC; ++v)
-                            un[v] = fma(uc, c[r][v], fma(un_nb, nb[r][v], C.bm * zp[r][v]));
-#pragma unroll
-                        for (int k = 0; k < L; ++k)
-#pragma unroll
-                            for (int v = 0; v < VEC; ++v) {
-                                const T up = (k == L - 1) ? c[r][v] : cur[r][k + 1][v];
-                                nw[k][v] = fma(up, C.invd, fma(C.ak[k], cur[r][k][v], C.bm * pk[r][k][v]));
-                            }
-                    }
-                    // K6: p and the iterate (Algorithm 1, K6)
-                    if (C.k6 == 1) {
-#pragma unroll
-                        for (int v = 0; v < VEC; ++v) pv[r][v] = C.pv * cur[r][0][v];
-                    } else if (C.k6 == 2) {
-#pragma unroll
-                        for (int v = 0; v < VEC; ++v) {
-                            xv[r][v] = fma(C.zx, pv[r][v], xv[r][v]);
-                            pv[r][v] = fma(C.pv, cur[r][0][v], C.pp * pv[r][v]);
+                        if (k6 == 2) {
+                            vld<T, VEC>(pvec + g0[r], pv[r]);
+                            vld<T, VEC>(xi + g0[r], xv[r]);
                         }
                     }
-                    // -- stores
-                    vst<T, VEC>(C.zl_new + g0[r], un);
-                    if (!rec) {
-                        for (int k = 0; k < C.ncopy; ++k) vst<T, VEC>(cf.cpy[k] + g0[r], un);
-                    } else {
 #pragma unroll
-                        for (int k = 0; k < L; ++k) vst<T, VEC>(C.nw[k] + g0[r], nw[k]);
-                    }
-                    if (C.k6 >= 1) vst<T, VEC>(pvec + g0[r], pv[r]);
-                    if (C.k6 == 2) vst<T, VEC>(xi + g0[r], xv[r]);
-                    // -- K5: partial dot products with u_{i+1} = M z^(l)_{i+1}
-                    // (M = I: z^(l)_{i+1} itself)
-                    T uM[VEC];
+                    for (int r = 0; r < RPT; ++r) {
+                        if (!ok[r]) continue;
+                        // -- compute
+                        T un[VEC], nw[L][VEC];
+                        if (!rec) {
+                            // u_{i+1} = A z^(l)_i - sigma_i z^(l)_i
 #pragma unroll
-                    for (int v = 0; v < VEC; ++v) uM[v] = (OP == kOpCsrJacobi) ? un[v] * dg[r] : un[v];
-#pragma unroll
-                    for (int q = 0; q <= 2 * L; ++q) {
-                        const int src = C.dsrc[q];
-                        if (src == 0) continue;
-                        T o[VEC];
-                        if (src == 1) {
-                            vld<T, VEC>(cf.dptr[q] + g0[r], o);
+                            for (int v = 0; v < VEC; ++v) un[v] = fma(kc - C.sig, c[r][v], kn * nb[r][v]);
                         } else {
+                            // K4: z^(l)_{i+1} = (A z^(l)_i - gamma z^(l)_i - delta' z^(l)_{i-1}) / delta
+                            // and z^(k)_{i-l+k+1}, k < l (Algorithm 1, K4)
+                            const T uc = fma(kc, C.invd, C.al), un_nb = kn * C.invd;
 #pragma unroll
                             for (int v = 0; v < VEC; ++v)
-                                o[v] = (src == 2) ? un[v] : (src == 3) ? nw[0][v] : (src == 4) ? c[r][v]
-                                     : zp[r][v];
+                                un[v] = fma(uc, c[r][v], fma(un_nb, nb[r][v], C.bm * zp[r][v]));
+#pragma unroll
+                            for (int k = 0; k < L; ++k)
+#pragma unroll
+                                for (int v = 0; v < VEC; ++v) {
+                                    const T up = (k == L - 1) ? c[r][v] : cur[r][k + 1][v];
+                                    nw[k][v] = fma(up, C.invd, fma(C.ak[k], cur[r][k][v], C.bm * pk[r][k][v]));
+                                }
                         }
-                        dac[q].add(uM, o);
+                        // K6: p and the iterate (Algorithm 1, K6)
+                        if (k6 == 1) {
+#pragma unroll
+                            for (int v = 0; v < VEC; ++v) pv[r][v] = C.pv * cur[r][0][v];
+                        } else if (k6 == 2) {
+#pragma unroll
+                            for (int v = 0; v < VEC; ++v) {
+                                xv[r][v] = fma(C.zx, pv[r][v], xv[r][v]);
+                                pv[r][v] = fma(C.pv, cur[r][0][v], C.pp * pv[r][v]);
+                            }
+                        }
+                        // -- stores
+                        vst<T, VEC>(C.zl_new + g0[r], un);
+                        if (!rec) {
+                            for (int k = 0; k < C.ncopy; ++k) vst<T, VEC>(cf.cpy[k] + g0[r], un);
+                        } else {
+#pragma unroll
+                            for (int k = 0; k < L; ++k) vst<T, VEC>(C.nw[k] + g0[r], nw[k]);
+                        }
+                        if (k6 >= 1) vst<T, VEC>(pvec + g0[r], pv[r]);
+                        if (k6 == 2) vst<T, VEC>(xi + g0[r], xv[r]);
+                        // -- K5: partial dot products with u_{i+1} = M z^(l)_{i+1}
+                        // (M = I: z^(l)_{i+1} itself)
+                        T uM[VEC];
+#pragma unroll
+                        for (int v = 0; v < VEC; ++v) uM[v] = (OP == kOpCsrJacobi) ? un[v] * dg[r] : un[v];
+#pragma unroll
+                        for (int q = 0; q <= 2 * L; ++q) {
+                            const int src = S ? steady_dot_src<L>(q) : C.dsrc[q];
+                            if (src == 0) continue;
+                            T o[VEC];
+                            if (src == 1) {
+                                vld<T, VEC>(cf.dptr[q] + g0[r], o);
+                            } else {
+#pragma unroll
+                                for (int v = 0; v < VEC; ++v)
+                                    o[v] = (src == 2) ? un[v] : (src == 3) ? nw[0][v] : (src == 4) ? c[r][v]
+                                         : zp[r][v];
+                            }
+                            dac[q].add(uM, o);
+                        }
+                    }
+                    if (++since_flush == kFlushUnits) {
+#pragma unroll
+                        for (int q = 0; q <= 2 * L; ++q) dac[q].flush();
+                        since_flush = 0;
                     }
                 }
-                if (++since_flush == kFlushUnits) {
-#pragma unroll
-                    for (int q = 0; q <= 2 * L; ++q) dac[q].flush();
-                    since_flush = 0;
-                }
-            }
+            };
+            if (steady) sweep(std::true_type{});
+            else sweep(std::false_type{});
             double acc[2 * L + 1];
 #pragma unroll
             for (int q = 0; q <= 2 * L; ++q) {
@@ -1211,6 +1234,7 @@ __device__ void cg_body(const SolveArgs<T> &a, Smem<T> &s, Grp &grp)
     const CsrDesc &csr = a.csr;
     T *rc = kF32 ? a.rc : reinterpret_cast<T *>(a.r);
     T *xi = kF32 ? a.zring + 2 * n : reinterpret_cast<T *>(a.x);
+    const uint32_t nn = (uint32_t)n;   // n < 2^31
 
     long long iters = 0, spmvs = 0, restarts = 0, refinements = 0, segments = 0;
     int last_end = kSegConverged;
@@ -1310,13 +1334,13 @@ __device__ void cg_body(const SolveArgs<T> &a, Smem<T> &s, Grp &grp)
             DotAcc<T, VEC> d1;
             int since_flush = 0;
             const int64_t nunits_s = (n + USWEEP - 1) / USWEEP;
-            for (int64_t u = grp.unit0(); u < nunits_s; u += grp.ustep()) {
+            for (uint32_t u = (uint32_t)grp.unit0(); u < (uint32_t)nunits_s; u += (uint32_t)grp.ustep()) {
                 T c[RPT][VEC], w[RPT][VEC], mi[RPT];
-                int64_t g0[RPT];
+                uint32_t g0[RPT];
 #pragma unroll
                 for (int r = 0; r < RPT; ++r) {
-                    g0[r] = u * USWEEP + ((int64_t)r * kBlock + tid) * VEC;
-                    if (g0[r] >= n) continue;
+                    g0[r] = u * USWEEP + ((uint32_t)r * kBlock + tid) * VEC;
+                    if (g0[r] >= nn) continue;
                     if (k == 0)
                         op_apply<T, T, VEC, OP>(st, csr, cC, cO, LdFirst<T>{rc}, g0[r], c[r], w[r]);
                     else
@@ -1326,7 +1350,7 @@ __device__ void cg_body(const SolveArgs<T> &a, Smem<T> &s, Grp &grp)
                 }
 #pragma unroll
                 for (int r = 0; r < RPT; ++r) {
-                    if (g0[r] >= n) continue;
+                    if (g0[r] >= nn) continue;
                     vst<T, VEC>(pn + g0[r], c[r]);
                     d1.add(c[r], w[r]);
                     if constexpr (OP == kOpCsrJacobi) w[r][0] *= mi[r];   // q = M^{-1} A p
@@ -1348,13 +1372,13 @@ __device__ void cg_body(const SolveArgs<T> &a, Smem<T> &s, Grp &grp)
             // ---- x += alpha p; r -= alpha q; (r, r)
             DotAcc<T, VEC> d2;
             since_flush = 0;
-            for (int64_t u = grp.unit0(); u < nunits_s; u += grp.ustep()) {
+            for (uint32_t u = (uint32_t)grp.unit0(); u < (uint32_t)nunits_s; u += (uint32_t)grp.ustep()) {
                 T pv[RPT][VEC], qv[RPT][VEC], xv[RPT][VEC], rv[RPT][VEC], dv[RPT][VEC];
-                int64_t g0[RPT];
+                uint32_t g0[RPT];
 #pragma unroll
                 for (int r = 0; r < RPT; ++r) {
-                    g0[r] = u * USWEEP + ((int64_t)r * kBlock + tid) * VEC;
-                    if (g0[r] >= n) continue;
+                    g0[r] = u * USWEEP + ((uint32_t)r * kBlock + tid) * VEC;
+                    if (g0[r] >= nn) continue;
                     vld<T, VEC>(pn + g0[r], pv[r]);
                     vld<T, VEC>(q + g0[r], qv[r]);
                     vld<T, VEC>(xi + g0[r], xv[r]);
@@ -1364,7 +1388,7 @@ __device__ void cg_body(const SolveArgs<T> &a, Smem<T> &s, Grp &grp)
                 }
 #pragma unroll
                 for (int r = 0; r < RPT; ++r) {
-                    if (g0[r] >= n) continue;
+                    if (g0[r] >= nn) continue;
 #pragma unroll
                     for (int v = 0; v < VEC; ++v) {
                         xv[r][v] = fma(al, pv[r][v], xv[r][v]);
