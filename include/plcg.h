@@ -100,7 +100,7 @@ typedef struct {
     double lmin, lmax;          /* spectrum interval for the shifts (0, 8)      */
     double rtol;                /* stop when ||b - A x|| < rtol ||b|| (1e-8);
                                    Jacobi: in the natural norm                   */
-    int64_t maxit;              /* budget on the iterate index k (100000)        */
+    int64_t maxit;              /* budget on the iterate index k, <= 2^30 (100000) */
     int prec;                   /* plcg_precision (PLCG_FP64)                    */
     int dots_2l1;               /* 1: the 2l+1 dot products of Algorithm 1, K5;
                                    0: l+1 dots via the symmetry of G (Sec. 2.2)  (0) */

@@ -340,6 +340,7 @@ static plcg_status build_solve(const plcg_matrix *A, const double *b, double *x,
             if (k == l) d = std::max(3, l);
             if (k == 0 && prm->dots_2l1) d = std::max(3, l + 1);
             a.depth[k] = d;
+            a.ddiv[k] = make_fastdiv((uint32_t)d);
             a.base[k] = nvec;
             nvec += d;
         }
@@ -480,7 +481,8 @@ static plcg_status check_params(const plcg_matrix *A, const plcg_params *p)
         return fail(PLCG_ERR_INVALID, "l must be in 1..%d", kMaxL);
     if (!(p->rtol > 0.0) || !std::isfinite(p->rtol))
         return fail(PLCG_ERR_INVALID, "rtol must be a positive finite number");
-    if (p->maxit < 0) return fail(PLCG_ERR_INVALID, "maxit must be >= 0");
+    if (p->maxit < 0 || p->maxit > (int64_t(1) << 30))
+        return fail(PLCG_ERR_INVALID, "maxit must be in [0, 2^30]");
     if (p->max_restarts < 0) return fail(PLCG_ERR_INVALID, "max_restarts must be >= 0");
     if (p->prec != PLCG_FP64 && p->prec != PLCG_FP32_FP64DOT)
         return fail(PLCG_ERR_INVALID, "unknown precision %d", p->prec);
@@ -655,6 +657,7 @@ static plcg_status run_batched(int count, plcg_matrix *const *A, const double *c
             if (k == l) d = std::max(3, l);
             if (k == 0 && prm->dots_2l1) d = std::max(3, l + 1);
             proto.depth[k] = d;
+            proto.ddiv[k] = make_fastdiv((uint32_t)d);
             proto.base[k] = nvec;
             nvec += d;
         }

@@ -79,6 +79,7 @@ struct SolveArgs {
     double *r;                // FP64 residual b - A x
     T *zring;                 // ring storage of the l+1 bases (p(l)-CG) / p ring (CG)
     int depth[kMaxL + 1];     // ring depth of basis k
+    FastDivU32 ddiv[kMaxL + 1];   // division by depth[k] (ring slots)
     int64_t base[kMaxL + 1];  // offset (in vectors) of basis k's ring
     T *p;                     // search direction p (p(l)-CG) / q = A p (CG)
     T *rc;                    // CG: the recursive residual in T (FP32 path)

@@ -85,6 +85,7 @@ plcg_status run(const StencilDesc &st, int64_t n, const double *b, double *x,
             if (k == l) d = std::max(3, l);
             if (k == 0 && prm->dots_2l1) d = std::max(3, l + 1);
             a.depth[k] = d;
+            a.ddiv[k] = make_fastdiv((uint32_t)d);
             a.base[k] = nvec;
             nvec += d;
         }
@@ -177,7 +178,8 @@ extern "C" plcg_status plcg_solve_stencil_noalloc(const plcg_stencil_desc *d, co
         return nafail(PLCG_ERR_INVALID, "unknown method");
     if (prm->method == PLCG_METHOD_PLCG && (prm->l < 1 || prm->l > kMaxL))
         return nafail(PLCG_ERR_INVALID, "l must be in 1..8");
-    if (!(prm->rtol > 0.0) || !std::isfinite(prm->rtol) || prm->maxit < 0 || prm->max_restarts < 0)
+    if (!(prm->rtol > 0.0) || !std::isfinite(prm->rtol) || prm->maxit < 0 ||
+        prm->maxit > (int64_t(1) << 30) || prm->max_restarts < 0)
         return nafail(PLCG_ERR_INVALID, "bad rtol, maxit or max_restarts");
     if (prm->prec != PLCG_FP64 && prm->prec != PLCG_FP32_FP64DOT)
         return nafail(PLCG_ERR_INVALID, "unknown precision");

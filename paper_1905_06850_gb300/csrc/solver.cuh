@@ -414,7 +414,7 @@ struct Smem {
     double raw[kMaxDots];
     double G[kMaxL + 1][kMaxDots];   // finalised columns c-l .. c (column c at c mod (l+1))
     double Ginv[kMaxL + 1];          // 1 / g_{c,c} of those columns
-    double gam[kMaxL + 1], del[kMaxL + 1];
+    double gam[kMaxL + 1], del[kMaxL + 1], idel[kMaxL + 1];   // gamma_j, delta_j, 1 / delta_j
     double eta[2], zeta[2], ieta[2]; // eta_m, zeta_m, 1 / eta_m
     double bring[kMaxL + 1][kMaxDots];   // one-CTA group: reduced dots of the last l+1 iterations
     double bnorm[2];
@@ -427,11 +427,14 @@ template <typename T> struct Eps;
 template <> struct Eps<double> { static constexpr double v = DBL_EPSILON; };
 template <> struct Eps<float> { static constexpr double v = (double)FLT_EPSILON; };
 
+// Vector j of basis k's ring: slot j mod depth[k] (j < 2^31; the modulo by
+// the invariant depth uses the host-prepared multiply-shift divisor).
 template <typename T>
 __device__ __forceinline__ T *ring(const SolveArgs<T> &a, int k, long long j)
 {
-    // j < 2^31 (iteration indices); 32-bit modulo
-    return a.zring + (a.base[k] + (int64_t)((unsigned)j % (unsigned)a.depth[k])) * a.n;
+    const uint32_t jj = (uint32_t)j;
+    const uint32_t q = (__umulhi(jj, a.ddiv[k].m) + jj) >> a.ddiv[k].s;
+    return a.zring + (a.base[k] + (int64_t)(jj - q * (uint32_t)a.depth[k])) * a.n;
 }
 
 // ------------------------------------------------------------------------
@@ -571,147 +574,29 @@ struct GangGroup {
 };
 
 // ------------------------------------------------------------------------
-// Scalar step of iteration i (thread 0 of every CTA; all CTAs compute the
-// same bits).  K2: finalise column c = i-l+1 of G (Algorithm 1)
-// and its breakdown check; K3: gamma_{i-l}, delta_{i-l};
-// K6 scalars: lambda, eta, zeta and the stop test.
+// Scalar step of iteration i (one thread of every CTA; all CTAs compute the
+// same bits).  K2: finalise column c = i-l+1 of G (Algorithm 1) and its
+// breakdown check; K3: gamma_{i-l}, delta_{i-l}; K6 scalars: lambda, eta,
+// zeta and the stop test.
 // A dependent FP64 operation costs ~64 cycles on GB300 and a division or a
-// square root ~500, so the step keeps 1/g_{j,j} and 1/eta_m and needs one
-// square root and three reciprocals per iteration (1/g_{c,c} is off the
-// critical path).
+// square root ~500, so the step is ordered for latency: the vector pointers
+// (integer work) first; then gamma, the K6 scalars (which do not need
+// g_{c,c}) and 1/sqrt(arg) are all in flight before the breakdown branch;
+// g_{c,c} = arg / sqrt(arg) and 1/delta_m = g_{m,m} / (g_{c,c} delta_{m-l})
+// come from that one reciprocal square root with the cached 1/delta, so
+// the critical path holds one rsqrt and one reciprocal (1/eta_m, off the
+// rsqrt's path).
 // ------------------------------------------------------------------------
 template <typename T, int L>
-__device__ void scalar_step(Smem<T> &s, Coef<T> &cf, const double *raw, const SolveArgs<T> &a,
-                            long long i, double rn, double tau, long long budget)
+__device__ __forceinline__ void step_vectors(Coef<T> &cf, const SolveArgs<T> &a, int i)
 {
-    cf.end = -1;
-    cf.fmode = 0;
-    cf.ncopy = 0;
-    const long long m = i - L;
-    if (i < L) {
-        cf.mode = 0;
-        cf.k6 = 0;
-        cf.sig = (T)a.sigma[i];
-    } else {
-        const long long c = i - L + 1;
-        double *col = s.G[c % (L + 1)];
-        auto g = [&](long long j, long long cc) -> double {
-            if (j < 0 || j < cc - 2 * L || j > cc) return 0.0;
-            return s.G[cc % (L + 1)][j - cc + 2 * L];
-        };
-        auto ginv = [&](long long j) -> double { return s.Ginv[j % (L + 1)]; };
-        auto del = [&](long long j) -> double { return j < 0 ? 0.0 : s.del[j % (L + 1)]; };
-        auto gam = [&](long long j) -> double { return s.gam[j % (L + 1)]; };
-        // raw column c (dots of iteration i-l): position q is row c-2l+q
-#pragma unroll
-        for (int q = 0; q <= 2 * L; ++q) col[q] = (c - 2 * L + q >= 0) ? raw[q] : 0.0;
-        const long long lo = (c - 2 * L > 0) ? c - 2 * L : 0;
-        if (!a.dots_2l1)   // Sec. 2.2: g_{j,c} = g_{c-l,j+l} for j = c-2l .. c-l-1
-            for (long long j = lo; j <= c - L - 1; ++j) col[j - c + 2 * L] = g(c - L, j + L);
-        for (long long j = (c - L + 1 > 0 ? c - L + 1 : 0); j <= c - 1; ++j) {
-            double t = col[j - c + 2 * L];
-            for (long long k = lo; k <= j - 1; ++k) t -= g(k, j) * col[k - c + 2 * L];
-            col[j - c + 2 * L] = t * ginv(j);
-        }
-        const double graw = col[2 * L];
-        double arg = graw;
-        for (long long k = lo; k <= c - 1; ++k) arg -= col[k - c + 2 * L] * col[k - c + 2 * L];
-        const double gmm = g(m, m), igmm = ginv(m);
-        const double gmc = col[m - c + 2 * L];
-        double gm;
-        if (m < L)
-            gm = (gmc + a.sigma[m] * gmm - (m >= 1 ? g(m - 1, m) * del(m - 1) : 0.0)) * igmm;
-        else
-            gm = (gmm * gam(m - L) + gmc * del(m - L) - g(m - 1, m) * del(m - 1)) * igmm;
-        s.gam[m % (L + 1)] = gm;
-        const double thr = 64.0 * Eps<T>::v * fabs(graw);
-        if (!isfinite(arg) || !isfinite(gm)) {
-            cf.end = kSegNonfinite;
-            cf.kseg = m;
-            return;
-        }
-        if (arg <= thr) {
-            if (arg >= -thr) {   // lucky breakdown: x_{m+1} is exact in this Krylov space
-                if (m == 0) {
-                    s.eta[0] = gm;
-                    s.zeta[0] = rn;
-                    cf.fmode = 2;
-                    cf.pv = (T)(1.0 / gm);
-                    cf.f2 = (T)rn;
-                } else {
-                    const double lam = del(m - 1) * s.ieta[(m - 1) & 1];
-                    const double em = gm - lam * del(m - 1);
-                    const double iem = 1.0 / em;
-                    const double zm = -lam * s.zeta[(m - 1) & 1];
-                    cf.fmode = 1;
-                    cf.f1 = (T)s.zeta[(m - 1) & 1];
-                    cf.pv = (T)iem;
-                    cf.pp = (T)(-del(m - 1) * iem);
-                    cf.f2 = (T)zm;
-                }
-                cf.end = kSegLucky;
-                cf.kseg = m + 1;
-            } else {             // breakdown: keep x_m and restart
-                cf.fmode = 0;
-                cf.f1 = (T)((m >= 1) ? s.zeta[(m - 1) & 1] : 0.0);
-                cf.end = kSegBreakdown;
-                cf.kseg = m;
-            }
-            cf.v0 = ring(a, 0, m);
-            return;
-        }
-        const double gcc = sqrt(arg);
-        col[2 * L] = gcc;
-        const double dm = (m < L) ? gcc * igmm : gcc * del(m - L) * igmm;
-        s.del[m % (L + 1)] = dm;
-        const double invd = 1.0 / dm;
-        s.Ginv[c % (L + 1)] = 1.0 / gcc;   // needed from the next iteration on
-        cf.mode = 1;
-        cf.invd = (T)invd;
-        cf.al = (T)(-gm * invd);
-        cf.bm = (T)((m >= 1) ? -del(m - 1) * invd : 0.0);
-        cf.prev0 = (m >= 1);
-#pragma unroll
-        for (int k = 0; k < L; ++k) cf.ak[k] = (T)((a.sigma[k] - gm) * invd);
-        if (i == L) {
-            s.eta[0] = gm;
-            s.zeta[0] = rn;
-            s.ieta[0] = 1.0 / gm;
-            cf.k6 = 1;
-            cf.pv = (T)s.ieta[0];
-        } else {
-            const double lam = del(m - 1) * s.ieta[(m - 1) & 1];
-            const double em = gm - lam * del(m - 1);
-            const double iem = 1.0 / em;
-            const double zm = -lam * s.zeta[(m - 1) & 1];
-            cf.k6 = 2;
-            cf.zx = (T)s.zeta[(m - 1) & 1];
-            cf.pv = (T)iem;
-            cf.pp = (T)(-del(m - 1) * iem);
-            s.eta[m & 1] = em;
-            s.ieta[m & 1] = iem;
-            s.zeta[m & 1] = zm;
-            if (!isfinite(zm)) {
-                cf.end = kSegNonfinite;
-                cf.kseg = m;
-                return;
-            }
-            if (fabs(zm) < tau || m >= budget) {
-                cf.end = (fabs(zm) < tau) ? kSegConverged : kSegMaxit;
-                cf.fmode = 0;
-                cf.f1 = cf.zx;
-                cf.kseg = m;
-                cf.v0 = ring(a, 0, m);
-                return;
-            }
-        }
-    }
-    // vectors of this iteration
+    const int m = i - L;
+    const bool rec = i >= L;
     cf.zl_cur = ring(a, L, i);
     cf.zl_prev = (i >= 1) ? ring(a, L, i - 1) : nullptr;
     cf.zl_new = ring(a, L, i + 1);
-    if (cf.mode == 0) {
-        for (int k = (int)i + 1; k <= L - 1; ++k) cf.cpy[cf.ncopy++] = ring(a, k, i + 1);
+    if (!rec) {
+        for (int k = i + 1; k <= L - 1; ++k) cf.cpy[cf.ncopy++] = ring(a, k, i + 1);
     } else {
 #pragma unroll
         for (int k = 0; k < L; ++k) {
@@ -723,25 +608,183 @@ __device__ void scalar_step(Smem<T> &s, Coef<T> &cf, const double *raw, const So
     // K5 operands: position q is row j = i-2l+1+q of column i+1 (Algorithm 1, K5)
 #pragma unroll
     for (int q = 0; q <= 2 * L; ++q) {
-        const long long j = i - 2 * L + 1 + q;
+        const int j = i - 2 * L + 1 + q;
         int src = 0;
         const T *ptr = nullptr;
         if (j >= 0) {
             if (q < L) {
                 if (a.dots_2l1) { src = 1; ptr = ring(a, 0, j); }
             } else if (q == L) {
-                if (i >= L) src = 3;
+                if (rec) src = 3;
                 else { src = 1; ptr = ring(a, 0, j); }
             } else {
                 if (j == i + 1) src = 2;
                 else if (j == i) src = 4;
-                else if (j == i - 1 && cf.mode == 1) src = 5;
+                else if (j == i - 1 && rec) src = 5;
                 else { src = 1; ptr = ring(a, L, j); }
             }
         }
         cf.dsrc[q] = src;
         cf.dptr[q] = ptr;
     }
+}
+
+template <typename T, int L>
+__device__ __forceinline__ void scalar_step_body(Smem<T> &s, Coef<T> &cf, const double *raw,
+                                                 const SolveArgs<T> &a, int i, double rn,
+                                                 double tau, long long budget)
+{
+    cf.end = -1;
+    cf.fmode = 0;
+    cf.ncopy = 0;
+    const int m = i - L;
+    step_vectors<T, L>(cf, a, i);
+    if (i < L) {
+        cf.mode = 0;
+        cf.k6 = 0;
+        cf.sig = (T)a.sigma[i];
+        return;
+    }
+    const int c = i - L + 1;
+    double *col = s.G[c % (L + 1)];
+    auto g = [&](int j, int cc) -> double {
+        if (j < 0 || j < cc - 2 * L || j > cc) return 0.0;
+        return s.G[cc % (L + 1)][j - cc + 2 * L];
+    };
+    auto ginv = [&](int j) -> double { return s.Ginv[j % (L + 1)]; };
+    auto del = [&](int j) -> double { return j < 0 ? 0.0 : s.del[j % (L + 1)]; };
+    auto idel = [&](int j) -> double { return s.idel[j % (L + 1)]; };
+    auto gam = [&](int j) -> double { return s.gam[j % (L + 1)]; };
+    // raw column c (dots of iteration i-l): position q is row c-2l+q
+#pragma unroll
+    for (int q = 0; q <= 2 * L; ++q) col[q] = (c - 2 * L + q >= 0) ? raw[q] : 0.0;
+    const int lo = (c - 2 * L > 0) ? c - 2 * L : 0;
+    if (!a.dots_2l1)   // Sec. 2.2: g_{j,c} = g_{c-l,j+l} for j = c-2l .. c-l-1
+        for (int j = lo; j <= c - L - 1; ++j) col[j - c + 2 * L] = g(c - L, j + L);
+    for (int j = (c - L + 1 > 0 ? c - L + 1 : 0); j <= c - 1; ++j) {
+        double t = col[j - c + 2 * L];
+        for (int k = lo; k <= j - 1; ++k) t -= g(k, j) * col[k - c + 2 * L];
+        col[j - c + 2 * L] = t * ginv(j);
+    }
+    const double graw = col[2 * L];
+    double arg = graw;
+    for (int k = lo; k <= c - 1; ++k) arg -= col[k - c + 2 * L] * col[k - c + 2 * L];
+    const double rg = rsqrt(arg);          // NaN or inf when arg <= 0: unused then
+    const double gmm = g(m, m), igmm = ginv(m);
+    const double gmc = col[m - c + 2 * L];
+    const double dm1 = del(m - 1);        // delta_{m-1} (0 for m = 0)
+    double gm;
+    if (m < L)
+        gm = (gmc + a.sigma[m] * gmm - (m >= 1 ? g(m - 1, m) * dm1 : 0.0)) * igmm;
+    else
+        gm = (gmm * gam(m - L) + gmc * del(m - L) - g(m - 1, m) * dm1) * igmm;
+    s.gam[m % (L + 1)] = gm;
+    // K6 scalars for m >= 1 (Sec. 2.1): lambda_m, eta_m, zeta_m need no g_{c,c}
+    double lam = 0.0, em = gm, iem = 0.0, zm = 0.0;
+    if (m >= 1) {
+        lam = dm1 * s.ieta[(m - 1) & 1];
+        em = gm - lam * dm1;
+        iem = 1.0 / em;
+        zm = -lam * s.zeta[(m - 1) & 1];
+    }
+    const double thr = 64.0 * Eps<T>::v * fabs(graw);
+    if (!isfinite(arg) || !isfinite(gm)) {
+        cf.end = kSegNonfinite;
+        cf.kseg = m;
+        return;
+    }
+    if (arg <= thr) {
+        if (arg >= -thr) {   // lucky breakdown: x_{m+1} is exact in this Krylov space
+            if (m == 0) {
+                s.eta[0] = gm;
+                s.zeta[0] = rn;
+                cf.fmode = 2;
+                cf.pv = (T)(1.0 / gm);
+                cf.f2 = (T)rn;
+            } else {
+                cf.fmode = 1;
+                cf.f1 = (T)s.zeta[(m - 1) & 1];
+                cf.pv = (T)iem;
+                cf.pp = (T)(-dm1 * iem);
+                cf.f2 = (T)zm;
+            }
+            cf.end = kSegLucky;
+            cf.kseg = m + 1;
+        } else {             // breakdown: keep x_m and restart
+            cf.fmode = 0;
+            cf.f1 = (T)((m >= 1) ? s.zeta[(m - 1) & 1] : 0.0);
+            cf.end = kSegBreakdown;
+            cf.kseg = m;
+        }
+        cf.v0 = ring(a, 0, m);
+        return;
+    }
+    // g_{c,c} = sqrt(arg) and the recurrence coefficients from 1/sqrt(arg):
+    // delta_m = g_{c,c} [delta_{m-l}] / g_{m,m}, 1/delta_m = g_{m,m} / (g_{c,c} [delta_{m-l}])
+    const double gcc = arg * rg;
+    col[2 * L] = gcc;
+    s.Ginv[c % (L + 1)] = rg;
+    const double invd = (m < L) ? rg * gmm : rg * gmm * idel(m - L);
+    const double dm = (m < L) ? gcc * igmm : gcc * del(m - L) * igmm;
+    s.del[m % (L + 1)] = dm;
+    s.idel[m % (L + 1)] = invd;
+    cf.mode = 1;
+    cf.invd = (T)invd;
+    cf.al = (T)(-gm * invd);
+    cf.bm = (T)((m >= 1) ? -dm1 * invd : 0.0);
+    cf.prev0 = (m >= 1);
+#pragma unroll
+    for (int k = 0; k < L; ++k) cf.ak[k] = (T)((a.sigma[k] - gm) * invd);
+    if (i == L) {
+        s.eta[0] = gm;
+        s.zeta[0] = rn;
+        s.ieta[0] = 1.0 / gm;
+        cf.k6 = 1;
+        cf.pv = (T)s.ieta[0];
+    } else {
+        cf.k6 = 2;
+        cf.zx = (T)s.zeta[(m - 1) & 1];
+        cf.pv = (T)iem;
+        cf.pp = (T)(-dm1 * iem);
+        s.eta[m & 1] = em;
+        s.ieta[m & 1] = iem;
+        s.zeta[m & 1] = zm;
+        if (!isfinite(zm)) {
+            cf.end = kSegNonfinite;
+            cf.kseg = m;
+            return;
+        }
+        if (fabs(zm) < tau || m >= budget) {
+            cf.end = (fabs(zm) < tau) ? kSegConverged : kSegMaxit;
+            cf.fmode = 0;
+            cf.f1 = cf.zx;
+            cf.kseg = m;
+            cf.v0 = ring(a, 0, m);
+            return;
+        }
+    }
+}
+
+template <typename T, int L>
+__device__ __noinline__ void scalar_step_call(Smem<T> &s, Coef<T> &cf, const double *raw,
+                                              const SolveArgs<T> &a, int i, double rn, double tau,
+                                              long long budget)
+{
+    scalar_step_body<T, L>(s, cf, raw, a, i, rn, tau, budget);
+}
+
+// The scalar step inline, except in the FP32 whole-grid kernels: there the
+// sweep runs at 80 registers (3 CTAs per SM) and an inlined scalar step
+// changes its register allocation enough to cost ~15% at 256^3 (measured);
+// the out-of-line call costs ~0.3 us per iteration, which the FP64 and
+// one-CTA paths (latency-bound on small systems) keep.
+template <typename T, int L, bool OOL>
+__device__ __forceinline__ void scalar_step(Smem<T> &s, Coef<T> &cf, const double *raw,
+                                            const SolveArgs<T> &a, int i, double rn, double tau,
+                                            long long budget)
+{
+    if constexpr (OOL) scalar_step_call<T, L>(s, cf, raw, a, i, rn, tau, budget);
+    else scalar_step_body<T, L>(s, cf, raw, a, i, rn, tau, budget);
 }
 
 // Per-thread accumulator of one dot product over the units a thread sweeps.
@@ -866,6 +909,7 @@ __device__ void plcg_body(const SolveArgs<T> &a, Smem<T> &s, Grp &grp)
 {
     constexpr int UNIT = kBlock * VEC;
     constexpr bool kF32 = (sizeof(T) == 4);
+    constexpr bool kOolScalar = kF32 && std::is_same<Grp, GridGroup<T>>::value;
     const int64_t n = a.n;
     const int64_t nunits = (n + UNIT - 1) / UNIT;
     const int tid = threadIdx.x;
@@ -969,7 +1013,7 @@ __device__ void plcg_body(const SolveArgs<T> &a, Smem<T> &s, Grp &grp)
         // l iterations later) with the local work, on one GPU.
         const bool la = (L >= 2) && a.lookahead;
         const int nsw = la ? kBlock - 32 : kBlock;   // threads that sweep
-        if (tid == 0) scalar_step<T, L>(s, s.cfb[0], s.raw, a, 0, rn, tau, budget);
+        if (tid == 0) scalar_step<T, L, kOolScalar>(s, s.cfb[0], s.raw, a, 0, rn, tau, budget);
         __syncthreads();
         for (long long i = 0;; ++i) {
             const Coef<T> &cf = s.cfb[i & 1];
@@ -1026,7 +1070,7 @@ __device__ void plcg_body(const SolveArgs<T> &a, Smem<T> &s, Grp &grp)
                 if (i + 1 >= L)
                     grp.template get_dots_warp<2 * L + 1>(a, s, (int)((i + 1 - L) % (L + 1)), s.raw2);
                 if ((tid & 31) == 0)
-                    scalar_step<T, L>(s, s.cfb[(i + 1) & 1], s.raw2, a, i + 1, rn, tau, budget);
+                    scalar_step<T, L, kOolScalar>(s, s.cfb[(i + 1) & 1], s.raw2, a, (int)(i + 1), rn, tau, budget);
                 __syncwarp();
             }
             // ---- one full iteration sweep: K1, K4, K5 (partials), K6.  A thread
@@ -1195,7 +1239,7 @@ __device__ void plcg_body(const SolveArgs<T> &a, Smem<T> &s, Grp &grp)
                     if (i + 1 >= L)
                         grp.template get_dots_warp<2 * L + 1>(a, s, (int)((i + 1 - L) % (L + 1)), s.raw);
                     if (tid == 0)
-                        scalar_step<T, L>(s, s.cfb[(i + 1) & 1], s.raw, a, i + 1, rn, tau, budget);
+                        scalar_step<T, L, kOolScalar>(s, s.cfb[(i + 1) & 1], s.raw, a, (int)(i + 1), rn, tau, budget);
                 }
                 __syncthreads();
             }
