@@ -16,6 +16,11 @@ const void *kernel_ptr(bool f32, int op, int vec, int l, bool cg)
     return vec == 4 ? kptr_f32_st4(l, cg) : kptr_f32_st1(l, cg);
 }
 
+const void *batched_kernel_ptr(bool f32, int l, bool cg)
+{
+    return f32 ? batched_kernel_ptr_f32(l, cg) : batched_kernel_ptr_f64(l, cg);
+}
+
 __global__ void round_to_f32_kernel(const double *src, float *dst, int64_t n)
 {
     for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;

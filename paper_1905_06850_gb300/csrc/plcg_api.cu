@@ -610,7 +610,7 @@ static plcg_status run_batched(int count, plcg_matrix *const *A, const double *c
     const bool f32 = sizeof(T) == 4;
     const bool cg = prm->method == PLCG_METHOD_CG;
     const int l = cg ? 1 : prm->l;
-    const void *func = batched_kernel_ptr(f32, l);
+    const void *func = batched_kernel_ptr(f32, l, cg);
     if (!func) return fail(PLCG_ERR_UNIMPL, "plcg_solve_batched: l must be 1..4");
     cudaStream_t stream = A[0]->stream;
     int dev = A[0]->device;

@@ -12,9 +12,10 @@ namespace plcg {
 // pipeline length l, classic CG?); nullptr when not instantiated.
 const void *kernel_ptr(bool f32, int op, int vec, int l, bool cg);
 
-// Address of the batched kernel (one system per CTA) for l = 1..4; the
-// classic-CG variant is the l = 1 instantiation with method = 1.
-const void *batched_kernel_ptr(bool f32, int l);
+// Address of the batched kernel for p(l)-CG (l = 1..4) or classic CG.
+const void *batched_kernel_ptr(bool f32, int l, bool cg);
+const void *batched_kernel_ptr_f32(int l, bool cg);
+const void *batched_kernel_ptr_f64(int l, bool cg);
 
 // Per-translation-unit getters used by kernel_ptr.
 const void *kptr_f64_st2(int l, bool cg);

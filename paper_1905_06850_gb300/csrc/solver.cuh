@@ -1515,10 +1515,14 @@ __global__ void __launch_bounds__(kBlock, 3) cg_kernel(SolveArgs<T> a)
 // __syncthreads as its barrier.  Converged systems retire at once and free
 // their CTA or gang for the next system.
 // ------------------------------------------------------------------------
-// Row groups per thread in the one-CTA path, where a CTA streams a whole
-// system and needs several loads in flight per thread (fewer for larger l,
-// whose sweep holds more vectors in registers).
-template <int L> constexpr int kBatchRPT = (L == 1) ? 4 : 2;
+// Launch shape of the batched kernel, per method: CTAs per SM (the
+// register budget) and row groups per thread in the one-CTA path, where a
+// CTA streams a whole system and latency is hidden by warps and by loads in
+// flight per thread.  Chosen by timing the 4096-system workload on GB300
+// over 2-6 CTAs per SM and 1, 2 or 4 row groups: 4 CTAs per SM for every
+// method; 4 row groups for classic CG and p(1)-CG, 1 for p(l >= 2)-CG.
+template <int L, bool CG> constexpr int kBatchMinBlocks = 4;
+template <int L, bool CG> constexpr int kBatchRPT = (CG || L == 1) ? 4 : 1;
 
 template <typename T>
 __device__ __forceinline__ void batch_args(const BatchArgs<T> &ba, const BatchSys &sy, T *ws,
@@ -1550,8 +1554,8 @@ __device__ __forceinline__ void batch_args(const BatchArgs<T> &ba, const BatchSy
                                      ((((size_t)(nvec + 2) * nv * sizeof(T)) + 255) / 256) * 256);
 }
 
-template <typename T, int L>
-__global__ void __launch_bounds__(kBlock, 2) batched_kernel(BatchArgs<T> ba)
+template <typename T, int L, bool CG>
+__global__ void __launch_bounds__(kBlock, kBatchMinBlocks<L, CG>) batched_kernel(BatchArgs<T> ba)
 {
     __shared__ Smem<T> s;
     __shared__ int s_next;
@@ -1580,7 +1584,7 @@ __global__ void __launch_bounds__(kBlock, 2) batched_kernel(BatchArgs<T> ba)
             const int sysi = s_next;
             if (sysi < 0) break;
             batch_args(ba, ba.sys[sysi], ws, a);
-            if (a.method == 1) cg_body<T, 1, kOpStencil>(a, s, grp);
+            if constexpr (CG) cg_body<T, 1, kOpStencil>(a, s, grp);
             else plcg_body<T, L, 1, kOpStencil>(a, s, grp);
             if (ld_volatile(grp.abort_flag)) return;
             // every member has read gslot before the leader overwrites it: they
@@ -1597,8 +1601,8 @@ __global__ void __launch_bounds__(kBlock, 2) batched_kernel(BatchArgs<T> ba)
         SolveArgs<T> a;
         batch_args(ba, ba.sys[ba.order_small[k]], ws, a);
         BlockGroup<T> grp;
-        if (a.method == 1) cg_body<T, 1, kOpStencil, BlockGroup<T>, 4>(a, s, grp);
-        else plcg_body<T, L, 1, kOpStencil, BlockGroup<T>, kBatchRPT<L>>(a, s, grp);
+        if constexpr (CG) cg_body<T, 1, kOpStencil, BlockGroup<T>, kBatchRPT<L, CG>>(a, s, grp);
+        else plcg_body<T, L, 1, kOpStencil, BlockGroup<T>, kBatchRPT<L, CG>>(a, s, grp);
     }
 }
 
