@@ -190,9 +190,13 @@ extern "C" plcg_status plcg_create_csr(int64_t n, int64_t nnz, const int64_t *ro
     if (st != PLCG_OK) { plcg_destroy(A); return st; }
     const cudaMemcpyKind kind = on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice;
     const size_t vsz = (prec == PLCG_FP64) ? sizeof(double) : sizeof(float);
+    // col and val carry 4 zeroed entries of padding: the solver bulk-copies
+    // entry ranges rounded out to 16-byte boundaries
     cudaError_t e = cudaMalloc(&A->rowptr, (n + 1) * sizeof(int64_t));
-    if (e == cudaSuccess) e = cudaMalloc(&A->col, std::max<int64_t>(nnz, 1) * sizeof(int32_t));
-    if (e == cudaSuccess) e = cudaMalloc(&A->val, std::max<int64_t>(nnz, 1) * vsz);
+    if (e == cudaSuccess) e = cudaMalloc(&A->col, (nnz + 4) * sizeof(int32_t));
+    if (e == cudaSuccess) e = cudaMalloc(&A->val, (nnz + 4) * vsz);
+    if (e == cudaSuccess) e = cudaMemset(A->col, 0, (nnz + 4) * sizeof(int32_t));
+    if (e == cudaSuccess) e = cudaMemset(A->val, 0, (nnz + 4) * vsz);
     if (e == cudaSuccess) e = cudaMemcpy(A->rowptr, rowptr, (n + 1) * sizeof(int64_t), kind);
     if (e == cudaSuccess && nnz) e = cudaMemcpy(A->col, col, nnz * sizeof(int32_t), kind);
     if (e == cudaSuccess && nnz) {
@@ -321,8 +325,16 @@ static plcg_status build_solve(const plcg_matrix *A, const double *b, double *x,
     }
     const void *func = kernel_ptr(f32, op, vec, cg ? 0 : l, cg);
     if (!func) return fail(PLCG_ERR_UNIMPL, "no kernel for prec=%d op=%d vec=%d l=%d", (int)f32, op, vec, l);
+    // CSR kernels stage each unit's entries in dynamic shared memory (FP64
+    // classic CG excepted, see cg_body)
+    const unsigned dsmem = (op != kOpStencil && (!cg || f32)) ? csr_stage_bytes((unsigned)sizeof(T)) : 0u;
+    if (dsmem) {
+        CUDA_TRY(cudaFuncSetAttribute(func, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)dsmem));
+        CUDA_TRY(cudaFuncSetAttribute(func, cudaFuncAttributePreferredSharedMemoryCarveout,
+                                      (int)cudaSharedmemCarveoutMaxShared));
+    }
     int per_sm = 0;
-    CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, func, kBlock, 0));
+    CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, func, kBlock, dsmem));
     if (per_sm < 1) return fail(PLCG_ERR_CUDA, "solver kernel cannot be resident");
     const int64_t unit = (int64_t)kBlock * vec;
     const int64_t nunits = (n + unit - 1) / unit;
@@ -402,6 +414,7 @@ static plcg_status build_solve(const plcg_matrix *A, const double *b, double *x,
     // l >= 2: compute each iteration's scalars during the previous sweep where
     // that latency is a visible share of an iteration (smaller systems)
     a.lookahead = (!cg && l >= 2 && n < (int64_t(1) << 22)) ? 1 : 0;
+    a.dsmem = dsmem;
     return PLCG_OK;
 }
 
@@ -415,7 +428,7 @@ static plcg_status launch_built(const SolveArgs<T> &a0, const void *func, int64_
     CUDA_TRY(cudaMemsetAsync(a.bar, 0, 256, stream));
     CUDA_TRY(cudaMemsetAsync(a.out, 0, sizeof(DevResult), stream));
     void *args[] = {&a};
-    CUDA_TRY(cudaLaunchCooperativeKernel(func, dim3((unsigned)P), dim3(kBlock), args, 0, stream));
+    CUDA_TRY(cudaLaunchCooperativeKernel(func, dim3((unsigned)P), dim3(kBlock), args, a.dsmem, stream));
     return PLCG_OK;
 }
 

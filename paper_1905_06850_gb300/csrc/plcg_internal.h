@@ -100,7 +100,16 @@ struct SolveArgs {
     unsigned long long poll_limit;
     int force_timeout;
     int lookahead;            // l >= 2: compute the next iteration's scalars during the sweep
+    unsigned dsmem;           // dynamic shared memory of the launch (CSR entry staging)
 };
+
+// CSR entries (column index + value) one CTA stages in shared memory per
+// sweep unit; units with more entries read them from global memory.
+constexpr int kCsrStageCap = 8192;
+constexpr unsigned csr_stage_bytes(unsigned value_bytes)
+{
+    return 16u + (unsigned)kCsrStageCap * (4u + value_bytes);
+}
 
 // One system of a batched solve (stencil operators only).
 struct BatchSys {

@@ -88,6 +88,65 @@ __device__ __forceinline__ bool grid_barrier(unsigned *bar, unsigned &epoch,
 }
 
 // ------------------------------------------------------------------------
+// Bulk-copy staging (TMA, cp.async.bulk) with an mbarrier in shared memory.
+// ------------------------------------------------------------------------
+__device__ __forceinline__ uint32_t smem_addr(const void *p)
+{
+    return (uint32_t)__cvta_generic_to_shared(p);
+}
+
+__device__ __forceinline__ void mbar_init(uint64_t *bar, uint32_t count)
+{
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_addr(bar)), "r"(count) : "memory");
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+}
+
+// The issuing thread's generic-proxy view of the buffer (the previous unit's
+// reads, ordered before it by a CTA barrier) precedes the async-proxy writes.
+__device__ __forceinline__ void fence_proxy_async_smem()
+{
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+}
+
+__device__ __forceinline__ void mbar_arrive_expect_tx(uint64_t *bar, uint32_t bytes)
+{
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;"
+                 ::"r"(smem_addr(bar)), "r"(bytes) : "memory");
+}
+
+// Global -> shared bulk copy of `bytes` (multiple of 16, both addresses
+// 16-byte aligned) completing its bytes on the mbarrier.
+__device__ __forceinline__ void bulk_copy_g2s(void *dst, const void *src, uint32_t bytes, uint64_t *bar)
+{
+    asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];"
+                 ::"r"(smem_addr(dst)), "l"(src), "r"(bytes), "r"(smem_addr(bar)) : "memory");
+}
+
+__device__ __forceinline__ bool mbar_try_wait(uint64_t *bar, uint32_t parity)
+{
+    uint32_t done;
+    asm volatile("{\n\t.reg .pred p;\n\t"
+                 "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+                 "selp.u32 %0, 1, 0, p;\n\t}"
+                 : "=r"(done) : "r"(smem_addr(bar)), "r"(parity) : "memory");
+    return done != 0;
+}
+
+// Bounded wait for phase `parity` of the mbarrier; false when the bound ran out.
+__device__ __forceinline__ bool mbar_wait(uint64_t *bar, uint32_t parity, unsigned long long limit)
+{
+    for (unsigned long long k = 0; k <= limit; ++k)
+        if (mbar_try_wait(bar, parity)) return true;
+    return false;
+}
+
+// Barrier of the first `count` threads of the CTA (named barrier 1).
+__device__ __forceinline__ void bar_sync_first(int count)
+{
+    asm volatile("bar.sync 1, %0;" ::"r"(count) : "memory");
+}
+
+// ------------------------------------------------------------------------
 // Reductions (fixed order, so every CTA gets the same bits).
 // ------------------------------------------------------------------------
 template <int ND>
@@ -322,6 +381,65 @@ __device__ __forceinline__ V csr_row(const CsrDesc &A, const Ld &ld, uint32_t ro
     return s;
 }
 
+// CSR row whose entries were staged in shared memory: scol / sval hold the
+// entries from global position e0s on.
+template <typename V, typename C, class Ld>
+__device__ __forceinline__ V csr_row_staged(const CsrDesc &A, const int32_t *scol, const C *sval,
+                                            int64_t e0s, const Ld &ld, uint32_t row)
+{
+    const uint32_t k0 = (uint32_t)(__ldg(A.rowptr + row) - e0s);
+    const uint32_t k1 = (uint32_t)(__ldg(A.rowptr + row + 1) - e0s);
+    V s = V(0);
+    for (uint32_t k = k0; k < k1; ++k) s = fma((V)sval[k], ld.one((uint32_t)scol[k]), s);
+    return s;
+}
+
+// Shared-memory staging area of the CSR kernels (dynamic shared memory):
+// an mbarrier, then kCsrStageCap column indices and kCsrStageCap values.
+template <typename T>
+struct CsrStage {
+    uint64_t *bar;
+    int32_t *col;
+    T *val;
+    uint32_t parity = 0;      // phase parity of bar for the next staged unit
+    __device__ __forceinline__ explicit CsrStage(unsigned char *dsm)
+        : bar(reinterpret_cast<uint64_t *>(dsm)), col(reinterpret_cast<int32_t *>(dsm + 16)),
+          val(reinterpret_cast<T *>(dsm + 16 + 4 * kCsrStageCap))
+    {
+    }
+    // Stage the entries of rows [r0, r1) -- the contiguous range
+    // [rowptr[r0], rowptr[r1]) rounded out to 16 bytes (the arrays carry the
+    // padding) -- with one bulk copy for the column indices and one for the
+    // values, issued by thread 0 once the first `nthreads` threads are done
+    // with the previous unit's entries; every caller waits for them.
+    // Returns false (read global memory) when the range exceeds the buffer;
+    // *e0s is the global position of the first staged entry.
+    __device__ __forceinline__ bool stage(const CsrDesc &csr, uint32_t r0, uint32_t r1, int nthreads,
+                                          int64_t *e0s, unsigned long long limit, int *abort_flag)
+    {
+        const int64_t e0 = __ldg(csr.rowptr + r0), e1 = __ldg(csr.rowptr + r1);
+        *e0s = e0 & ~int64_t(3);
+        const int64_t cnt = ((e1 + 3) & ~int64_t(3)) - *e0s;
+        const bool on = cnt > 0 && cnt <= kCsrStageCap;
+        bar_sync_first(nthreads);
+        if (on) {
+            if (threadIdx.x == 0) {
+                fence_proxy_async_smem();
+                const uint32_t cb = (uint32_t)cnt * 4u, vb = (uint32_t)cnt * (uint32_t)sizeof(T);
+                mbar_arrive_expect_tx(bar, cb + vb);
+                bulk_copy_g2s(col, csr.col + *e0s, cb, bar);
+                bulk_copy_g2s(val, static_cast<const T *>(csr.val) + *e0s, vb, bar);
+            }
+            if (!mbar_wait(bar, parity, limit)) {
+                atomicExch(abort_flag, 1);          // the solve ends at the next barrier
+                mbar_wait(bar, parity, limit);      // the copy in flight lands first
+            }
+            parity ^= 1u;
+        }
+        return on;
+    }
+};
+
 // (c, nb) with (A z)_g = kc * c + kn * nb: stencil (center, off), CSR (0, 1).
 template <typename V, typename C, int VEC, int OP, class Ld>
 __device__ __forceinline__ void op_parts(const StencilDesc &st, const CsrDesc &csr, const Ld &ld,
@@ -420,6 +538,8 @@ struct Smem {
     double bnorm[2];
     double raw2[kMaxDots];           // the scalar warp's copy of a reduced dot column
     Coef<T> cfb[2];                  // coefficients of iterations i (i & 1) and i + 1
+    long long stg_e0;                // CSR staging: global position of the unit's first staged entry
+    int stg_on;                      // CSR staging: this unit's entries are in shared memory
     int ok;
 };
 
@@ -910,6 +1030,15 @@ __device__ void plcg_body(const SolveArgs<T> &a, Smem<T> &s, Grp &grp)
     constexpr int UNIT = kBlock * VEC;
     constexpr bool kF32 = (sizeof(T) == 4);
     constexpr bool kOolScalar = kF32 && std::is_same<Grp, GridGroup<T>>::value;
+    // CSR on the whole grid: each sweep unit's entries are bulk-copied into
+    // shared memory (one contiguous range per unit) before its rows are read
+    constexpr bool kStage = OP != kOpStencil && std::is_same<Grp, GridGroup<T>>::value && RPT == 1;
+    extern __shared__ __align__(128) unsigned char plcg_dsm[];
+    CsrStage<T> stage(plcg_dsm);
+    if constexpr (kStage) {
+        if (threadIdx.x == 0) mbar_init(stage.bar, 1);
+        __syncthreads();
+    }
     const int64_t n = a.n;
     const int64_t nunits = (n + UNIT - 1) / UNIT;
     const int tid = threadIdx.x;
@@ -1113,6 +1242,11 @@ __device__ void plcg_body(const SolveArgs<T> &a, Smem<T> &s, Grp &grp)
                         g0[r] = u * usw + ((uint32_t)r * nsw + tid) * VEC;
                         ok[r] = g0[r] < nn;
                     }
+                    bool stg = false;
+                    int64_t e0s = 0;
+                    if constexpr (kStage)
+                        stg = stage.stage(csr, u * usw, min(u * usw + usw, nn), nsw, &e0s, a.poll_limit,
+                                          &a.out->abort);
                     // -- loads
                     T c[RPT][VEC], nb[RPT][VEC], zp[RPT][VEC], cur[RPT][L][VEC], pk[RPT][L][VEC];
                     T pv[RPT][VEC], xv[RPT][VEC];
@@ -1123,7 +1257,16 @@ __device__ void plcg_body(const SolveArgs<T> &a, Smem<T> &s, Grp &grp)
                         for (int v = 0; v < VEC; ++v) zp[r][v] = T(0);
                         dg[r] = T(1);
                         if (!ok[r]) continue;
-                        op_parts<T, T, VEC, OP>(st, csr, Ld1<T>{C.zl_cur}, g0[r], c[r], nb[r]);   // K1 operands
+                        if constexpr (kStage) {   // K1 operands
+                            if (stg) {
+                                c[r][0] = C.zl_cur[g0[r]];
+                                nb[r][0] = csr_row_staged<T, T>(csr, stage.col, stage.val, e0s, Ld1<T>{C.zl_cur}, g0[r]);
+                            } else {
+                                op_parts<T, T, VEC, OP>(st, csr, Ld1<T>{C.zl_cur}, g0[r], c[r], nb[r]);
+                            }
+                        } else {
+                            op_parts<T, T, VEC, OP>(st, csr, Ld1<T>{C.zl_cur}, g0[r], c[r], nb[r]);
+                        }
                         if constexpr (OP == kOpCsrJacobi) {
                             // K1 with M = diag(A): z^(l)_{i+1} is built from M^{-1} A z^(l)_i
                             nb[r][0] *= __ldg(static_cast<const T *>(csr.dinv) + g0[r]);
@@ -1279,6 +1422,17 @@ __device__ void cg_body(const SolveArgs<T> &a, Smem<T> &s, Grp &grp)
     T *rc = kF32 ? a.rc : reinterpret_cast<T *>(a.r);
     T *xi = kF32 ? a.zring + 2 * n : reinterpret_cast<T *>(a.x);
     const uint32_t nn = (uint32_t)n;   // n < 2^31
+    // CSR on the whole grid, FP32: the SpMV sweep stages each unit's entries
+    // (as in p(l)-CG).  FP64 CG runs without: its 3 CTAs per SM would not fit
+    // the FP64 staging buffer (measured: 2 CTAs with staging are slower).
+    constexpr bool kStage = OP != kOpStencil && std::is_same<Grp, GridGroup<T>>::value && RPT == 1 &&
+                            sizeof(T) == 4;
+    extern __shared__ __align__(128) unsigned char plcg_dsm[];
+    CsrStage<T> stage(plcg_dsm);
+    if constexpr (kStage) {
+        if (threadIdx.x == 0) mbar_init(stage.bar, 1);
+        __syncthreads();
+    }
 
     long long iters = 0, spmvs = 0, restarts = 0, refinements = 0, segments = 0;
     int last_end = kSegConverged;
@@ -1381,14 +1535,30 @@ __device__ void cg_body(const SolveArgs<T> &a, Smem<T> &s, Grp &grp)
             for (uint32_t u = (uint32_t)grp.unit0(); u < (uint32_t)nunits_s; u += (uint32_t)grp.ustep()) {
                 T c[RPT][VEC], w[RPT][VEC], mi[RPT];
                 uint32_t g0[RPT];
+                bool stg = false;
+                int64_t e0s = 0;
+                if constexpr (kStage)
+                    stg = stage.stage(csr, u * USWEEP, min(u * USWEEP + USWEEP, nn), kBlock, &e0s,
+                                      a.poll_limit, &a.out->abort);
 #pragma unroll
                 for (int r = 0; r < RPT; ++r) {
                     g0[r] = u * USWEEP + ((uint32_t)r * kBlock + tid) * VEC;
                     if (g0[r] >= nn) continue;
-                    if (k == 0)
+                    if (stg) {
+                        if (k == 0) {
+                            const LdFirst<T> ld{rc};
+                            c[r][0] = ld.one(g0[r]);
+                            w[r][0] = csr_row_staged<T, T>(csr, stage.col, stage.val, e0s, ld, g0[r]);
+                        } else {
+                            const LdAxpy<T> ld{rc, po, (T)beta};
+                            c[r][0] = ld.one(g0[r]);
+                            w[r][0] = csr_row_staged<T, T>(csr, stage.col, stage.val, e0s, ld, g0[r]);
+                        }
+                    } else if (k == 0) {
                         op_apply<T, T, VEC, OP>(st, csr, cC, cO, LdFirst<T>{rc}, g0[r], c[r], w[r]);
-                    else
+                    } else {
                         op_apply<T, T, VEC, OP>(st, csr, cC, cO, LdAxpy<T>{rc, po, (T)beta}, g0[r], c[r], w[r]);
+                    }
                     if constexpr (OP == kOpCsrJacobi)
                         mi[r] = __ldg(static_cast<const T *>(csr.dinv) + g0[r]);
                 }
