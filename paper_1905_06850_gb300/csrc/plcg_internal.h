@@ -103,12 +103,14 @@ struct SolveArgs {
     unsigned dsmem;           // dynamic shared memory of the launch (CSR entry staging)
 };
 
-// CSR entries (column index + value) one CTA stages in shared memory per
-// sweep unit; units with more entries read them from global memory.
-constexpr int kCsrStageCap = 8192;
+// CSR entries (column index + value) each warp of a CSR kernel stages in
+// shared memory for its 32 rows of a sweep unit; warps whose rows have more
+// entries read them from global memory.  Layout of the dynamic shared
+// memory: 8 mbarriers (128 bytes), the warps' column indices, their values.
+constexpr int kCsrStageWarpCap = 1024;
 constexpr unsigned csr_stage_bytes(unsigned value_bytes)
 {
-    return 16u + (unsigned)kCsrStageCap * (4u + value_bytes);
+    return 128u + 8u * (unsigned)kCsrStageWarpCap * (4u + value_bytes);
 }
 
 // One system of a batched solve (stencil operators only).

@@ -140,12 +140,6 @@ __device__ __forceinline__ bool mbar_wait(uint64_t *bar, uint32_t parity, unsign
     return false;
 }
 
-// Barrier of the first `count` threads of the CTA (named barrier 1).
-__device__ __forceinline__ void bar_sync_first(int count)
-{
-    asm volatile("bar.sync 1, %0;" ::"r"(count) : "memory");
-}
-
 // ------------------------------------------------------------------------
 // Reductions (fixed order, so every CTA gets the same bits).
 // ------------------------------------------------------------------------
@@ -394,36 +388,48 @@ __device__ __forceinline__ V csr_row_staged(const CsrDesc &A, const int32_t *sco
     return s;
 }
 
-// Shared-memory staging area of the CSR kernels (dynamic shared memory):
-// an mbarrier, then kCsrStageCap column indices and kCsrStageCap values.
+// Per-warp staging of CSR entries in shared memory (dynamic shared memory,
+// layout in plcg_internal.h).  Every warp stages the entries of its own 32
+// rows of a sweep unit -- a contiguous range, since the rows are -- with one
+// bulk copy for the column indices and one for the values, completing on
+// the warp's mbarrier, and waits only for them: the CTA's warps are
+// independent copy/compute pipelines, so one warp's copy overlaps the others'
+// arithmetic.
 template <typename T>
 struct CsrStage {
     uint64_t *bar;
     int32_t *col;
     T *val;
-    uint32_t parity = 0;      // phase parity of bar for the next staged unit
+    uint32_t parity = 0;      // phase parity of bar for the warp's next staged rows
     __device__ __forceinline__ explicit CsrStage(unsigned char *dsm)
-        : bar(reinterpret_cast<uint64_t *>(dsm)), col(reinterpret_cast<int32_t *>(dsm + 16)),
-          val(reinterpret_cast<T *>(dsm + 16 + 4 * kCsrStageCap))
     {
+        const int w = threadIdx.x >> 5;
+        bar = reinterpret_cast<uint64_t *>(dsm) + w;
+        col = reinterpret_cast<int32_t *>(dsm + 128) + w * kCsrStageWarpCap;
+        val = reinterpret_cast<T *>(dsm + 128 + 8 * 4 * kCsrStageWarpCap) + w * kCsrStageWarpCap;
     }
-    // Stage the entries of rows [r0, r1) -- the contiguous range
-    // [rowptr[r0], rowptr[r1]) rounded out to 16 bytes (the arrays carry the
-    // padding) -- with one bulk copy for the column indices and one for the
-    // values, issued by thread 0 once the first `nthreads` threads are done
-    // with the previous unit's entries; every caller waits for them.
-    // Returns false (read global memory) when the range exceeds the buffer;
-    // *e0s is the global position of the first staged entry.
-    __device__ __forceinline__ bool stage(const CsrDesc &csr, uint32_t r0, uint32_t r1, int nthreads,
-                                          int64_t *e0s, unsigned long long limit, int *abort_flag)
+    // One thread per warp initialises the warp's mbarrier (then a CTA barrier).
+    __device__ __forceinline__ void init()
     {
+        if ((threadIdx.x & 31) == 0) mbar_init(bar, 1);
+    }
+    // Stage the entries of rows [r0, r1) (the warp's rows): the range
+    // [rowptr[r0], rowptr[r1]) rounded out to 16 bytes (the arrays carry the
+    // padding), issued by lane 0 once every lane is done with the previous
+    // rows' entries; every lane waits.  Returns false (read global memory)
+    // when the range exceeds the warp's buffer; *e0s is the global position of
+    // the first staged entry.
+    __device__ __forceinline__ bool stage(const CsrDesc &csr, uint32_t r0, uint32_t r1, int64_t *e0s,
+                                          unsigned long long limit, int *abort_flag)
+    {
+        if (r0 >= r1) return false;
         const int64_t e0 = __ldg(csr.rowptr + r0), e1 = __ldg(csr.rowptr + r1);
         *e0s = e0 & ~int64_t(3);
         const int64_t cnt = ((e1 + 3) & ~int64_t(3)) - *e0s;
-        const bool on = cnt > 0 && cnt <= kCsrStageCap;
-        bar_sync_first(nthreads);
+        const bool on = cnt > 0 && cnt <= kCsrStageWarpCap;
+        __syncwarp();
         if (on) {
-            if (threadIdx.x == 0) {
+            if ((threadIdx.x & 31) == 0) {
                 fence_proxy_async_smem();
                 const uint32_t cb = (uint32_t)cnt * 4u, vb = (uint32_t)cnt * (uint32_t)sizeof(T);
                 mbar_arrive_expect_tx(bar, cb + vb);
@@ -1036,7 +1042,7 @@ __device__ void plcg_body(const SolveArgs<T> &a, Smem<T> &s, Grp &grp)
     extern __shared__ __align__(128) unsigned char plcg_dsm[];
     CsrStage<T> stage(plcg_dsm);
     if constexpr (kStage) {
-        if (threadIdx.x == 0) mbar_init(stage.bar, 1);
+        stage.init();
         __syncthreads();
     }
     const int64_t n = a.n;
@@ -1244,9 +1250,10 @@ __device__ void plcg_body(const SolveArgs<T> &a, Smem<T> &s, Grp &grp)
                     }
                     bool stg = false;
                     int64_t e0s = 0;
-                    if constexpr (kStage)
-                        stg = stage.stage(csr, u * usw, min(u * usw + usw, nn), nsw, &e0s, a.poll_limit,
-                                          &a.out->abort);
+                    if constexpr (kStage) {   // this warp's 32 rows of the unit
+                        const uint32_t w0 = u * usw + (uint32_t)(tid & ~31);
+                        stg = stage.stage(csr, w0, min(w0 + 32u, nn), &e0s, a.poll_limit, &a.out->abort);
+                    }
                     // -- loads
                     T c[RPT][VEC], nb[RPT][VEC], zp[RPT][VEC], cur[RPT][L][VEC], pk[RPT][L][VEC];
                     T pv[RPT][VEC], xv[RPT][VEC];
@@ -1430,7 +1437,7 @@ __device__ void cg_body(const SolveArgs<T> &a, Smem<T> &s, Grp &grp)
     extern __shared__ __align__(128) unsigned char plcg_dsm[];
     CsrStage<T> stage(plcg_dsm);
     if constexpr (kStage) {
-        if (threadIdx.x == 0) mbar_init(stage.bar, 1);
+        stage.init();
         __syncthreads();
     }
 
@@ -1537,9 +1544,10 @@ __device__ void cg_body(const SolveArgs<T> &a, Smem<T> &s, Grp &grp)
                 uint32_t g0[RPT];
                 bool stg = false;
                 int64_t e0s = 0;
-                if constexpr (kStage)
-                    stg = stage.stage(csr, u * USWEEP, min(u * USWEEP + USWEEP, nn), kBlock, &e0s,
-                                      a.poll_limit, &a.out->abort);
+                if constexpr (kStage) {   // this warp's 32 rows of the unit
+                    const uint32_t w0 = u * USWEEP + (uint32_t)(tid & ~31);
+                    stg = stage.stage(csr, w0, min(w0 + 32u, nn), &e0s, a.poll_limit, &a.out->abort);
+                }
 #pragma unroll
                 for (int r = 0; r < RPT; ++r) {
                     g0[r] = u * USWEEP + ((uint32_t)r * kBlock + tid) * VEC;
