@@ -10,7 +10,9 @@ input generators produce:
 * stencil: ``{"kind": "stencil", "dim": 2|3, "nx", "ny", "nz", "center", "off"}``
   (Dirichlet 5-/7-point, lexicographic order with x fastest; ``center``
   already includes any diagonal shift);
-* CSR: ``{"kind": "csr", "n", "rowptr" (int64), "col" (int32), "val" (float64)}``.
+* CSR: ``{"kind": "csr", "n", "rowptr" (int64), "col" (int32), "val" (float64)}``;
+* structured 27-point: ``{"kind": "var27", "nx", "ny", "nz", "coef" (14, n)}``
+  (diagonal, then the weights to the 13 forward neighbours).
 
 The method's arithmetic lives in the C file; this module only marshals arrays.
 """
@@ -42,6 +44,7 @@ class _Op(C.Structure):
         ("center", C.c_double), ("off", C.c_double),
         ("n", C.c_int64),
         ("rowptr", C.c_void_p), ("col", C.c_void_p), ("val", C.c_void_p),
+        ("coef", C.c_void_p),
     ]
 
 
@@ -129,6 +132,16 @@ class _OpHolder:
                 raise ValueError("inconsistent CSR arrays")
             o.rowptr, o.col, o.val = _ptr(rowptr), _ptr(col), _ptr(val)
             self.keep = (rowptr, col, val)
+        elif op["kind"] == "var27":
+            o.kind = 2
+            o.dim = 3
+            o.nx, o.ny, o.nz = int(op["nx"]), int(op["ny"]), int(op["nz"])
+            o.n = o.nx * o.ny * o.nz
+            coef = np.ascontiguousarray(op["coef"], dtype=np.float64)
+            if coef.shape != (14, o.n):
+                raise ValueError("var27 coef must have shape (14, n)")
+            o.coef = _ptr(coef)
+            self.keep = (coef,)
         else:
             raise ValueError(f"unknown operator kind {op['kind']!r}")
         self.op = o

@@ -12,7 +12,9 @@
  *
  * What it computes
  *   - orc_apply      : y = A x for a Dirichlet 5-point (2D) / 7-point (3D)
- *                      constant-coefficient stencil, or for a CSR matrix.
+ *                      constant-coefficient stencil, a CSR matrix, or a
+ *                      symmetric 27-point variable-coefficient stencil given
+ *                      by its diagonal and 13 forward weights per cell.
  *   - orc_cg         : classic Hestenes-Stiefel CG (the paper cites it, Sec. 1,
  *                      and costs it in Table 1, but prints no listing, so the
  *                      textbook recurrence is used).
@@ -83,10 +85,11 @@
 
 #define ORC_STENCIL 0
 #define ORC_CSR     1
+#define ORC_VAR27   2
 
 /* The operator A.  Stencil: unknowns in lexicographic order, x fastest. */
 typedef struct {
-    int kind;                 /* ORC_STENCIL or ORC_CSR                     */
+    int kind;                 /* ORC_STENCIL, ORC_CSR or ORC_VAR27          */
     int dim;                  /* stencil: 2 (5-point) or 3 (7-point)        */
     int64_t nx, ny, nz;       /* stencil grid (nz = 1 in 2D)                */
     double center, off;       /* stencil: diagonal and off-diagonal weight  */
@@ -94,6 +97,8 @@ typedef struct {
     const int64_t *rowptr;    /* CSR: n+1 offsets                            */
     const int32_t *col;       /* CSR: column indices                         */
     const double *val;        /* CSR: values                                 */
+    const double *coef;       /* VAR27: [14][n] diagonal, then the weights to
+                                 the 13 forward neighbours (see var27_fwd)   */
 } orc_op;
 
 /* Parameters of one solve. */
@@ -145,8 +150,40 @@ static double nrm2(int64_t n, const double *a) { return sqrt(dot(n, a, a)); }
 /* ------------------------------------------------------------------ */
 /* y = A x                                                              */
 /* ------------------------------------------------------------------ */
+/* The 13 forward offsets (dz, dy, dx) of the symmetric 27-point operator, in
+ * lexicographic order (the layout of coef[1..13]); the entry to c - d is the
+ * neighbour's entry to c. */
+static const int var27_fwd[13][3] = {
+    {0, 0, 1}, {0, 1, -1}, {0, 1, 0}, {0, 1, 1},
+    {1, -1, -1}, {1, -1, 0}, {1, -1, 1}, {1, 0, -1}, {1, 0, 0}, {1, 0, 1},
+    {1, 1, -1}, {1, 1, 0}, {1, 1, 1}};
+
+static int in_grid(const orc_op *A, int64_t i, int64_t j, int64_t k)
+{
+    return i >= 0 && i < A->nx && j >= 0 && j < A->ny && k >= 0 && k < A->nz;
+}
+
 void orc_apply(const orc_op *A, const double *x, double *y)
 {
+    if (A->kind == ORC_VAR27) {
+        const int64_t n = A->n;
+        for (int64_t k = 0; k < A->nz; ++k)
+            for (int64_t j = 0; j < A->ny; ++j)
+                for (int64_t i = 0; i < A->nx; ++i) {
+                    const int64_t c = (k * A->ny + j) * A->nx + i;
+                    double s = A->coef[c] * x[c];
+                    for (int d = 0; d < 13; ++d) {
+                        const int dz = var27_fwd[d][0], dy = var27_fwd[d][1], dx = var27_fwd[d][2];
+                        const int64_t off = (dz * A->ny + dy) * A->nx + dx;
+                        if (in_grid(A, i + dx, j + dy, k + dz))
+                            s += A->coef[(1 + d) * n + c] * x[c + off];
+                        if (in_grid(A, i - dx, j - dy, k - dz))
+                            s += A->coef[(1 + d) * n + c - off] * x[c - off];
+                    }
+                    y[c] = s;
+                }
+        return;
+    }
     if (A->kind == ORC_CSR) {
         for (int64_t r = 0; r < A->n; ++r) {
             double s = 0.0;
@@ -204,6 +241,8 @@ static int jacobi_minv(const orc_op *A, double *minv)
         if (A->kind == ORC_CSR) {
             for (int64_t e = A->rowptr[r]; e < A->rowptr[r + 1]; ++e)
                 if (A->col[e] == r) d += A->val[e];
+        } else if (A->kind == ORC_VAR27) {
+            d = A->coef[r];
         } else {
             d = A->center;
         }

@@ -56,6 +56,8 @@ def stencil3d(nx: int, ny: int, nz: int, center: float = 6.0, off: float = -1.0,
 def op_size(op: dict) -> int:
     if op["kind"] == "stencil":
         return int(op["nx"]) * int(op["ny"]) * (int(op["nz"]) if op["dim"] == 3 else 1)
+    if op["kind"] == "var27":
+        return int(op["nx"]) * int(op["ny"]) * int(op["nz"])
     return int(op["n"])
 
 
@@ -80,6 +82,8 @@ def shift_interval(op: dict) -> tuple[float, float]:
         base = 4.0 if op["dim"] == 2 else 6.0
         shift = op["center"] - base
         return (max(0.0, shift), op["center"] + 2 * op["dim"] * abs(op["off"]))
+    if op["kind"] == "var27":
+        op = var27_to_csr(op)
     rowsum = np.add.reduceat(np.abs(op["val"]), op["rowptr"][:-1]) \
         if op["val"].size else np.zeros(op["n"])
     return (0.0, float(rowsum.max()))
@@ -93,6 +97,8 @@ def jacobi_shift_interval(op: dict) -> tuple[float, float]:
     if op["kind"] == "stencil":
         lo, hi = shift_interval(op)
         return lo / op["center"], hi / op["center"]
+    if op["kind"] == "var27":
+        op = var27_to_csr(op)
     val, rowptr = op["val"], op["rowptr"]
     n = op["n"]
     rows = np.repeat(np.arange(n), np.diff(rowptr))
@@ -100,6 +106,43 @@ def jacobi_shift_interval(op: dict) -> tuple[float, float]:
     np.add.at(diag, rows[op["col"] == rows], val[op["col"] == rows])
     rowsum = np.add.reduceat(np.abs(val), rowptr[:-1]) if val.size else np.zeros(n)
     return 0.0, float((rowsum / diag).max())
+
+
+# The 13 "forward" neighbour offsets (dz, dy, dx) of a 27-point stencil, in
+# lexicographic order: the structured operator stores the weight to each of
+# them per cell; the weight to c - d is the neighbour's weight to c (symmetry).
+VAR27_FORWARD = [(0, 0, 1), (0, 1, -1), (0, 1, 0), (0, 1, 1),
+                 (1, -1, -1), (1, -1, 0), (1, -1, 1), (1, 0, -1), (1, 0, 0), (1, 0, 1),
+                 (1, 1, -1), (1, 1, 0), (1, 1, 1)]
+
+
+def _hetero27_entries(nx: int, ny: int, nz: int, seed: int, sigma: float):
+    """Entries of the 27-point heterogeneous-diffusion operator: for each of
+    the 27 offsets (dz, dy, dx) the (nz, ny, nx) array of A[c, c + d] (the
+    diagonal for (0, 0, 0)) and the mask of in-grid neighbours."""
+    rng = np.random.default_rng(seed)
+    n = nx * ny * nz
+    kappa = np.exp(sigma * rng.standard_normal(n))
+    k3 = kappa.reshape(nz, ny, nx)
+    iz, iy, ix = np.meshgrid(np.arange(nz), np.arange(ny), np.arange(nx), indexing="ij")
+    offsets = [(dz, dy, dx) for dz in (-1, 0, 1) for dy in (-1, 0, 1) for dx in (-1, 0, 1)]
+    masks, entries = {}, {}
+    diag = np.zeros((nz, ny, nx))
+    for dz, dy, dx in offsets:
+        if (dz, dy, dx) == (0, 0, 0):
+            continue
+        s = 1.0 / (abs(dz) + abs(dy) + abs(dx))
+        valid = ((iz + dz >= 0) & (iz + dz < nz) & (iy + dy >= 0) & (iy + dy < ny)
+                 & (ix + dx >= 0) & (ix + dx < nx))
+        kd = np.roll(k3, shift=(-dz, -dy, -dx), axis=(0, 1, 2))
+        kd = np.where(valid, kd, k3)
+        w = s * 2.0 * (k3 * kd) / (k3 + kd)   # symmetric in (c, d) bit for bit
+        diag += w
+        masks[(dz, dy, dx)] = valid
+        entries[(dz, dy, dx)] = -w
+    masks[(0, 0, 0)] = np.ones((nz, ny, nx), dtype=bool)
+    entries[(0, 0, 0)] = diag
+    return offsets, masks, entries
 
 
 def hetero27_csr(nx: int, ny: int, nz: int, seed: int = 3, sigma: float = 1.0) -> dict:
@@ -112,29 +155,9 @@ def hetero27_csr(nx: int, ny: int, nz: int, seed: int = 3, sigma: float = 1.0) -
     neighbour outside the grid takes k_d = k_c and stays on the diagonal
     only (Dirichlet).  The result is a symmetric, irreducibly diagonally
     dominant M-matrix, hence SPD."""
-    rng = np.random.default_rng(seed)
     n = nx * ny * nz
-    kappa = np.exp(sigma * rng.standard_normal(n))
-    k3 = kappa.reshape(nz, ny, nx)
-    iz, iy, ix = np.meshgrid(np.arange(nz), np.arange(ny), np.arange(nx), indexing="ij")
-    offsets = [(dz, dy, dx) for dz in (-1, 0, 1) for dy in (-1, 0, 1) for dx in (-1, 0, 1)]
-    masks, weights = [], []
-    diag = np.zeros((nz, ny, nx))
-    for dz, dy, dx in offsets:
-        if (dz, dy, dx) == (0, 0, 0):
-            masks.append(np.ones((nz, ny, nx), dtype=bool))
-            weights.append(None)
-            continue
-        s = 1.0 / (abs(dz) + abs(dy) + abs(dx))
-        valid = ((iz + dz >= 0) & (iz + dz < nz) & (iy + dy >= 0) & (iy + dy < ny)
-                 & (ix + dx >= 0) & (ix + dx < nx))
-        kd = np.roll(k3, shift=(-dz, -dy, -dx), axis=(0, 1, 2))
-        kd = np.where(valid, kd, k3)
-        w = s * 2.0 * (k3 * kd) / (k3 + kd)   # symmetric in (c, d) bit for bit
-        diag += w
-        masks.append(valid)
-        weights.append(-w)
-    counts = sum(m.astype(np.int64) for m in masks).ravel()
+    offsets, masks, entries = _hetero27_entries(nx, ny, nz, seed, sigma)
+    counts = sum(masks[o].astype(np.int64) for o in offsets).ravel()
     rowptr = np.zeros(n + 1, dtype=np.int64)
     np.cumsum(counts, out=rowptr[1:])
     nnz = int(rowptr[-1])
@@ -142,13 +165,54 @@ def hetero27_csr(nx: int, ny: int, nz: int, seed: int = 3, sigma: float = 1.0) -
     val = np.empty(nnz, dtype=np.float64)
     cursor = rowptr[:-1].copy()
     lin = np.arange(n, dtype=np.int64)
-    for (dz, dy, dx), m, w in zip(offsets, masks, weights):
-        mf = m.ravel()
+    for dz, dy, dx in offsets:
+        mf = masks[(dz, dy, dx)].ravel()
         pos = cursor[mf]
         col[pos] = (lin[mf] + (dz * ny + dy) * nx + dx).astype(np.int32)
-        val[pos] = diag.ravel()[mf] if w is None else w.ravel()[mf]
+        val[pos] = entries[(dz, dy, dx)].ravel()[mf]
         cursor[mf] += 1
     return {"kind": "csr", "n": n, "rowptr": rowptr, "col": col, "val": val}
+
+
+def hetero27_var27(nx: int, ny: int, nz: int, seed: int = 3, sigma: float = 1.0) -> dict:
+    """The same operator as hetero27_csr (same seed: the same matrix, entry for
+    entry) in the structured variable-coefficient layout: coef[0] = the
+    diagonal, coef[1 + k] = A[c, c + VAR27_FORWARD[k]] (0 where that neighbour
+    is outside the grid), each a length-n array in lexicographic order."""
+    n = nx * ny * nz
+    _, masks, entries = _hetero27_entries(nx, ny, nz, seed, sigma)
+    coef = np.zeros((14, n))
+    coef[0] = entries[(0, 0, 0)].ravel()
+    for k, o in enumerate(VAR27_FORWARD):
+        coef[1 + k] = np.where(masks[o], entries[o], 0.0).ravel()
+    return {"kind": "var27", "nx": nx, "ny": ny, "nz": nz, "coef": coef}
+
+
+def var27_to_csr(op: dict) -> dict:
+    """CSR form of a structured 27-point operator (forward weights, their
+    symmetric partners and the diagonal; entries to cells outside the grid
+    dropped), columns sorted per row."""
+    import scipy.sparse as sp
+    nx, ny, nz = op["nx"], op["ny"], op["nz"]
+    n = nx * ny * nz
+    coef = op["coef"]
+    iz, iy, ix = np.meshgrid(np.arange(nz), np.arange(ny), np.arange(nx), indexing="ij")
+    iz, iy, ix = iz.ravel(), iy.ravel(), ix.ravel()
+    lin = np.arange(n)
+    rows, cols, vals = [lin], [lin], [coef[0]]
+    for k, (dz, dy, dx) in enumerate(VAR27_FORWARD):
+        valid = ((iz + dz < nz) & (iy + dy >= 0) & (iy + dy < ny) & (ix + dx >= 0) & (ix + dx < nx))
+        c = lin[valid]
+        d = c + (dz * ny + dy) * nx + dx
+        w = coef[1 + k][valid]
+        rows += [c, d]
+        cols += [d, c]
+        vals += [w, w]
+    A = sp.csr_matrix((np.concatenate(vals), (np.concatenate(rows), np.concatenate(cols))),
+                      shape=(n, n))
+    A.sort_indices()
+    return {"kind": "csr", "n": n, "rowptr": A.indptr.astype(np.int64),
+            "col": A.indices.astype(np.int32), "val": A.data.astype(np.float64)}
 
 
 def random_spd_csr(n: int, seed: int, nnz_lo: int = 5, nnz_hi: int = 30) -> dict:
@@ -184,6 +248,8 @@ def fp32_rounded(op: dict) -> dict:
     if op["kind"] == "stencil":
         out["center"] = float(np.float32(op["center"]))
         out["off"] = float(np.float32(op["off"]))
+    elif op["kind"] == "var27":
+        out["coef"] = op["coef"].astype(np.float32).astype(np.float64)
     else:
         out["val"] = op["val"].astype(np.float32).astype(np.float64)
     return out
@@ -193,6 +259,8 @@ def to_scipy(op: dict):
     """A scipy.sparse CSR matrix of the operator (library construction:
     Kronecker sums for stencils), used to form right-hand sides."""
     import scipy.sparse as sp
+    if op["kind"] == "var27":
+        op = var27_to_csr(op)
     if op["kind"] == "csr":
         n = op["n"]
         return sp.csr_matrix((op["val"], op["col"], op["rowptr"]), shape=(n, n))
@@ -215,7 +283,7 @@ def to_scipy(op: dict):
 
 def rhs(op: dict, xstar: np.ndarray) -> np.ndarray:
     """b = A x* in FP64 (scipy.sparse for CSR; array shifts for stencils)."""
-    if op["kind"] == "csr":
+    if op["kind"] in ("csr", "var27"):
         return to_scipy(op) @ xstar
     dims = (op["nz"], op["ny"], op["nx"]) if op["dim"] == 3 else (op["ny"], op["nx"])
     X = xstar.reshape(dims)
@@ -279,6 +347,14 @@ def e3_diagonal(nx: int = 100, seed: int = 1) -> dict:
     bt = scipy.fft.dstn(lap["b"].reshape(nx, nx), type=1, norm="ortho").ravel()
     return {"op": op, "b": bt, "b_laplacian": lap["b"], "interval": (0.0, 8.0),
             "rtol": 1e-6}
+
+
+def config_hetero27_var27(nx: int = 128, seed: int = 3) -> dict:
+    """The 27-point heterogeneous operator of config_hetero27 (FP32-rounded
+    values, the same x* and b) in the structured layout."""
+    op = fp32_rounded(hetero27_var27(nx, nx, nx, seed=seed))
+    xs = np.random.default_rng(seed + 1000).standard_normal(op_size(op))
+    return {"op": op, "b": rhs(op, xs), "xstar": xs, "rtol": 1e-8}
 
 
 def batched_systems(count: int = 4096, s_lo: int = 16, s_hi: int = 256, seed: int = 4):

@@ -614,3 +614,38 @@ def test_p10_e3_workload_generator(l):
     xa = scipy.fft.idstn(a.x.reshape(N, N), type=1, norm="ortho").ravel()
     assert np.linalg.norm(xa - b.x) <= 1e-12 * np.linalg.norm(b.x)
     assert np.array_equal(e["b_laplacian"], lap["b"])
+
+
+# ------------------------------------------- structured 27-point operator --
+@pytest.mark.parametrize("dims", [(5, 5, 5), (7, 4, 6), (1, 3, 2), (9, 8, 7)])
+def test_var27_apply_matches_the_csr_operator(dims):
+    """The oracle's structured 27-point apply (diagonal + 13 forward weights,
+    backward weights from the neighbours) equals scipy's product with the CSR
+    matrix the generator builds independently from the same coefficients."""
+    v = W.hetero27_var27(*dims, seed=11)
+    c = W.hetero27_csr(*dims, seed=11)
+    x = np.random.default_rng(1).standard_normal(c["n"])
+    y = O.apply(v, x)
+    ref = W.to_scipy(c) @ x
+    assert np.abs(y - ref).max() <= 1e-13 * np.abs(ref).max()
+
+
+def test_var27_solves_vs_dense_cholesky():
+    """CG, p(l)-CG and their Jacobi forms on the structured operator reach
+    the Cholesky solution of the same matrix (P1 / J5 bounds)."""
+    v = W.hetero27_var27(6, 5, 7, seed=12)
+    A = dense(W.hetero27_csr(6, 5, 7, seed=12))
+    b = np.random.default_rng(3).standard_normal(A.shape[0])
+    x_chol = scipy.linalg.cho_solve(scipy.linalg.cho_factor(A), b)
+    ev = np.linalg.eigvalsh(A)
+    d = np.diag(A)
+    rtol = 1e-10
+    bound = 1.01 * (ev[-1] / ev[0]) * math.sqrt(d.max() / d.min()) * rtol + 1e-13
+    runs = [O.cg(v, b, rtol=rtol), O.cg(v, b, rtol=rtol, precond="jacobi")]
+    for l in (1, 2, 3):
+        runs.append(O.plcg(v, b, l=l, sigma=O.chebyshev_shifts(l, *W.shift_interval(v)), rtol=rtol))
+        runs.append(O.plcg(v, b, l=l, sigma=O.chebyshev_shifts(l, *W.jacobi_shift_interval(v)),
+                           rtol=rtol, precond="jacobi"))
+    for r in runs:
+        assert r.status == O.ORC_OK and r.true_relres < rtol
+        assert np.linalg.norm(r.x - x_chol) / np.linalg.norm(x_chol) <= bound
