@@ -406,6 +406,28 @@ def other_configs(plcg, W, dev, hbm_peak):
                    "hbm_frac": round(byt / min(ts) / 1e9 / hbm_peak, 4)}
     A.close()
     out["h27_csr_128_fp32"] = d
+    # ---- the same operator in the structured 27-point layout (diagonal + 13
+    # forward weights per cell, no column indices), FP32, Jacobi
+    c27 = W.config_hetero27_var27(nx=128)
+    A = plcg.Matrix(c27["op"], prec="fp32")
+    interval = W.jacobi_shift_interval(op)
+    d = {"n": n, "bytes_per_row_operator": 14 * 4}
+    for name, kw in (("jacobi_plcg_l1", {"l": 1}), ("jacobi_plcg_l2", {"l": 2}),
+                     ("jacobi_classic_cg", {"method": "cg"})):
+        ts = []
+        for _ in range(2):
+            x = torch.zeros_like(b)
+            r = A.solve(b, x, interval=interval, rtol=1e-8, prec="fp32", max_restarts=64,
+                        precond="jacobi", check=False, **kw)
+            ts.append(r.seconds)
+        ll = kw.get("l", 1)
+        vec_passes = (10 if "method" in kw else 3 * (ll + 1) + 4) + 1   # + 1/a_rr
+        byt = r.iters * (vec_passes * 4 * n + 14 * 4 * n)
+        d[name] = {"status": r.status, "iters": r.iters, "restarts": r.restarts,
+                   "time_to_rtol_s": round(min(ts), 5), "hbm_gbs": round(byt / min(ts) / 1e9, 1),
+                   "hbm_frac": round(byt / min(ts) / 1e9 / hbm_peak, 4)}
+    A.close()
+    out["h27_var27_128_fp32"] = d
     # ---- batched: 4096 shifted 2D Poisson systems, FP32 with FP64 correction
     systems = W.batched_systems(4096)
     mats = [plcg.Matrix(s_["op"]) for s_ in systems]

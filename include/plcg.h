@@ -150,6 +150,26 @@ plcg_status plcg_create_csr(int64_t n, int64_t nnz, const int64_t *rowptr,
                             const int32_t *col, const double *val, int on_device,
                             int prec, void *stream, plcg_matrix **out);
 
+/* Create a structured symmetric 27-point operator with per-cell coefficients
+ * on an nx x ny x nz grid (lexicographic order, x fastest; n = nx*ny*nz <
+ * 2^31), the operator of a variable-coefficient 27-point discretisation
+ * stored without column indices.  coef[14][n] (FP64; host, or device when
+ * on_device = 1): coef[0][c] = A[c][c]; coef[1+k][c] = A[c][c + d_k] for the
+ * 13 "forward" offsets d_k = (dz, dy, dx), in this order:
+ *   (0,0,1) (0,1,-1) (0,1,0) (0,1,1) (1,-1,-1) (1,-1,0) (1,-1,1)
+ *   (1,0,-1) (1,0,0) (1,0,1) (1,1,-1) (1,1,0) (1,1,1),
+ * offset index d = (dz*ny + dy)*nx + dx.  A[c][c - d_k] = A[c - d_k][c] (A is
+ * symmetric, so the backward entries are the neighbours' forward ones).
+ * Entries towards cells outside the grid are ignored (Dirichlet).  A must be
+ * positive definite (not checked).  prec fixes the stored type as for CSR:
+ * PLCG_FP32_FP64DOT rounds the coefficients to FP32 once and every solve
+ * (the FP64 residuals included) uses the rounded values.  The array is
+ * copied; the Jacobi data (1/A[c][c]) is formed here.
+ * Errors: PLCG_ERR_INVALID (sizes, NULL, non-finite values when on host),
+ * PLCG_ERR_NOMEM, PLCG_ERR_CUDA. */
+plcg_status plcg_create_var27(int64_t nx, int64_t ny, int64_t nz, const double *coef,
+                              int on_device, int prec, void *stream, plcg_matrix **out);
+
 /* Release the matrix, its device copies and workspaces.  NULL is a no-op. */
 void plcg_destroy(plcg_matrix *A);
 

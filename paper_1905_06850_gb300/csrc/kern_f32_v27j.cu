@@ -1,0 +1,25 @@
+// kern_f32_v27j.cu -- instantiations of the persistent solvers for T = float,
+// VEC = 1, operator kOpVar27Jacobi (the structured 27-point operator with M = diag(A)); one translation unit per combination so that
+// the build compiles them in parallel.
+#include "solver.cuh"
+#include "plcg_kernels.h"
+
+namespace plcg {
+
+const void *kptr_f32_v27j(int l, bool cg)
+{
+    if (cg) return reinterpret_cast<const void *>(&cg_kernel<float, 1, kOpVar27Jacobi>);
+    switch (l) {
+    case 1: return reinterpret_cast<const void *>(&plcg_kernel<float, 1, 1, kOpVar27Jacobi>);
+    case 2: return reinterpret_cast<const void *>(&plcg_kernel<float, 2, 1, kOpVar27Jacobi>);
+    case 3: return reinterpret_cast<const void *>(&plcg_kernel<float, 3, 1, kOpVar27Jacobi>);
+    case 4: return reinterpret_cast<const void *>(&plcg_kernel<float, 4, 1, kOpVar27Jacobi>);
+    case 5: return reinterpret_cast<const void *>(&plcg_kernel<float, 5, 1, kOpVar27Jacobi>);
+    case 6: return reinterpret_cast<const void *>(&plcg_kernel<float, 6, 1, kOpVar27Jacobi>);
+    case 7: return reinterpret_cast<const void *>(&plcg_kernel<float, 7, 1, kOpVar27Jacobi>);
+    case 8: return reinterpret_cast<const void *>(&plcg_kernel<float, 8, 1, kOpVar27Jacobi>);
+    default: return nullptr;
+    }
+}
+
+}  // namespace plcg

@@ -9,10 +9,14 @@ const void *kernel_ptr(bool f32, int op, int vec, int l, bool cg)
     if (!f32) {
         if (op == kOpCsr) return kptr_f64_csr(l, cg);
         if (op == kOpCsrJacobi) return kptr_f64_csrj(l, cg);
+        if (op == kOpVar27) return kptr_f64_v27(l, cg);
+        if (op == kOpVar27Jacobi) return kptr_f64_v27j(l, cg);
         return vec == 2 ? kptr_f64_st2(l, cg) : kptr_f64_st1(l, cg);
     }
     if (op == kOpCsr) return kptr_f32_csr(l, cg);
     if (op == kOpCsrJacobi) return kptr_f32_csrj(l, cg);
+    if (op == kOpVar27) return kptr_f32_v27(l, cg);
+    if (op == kOpVar27Jacobi) return kptr_f32_v27j(l, cg);
     return vec == 4 ? kptr_f32_st4(l, cg) : kptr_f32_st1(l, cg);
 }
 
@@ -72,6 +76,36 @@ cudaError_t launch_jacobi_setup(bool f32, const int64_t *rowptr, const int32_t *
         jacobi_setup_kernel<double><<<g, 256, 0, s>>>(rowptr, col, static_cast<const double *>(val), n,
                                                       dinv64, static_cast<double *>(dinv),
                                                       static_cast<double *>(diag), bad);
+    return cudaGetLastError();
+}
+
+template <typename V>
+__global__ void var27_jacobi_setup_kernel(const V *diag, int64_t n, double *dinv64, V *dinv, int *bad)
+{
+    for (int64_t r = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; r < n;
+         r += (int64_t)gridDim.x * blockDim.x) {
+        double d = (double)diag[r];
+        if (!(d > 0.0) || !isfinite(d)) {
+            atomicExch(bad, 1);
+            d = 1.0;
+        }
+        const double di = 1.0 / d;
+        dinv64[r] = di;
+        dinv[r] = (V)di;
+    }
+}
+
+cudaError_t launch_var27_jacobi_setup(bool f32, const void *coef, int64_t n, double *dinv64,
+                                      void *dinv, int *bad, cudaStream_t s)
+{
+    const int64_t blocks = (n + 255) / 256;
+    const unsigned g = (unsigned)(blocks < 65535 ? (blocks > 0 ? blocks : 1) : 65535);
+    if (f32)
+        var27_jacobi_setup_kernel<float><<<g, 256, 0, s>>>(static_cast<const float *>(coef), n, dinv64,
+                                                           static_cast<float *>(dinv), bad);
+    else
+        var27_jacobi_setup_kernel<double><<<g, 256, 0, s>>>(static_cast<const double *>(coef), n, dinv64,
+                                                            static_cast<double *>(dinv), bad);
     return cudaGetLastError();
 }
 

@@ -81,7 +81,7 @@ struct plcg_matrix {
     // Jacobi data (CSR): 1 / a_rr in FP64, 1 / a_rr and a_rr in the stored type
     double *jdinv64 = nullptr;
     void *jdinv = nullptr;
-    void *jdiag = nullptr;
+    void *jdiag = nullptr;       // CSR: own array; structured 27-point: coef[0] (not owned)
     bool jacobi_ok = false;
     cudaStream_t stream = nullptr;
     int device = 0;
@@ -243,6 +243,80 @@ extern "C" plcg_status plcg_create_csr(int64_t n, int64_t nnz, const int64_t *ro
     return PLCG_OK;
 }
 
+extern "C" plcg_status plcg_create_var27(int64_t nx, int64_t ny, int64_t nz, const double *coef,
+                                         int on_device, int prec, void *stream, plcg_matrix **out)
+{
+    if (!out) return fail(PLCG_ERR_INVALID, "plcg_create_var27: NULL out");
+    *out = nullptr;
+    if (!coef) return fail(PLCG_ERR_INVALID, "var27: NULL coefficients");
+    if (nx < 1 || ny < 1 || nz < 1 || nx >= (1 << 30) || ny >= (1 << 30) || nz >= (1 << 30))
+        return fail(PLCG_ERR_INVALID, "var27: grid sizes must be in [1, 2^30)");
+    const int64_t n = nx * ny * nz;
+    if (n >= (int64_t(1) << 31)) return fail(PLCG_ERR_INVALID, "var27: n must be < 2^31");
+    if (prec != PLCG_FP64 && prec != PLCG_FP32_FP64DOT)
+        return fail(PLCG_ERR_INVALID, "var27: unknown precision %d", prec);
+    if (!on_device)
+        for (int64_t e = 0; e < 14 * n; ++e)
+            if (!std::isfinite(coef[e]))
+                return fail(PLCG_ERR_INVALID, "var27: non-finite coefficient at entry %lld", (long long)e);
+    plcg_matrix *A = new plcg_matrix();
+    A->kind = kOpVar27;
+    A->n = n;
+    A->csr_prec = prec;
+    A->st.dim = 3;
+    A->st.nx = (int)nx;
+    A->st.ny = (int)ny;
+    A->st.nz = (int)nz;
+    A->st.dnx = make_fastdiv((uint32_t)nx);
+    A->st.dny = make_fastdiv((uint32_t)ny);
+    plcg_status st = matrix_common_init(A, stream);
+    if (st != PLCG_OK) { plcg_destroy(A); return st; }
+    const cudaMemcpyKind kind = on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice;
+    const size_t vsz = (prec == PLCG_FP64) ? sizeof(double) : sizeof(float);
+    const size_t cnt = (size_t)14 * n;
+    cudaError_t e = cudaMalloc(&A->val, cnt * vsz);
+    if (e == cudaSuccess) {
+        if (prec == PLCG_FP64) {
+            e = cudaMemcpy(A->val, coef, cnt * sizeof(double), kind);
+        } else {
+            double *tmp = nullptr;
+            const double *src = coef;
+            if (!on_device) {
+                e = cudaMalloc(&tmp, cnt * sizeof(double));
+                if (e == cudaSuccess) e = cudaMemcpy(tmp, coef, cnt * sizeof(double), kind);
+                src = tmp;
+            }
+            if (e == cudaSuccess) e = launch_round_to_f32(src, static_cast<float *>(A->val), (int64_t)cnt, nullptr);
+            if (e == cudaSuccess) e = cudaDeviceSynchronize();
+            if (tmp) cudaFree(tmp);
+        }
+    }
+    // Jacobi data: the diagonal is coef[0]; its inverse is formed here
+    int *bad = nullptr;
+    A->jdiag = A->val;
+    if (e == cudaSuccess) e = cudaMalloc(&A->jdinv64, n * sizeof(double));
+    if (e == cudaSuccess) {
+        if (prec == PLCG_FP64) A->jdinv = A->jdinv64;
+        else e = cudaMalloc(&A->jdinv, n * vsz);
+    }
+    if (e == cudaSuccess) e = cudaMalloc(&bad, sizeof(int));
+    if (e == cudaSuccess) e = cudaMemset(bad, 0, sizeof(int));
+    if (e == cudaSuccess)
+        e = launch_var27_jacobi_setup(prec != PLCG_FP64, A->val, n, A->jdinv64, A->jdinv, bad, nullptr);
+    int hbad = 1;
+    if (e == cudaSuccess) e = cudaMemcpy(&hbad, bad, sizeof(int), cudaMemcpyDeviceToHost);
+    if (bad) cudaFree(bad);
+    A->jacobi_ok = (e == cudaSuccess && hbad == 0);
+    if (e != cudaSuccess) {
+        plcg_status s2 = fail(e == cudaErrorMemoryAllocation ? PLCG_ERR_NOMEM : PLCG_ERR_CUDA,
+                              "var27 upload: %s", cudaGetErrorString(e));
+        plcg_destroy(A);
+        return s2;
+    }
+    *out = A;
+    return PLCG_OK;
+}
+
 extern "C" void plcg_destroy(plcg_matrix *A)
 {
     if (!A) return;
@@ -250,10 +324,10 @@ extern "C" void plcg_destroy(plcg_matrix *A)
     else cudaDeviceSynchronize();
     cudaFree(A->rowptr);
     cudaFree(A->col);
+    if (A->jdiag != A->val) cudaFree(A->jdiag);
     cudaFree(A->val);
     if (A->jdinv != A->jdinv64) cudaFree(A->jdinv);
     cudaFree(A->jdinv64);
-    cudaFree(A->jdiag);
     cudaFree(A->ws.mem);
     cudaFree(A->b_dev);
     cudaFree(A->x_dev);
@@ -315,8 +389,8 @@ static plcg_status build_solve(const plcg_matrix *A, const double *b, double *x,
     const int64_t n = A->n;
     const int l = prm->l;
     const bool cg = prm->method == PLCG_METHOD_CG;
-    const bool jac = prm->precond == PLCG_PRECOND_JACOBI && A->kind == kOpCsr;
-    const int op = jac ? (int)kOpCsrJacobi : A->kind;
+    const bool jac = prm->precond == PLCG_PRECOND_JACOBI && A->kind != kOpStencil;
+    const int op = !jac ? A->kind : (A->kind == kOpCsr) ? (int)kOpCsrJacobi : (int)kOpVar27Jacobi;
     const bool f32 = sizeof(T) == 4;
     int vec = 1;
     if (op == kOpStencil) {
@@ -327,7 +401,7 @@ static plcg_status build_solve(const plcg_matrix *A, const double *b, double *x,
     if (!func) return fail(PLCG_ERR_UNIMPL, "no kernel for prec=%d op=%d vec=%d l=%d", (int)f32, op, vec, l);
     // CSR kernels stage each unit's entries in dynamic shared memory (FP64
     // classic CG excepted, see cg_body)
-    const unsigned dsmem = (op != kOpStencil && (!cg || f32)) ? csr_stage_bytes((unsigned)sizeof(T)) : 0u;
+    const unsigned dsmem = (op_is_csr(op) && (!cg || f32)) ? csr_stage_bytes((unsigned)sizeof(T)) : 0u;
     if (dsmem) {
         CUDA_TRY(cudaFuncSetAttribute(func, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)dsmem));
         CUDA_TRY(cudaFuncSetAttribute(func, cudaFuncAttributePreferredSharedMemoryCarveout,
@@ -499,14 +573,14 @@ static plcg_status check_params(const plcg_matrix *A, const plcg_params *p)
     if (p->max_restarts < 0) return fail(PLCG_ERR_INVALID, "max_restarts must be >= 0");
     if (p->prec != PLCG_FP64 && p->prec != PLCG_FP32_FP64DOT)
         return fail(PLCG_ERR_INVALID, "unknown precision %d", p->prec);
-    if (A->kind == kOpCsr && p->prec != A->csr_prec)
-        return fail(PLCG_ERR_INVALID, "CSR matrix was created for precision %d", A->csr_prec);
+    if (A->kind != kOpStencil && p->prec != A->csr_prec)
+        return fail(PLCG_ERR_INVALID, "matrix was created for precision %d", A->csr_prec);
     if (p->prec == PLCG_FP32_FP64DOT && !(p->inner_rtol_floor > 0.0 && p->inner_rtol_floor < 1.0))
         return fail(PLCG_ERR_INVALID, "inner_rtol_floor must be in (0, 1)");
     if (p->precond != PLCG_PRECOND_NONE && p->precond != PLCG_PRECOND_JACOBI)
         return fail(PLCG_ERR_INVALID, "unknown preconditioner %d", p->precond);
     if (p->precond == PLCG_PRECOND_JACOBI) {
-        if (A->kind == kOpCsr && !A->jacobi_ok)
+        if (A->kind != kOpStencil && !A->jacobi_ok)
             return fail(PLCG_ERR_INVALID, "Jacobi preconditioner: a diagonal entry is not positive");
         if (A->kind == kOpStencil && !(A->st.center > 0.0))
             return fail(PLCG_ERR_INVALID, "Jacobi preconditioner: the stencil center is not positive");

@@ -11,8 +11,18 @@ constexpr int kMaxDots = 2 * kMaxL + 1;   // dot products per iteration (Algorit
 constexpr int kBlock = 256;               // threads per CTA of the persistent solver
 constexpr int kNormSlots = 2;             // doubles per CTA in the norm partials
 
-// kOpCsrJacobi: CSR with the Jacobi preconditioner M = diag(A) (Sec. 2.2).
-enum OpKind : int { kOpStencil = 0, kOpCsr = 1, kOpCsrJacobi = 2 };
+// Operators: constant-coefficient stencil, CSR, the structured symmetric
+// 27-point variable-coefficient stencil (diagonal + 13 forward weights per
+// cell); the *Jacobi kinds add the preconditioner M = diag(A) (Sec. 2.2).
+enum OpKind : int { kOpStencil = 0, kOpCsr = 1, kOpCsrJacobi = 2, kOpVar27 = 3, kOpVar27Jacobi = 4 };
+#ifdef __CUDACC__
+#define PLCG_HD __host__ __device__
+#else
+#define PLCG_HD
+#endif
+PLCG_HD constexpr bool op_is_csr(int op) { return op == kOpCsr || op == kOpCsrJacobi; }
+PLCG_HD constexpr bool op_is_var27(int op) { return op == kOpVar27 || op == kOpVar27Jacobi; }
+PLCG_HD constexpr bool op_is_jacobi(int op) { return op == kOpCsrJacobi || op == kOpVar27Jacobi; }
 
 // End reasons of one segment (a run of Algorithm 1 from a residual).
 enum SegEnd : int { kSegConverged = 0, kSegMaxit = 1, kSegBreakdown = 2, kSegLucky = 3,
@@ -58,7 +68,8 @@ struct StencilDesc {
 };
 
 // CSR arrays in device memory; val, dinv and diag are float or double (the
-// kernel's T).  dinv / diag (1 / a_rr and a_rr) are set for kOpCsrJacobi.
+// kernel's T).  dinv / diag (1 / a_rr and a_rr) are set for the Jacobi kinds.
+// The structured 27-point operator keeps its [14][n] coefficients in val.
 struct CsrDesc {
     const int64_t *rowptr;
     const int32_t *col;

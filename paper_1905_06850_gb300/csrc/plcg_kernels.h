@@ -26,6 +26,10 @@ const void *kptr_f32_st1(int l, bool cg);
 const void *kptr_f32_csr(int l, bool cg);
 const void *kptr_f64_csrj(int l, bool cg);
 const void *kptr_f32_csrj(int l, bool cg);
+const void *kptr_f64_v27(int l, bool cg);
+const void *kptr_f32_v27(int l, bool cg);
+const void *kptr_f64_v27j(int l, bool cg);
+const void *kptr_f32_v27j(int l, bool cg);
 
 // Sets the thread-local message returned by plcg_last_error().
 void set_last_error(const std::string &msg);
@@ -36,6 +40,12 @@ void set_last_error(const std::string &msg);
 cudaError_t launch_jacobi_setup(bool f32, const int64_t *rowptr, const int32_t *col,
                                 const void *val, int64_t n, double *dinv64, void *dinv,
                                 void *diag, int *bad, cudaStream_t s);
+
+// Jacobi data of the structured 27-point operator (diagonal = coef[0..n)):
+// dinv64 = 1 / diag (FP64), dinv in the stored type; *bad = 1 if an entry
+// is not positive.
+cudaError_t launch_var27_jacobi_setup(bool f32, const void *coef, int64_t n, double *dinv64,
+                                      void *dinv, int *bad, cudaStream_t s);
 
 // dst[i] = (float) src[i] on the device.
 cudaError_t launch_round_to_f32(const double *src, float *dst, int64_t n, cudaStream_t s);

@@ -364,6 +364,51 @@ __device__ __forceinline__ void stencil_apply(const StencilDesc &st, V cC, V cO,
     for (int v = 0; v < VEC; ++v) w[v] = fma(cO, nb[v], cC * c[v]);
 }
 
+// The 13 forward offsets (dz, dy, dx) of the structured 27-point operator,
+// lexicographic (the order of its coefficient arrays 1..13).
+__device__ __forceinline__ constexpr int v27_dz(int k) { return k < 4 ? 0 : 1; }
+__device__ __forceinline__ constexpr int v27_dy(int k)
+{
+    return k == 0 ? 0 : k < 4 ? 1 : k < 7 ? -1 : k < 10 ? 0 : 1;
+}
+__device__ __forceinline__ constexpr int v27_dx(int k)
+{
+    return k == 0 ? 1 : k < 4 ? k - 2 : (k - 4) % 3 - 1;
+}
+
+// Row g of the structured symmetric 27-point operator (VEC = 1): the full
+// (A z)_g = a_gg z_g + sum over the 13 forward offsets d of
+// w_d(g) z_{g+d} + w_d(g-d) z_{g-d}, where w_d(c) = coef[1+k][c] is the
+// entry A[c, c+d] and the backward entry comes from the neighbour by
+// symmetry; neighbours outside the grid are skipped (Dirichlet).  C is the
+// stored coefficient type.
+template <typename V, typename C, class Ld>
+__device__ __forceinline__ V var27_row(const StencilDesc &st, const C *coef, const Ld &ld, uint32_t g)
+{
+    const uint32_t nx = (uint32_t)st.nx, ny = (uint32_t)st.ny, nz = (uint32_t)st.nz;
+    const uint32_t nxy = nx * ny;
+    const size_t n = (size_t)nxy * nz;
+    const uint32_t line = (__umulhi(g, st.dnx.m) + g) >> st.dnx.s;
+    const uint32_t x = g - line * nx;
+    const uint32_t zc = (__umulhi(line, st.dny.m) + line) >> st.dny.s;
+    const uint32_t y = line - zc * ny;
+    const bool xm = x > 0, xp = x + 1 < nx, ym = y > 0, yp = y + 1 < ny, zm = zc > 0, zp = zc + 1 < nz;
+    V s = (V)__ldg(coef + g) * ld.one(g);
+#pragma unroll
+    for (int k = 0; k < 13; ++k) {
+        const int dz = v27_dz(k), dy = v27_dy(k), dx = v27_dx(k);
+        const uint32_t off = (uint32_t)(dz * (int)nxy + dy * (int)nx + dx);   // > 0
+        const bool fwd = (dx > 0 ? xp : dx < 0 ? xm : true) && (dy > 0 ? yp : dy < 0 ? ym : true) &&
+                         (dz > 0 ? zp : true);
+        const bool bwd = (dx > 0 ? xm : dx < 0 ? xp : true) && (dy > 0 ? ym : dy < 0 ? yp : true) &&
+                         (dz > 0 ? zm : true);
+        const C *ck = coef + (size_t)(1 + k) * n;
+        if (fwd) s = fma((V)__ldg(ck + g), ld.one(g + off), s);
+        if (bwd) s = fma((V)__ldg(ck + (g - off)), ld.one(g - off), s);
+    }
+    return s;
+}
+
 // CSR row (VEC = 1).  C is the stored value type (float or double).
 template <typename V, typename C, class Ld>
 __device__ __forceinline__ V csr_row(const CsrDesc &A, const Ld &ld, uint32_t row)
@@ -453,6 +498,10 @@ __device__ __forceinline__ void op_parts(const StencilDesc &st, const CsrDesc &c
 {
     if constexpr (OP == kOpStencil) {
         stencil_parts<V, VEC>(st, ld, g0, c, nb);
+    } else if constexpr (op_is_var27(OP)) {
+        static_assert(VEC == 1, "27-point rows are one per thread");
+        c[0] = ld.one(g0);
+        nb[0] = var27_row<V, C>(st, static_cast<const C *>(csr.val), ld, g0);
     } else {
         static_assert(VEC == 1, "CSR rows are one per thread");
         c[0] = ld.one(g0);
@@ -466,6 +515,10 @@ __device__ __forceinline__ void op_apply(const StencilDesc &st, const CsrDesc &c
 {
     if constexpr (OP == kOpStencil) {
         stencil_apply<V, VEC>(st, cC, cO, ld, g0, c, w);
+    } else if constexpr (op_is_var27(OP)) {
+        static_assert(VEC == 1, "27-point rows are one per thread");
+        c[0] = ld.one(g0);
+        w[0] = var27_row<V, C>(st, static_cast<const C *>(csr.val), ld, g0);
     } else {
         static_assert(VEC == 1, "CSR rows are one per thread");
         c[0] = ld.one(g0);
@@ -978,6 +1031,9 @@ __device__ void residual_sweep(const SolveArgs<T> &a, Smem<T> &s, const Grp &grp
         double c[V64], w[V64], bv[V64];
         if constexpr (OP == kOpStencil) {
             stencil_apply<double, V64>(a.st, cC, cO, ld, g0, c, w);
+        } else if constexpr (op_is_var27(OP)) {
+            c[0] = a.x[g0];
+            w[0] = var27_row<double, T>(a.st, static_cast<const T *>(a.csr.val), ld, g0);
         } else {
             c[0] = a.x[g0];
             w[0] = csr_row<double, T>(a.csr, ld, g0);
@@ -987,7 +1043,7 @@ __device__ void residual_sweep(const SolveArgs<T> &a, Smem<T> &s, const Grp &grp
 #pragma unroll
         for (int v = 0; v < V64; ++v) {
             rv[v] = bv[v] - w[v];
-            if constexpr (OP == kOpCsrJacobi) {
+            if constexpr (op_is_jacobi(OP)) {
                 const double mi = __ldg(a.dinv64 + g0 + v);
                 acc[0] = fma(bv[v] * mi, bv[v], acc[0]);
                 acc[1] = fma(rv[v] * mi, rv[v], acc[1]);
@@ -1038,7 +1094,7 @@ __device__ void plcg_body(const SolveArgs<T> &a, Smem<T> &s, Grp &grp)
     constexpr bool kOolScalar = kF32 && std::is_same<Grp, GridGroup<T>>::value;
     // CSR on the whole grid: each sweep unit's entries are bulk-copied into
     // shared memory (one contiguous range per unit) before its rows are read
-    constexpr bool kStage = OP != kOpStencil && std::is_same<Grp, GridGroup<T>>::value && RPT == 1;
+    constexpr bool kStage = op_is_csr(OP) && std::is_same<Grp, GridGroup<T>>::value && RPT == 1;
     extern __shared__ __align__(128) unsigned char plcg_dsm[];
     CsrStage<T> stage(plcg_dsm);
     if constexpr (kStage) {
@@ -1114,7 +1170,7 @@ __device__ void plcg_body(const SolveArgs<T> &a, Smem<T> &s, Grp &grp)
                 T z[VEC];
 #pragma unroll
                 for (int v = 0; v < VEC; ++v) {
-                    if constexpr (OP == kOpCsrJacobi)
+                    if constexpr (op_is_jacobi(OP))
                         z[v] = (T)(a.r[g0 + v] * __ldg(a.dinv64 + g0 + v) * inv);
                     else
                         z[v] = (T)(a.r[g0 + v] * inv);
@@ -1274,7 +1330,7 @@ __device__ void plcg_body(const SolveArgs<T> &a, Smem<T> &s, Grp &grp)
                         } else {
                             op_parts<T, T, VEC, OP>(st, csr, Ld1<T>{C.zl_cur}, g0[r], c[r], nb[r]);
                         }
-                        if constexpr (OP == kOpCsrJacobi) {
+                        if constexpr (op_is_jacobi(OP)) {
                             // K1 with M = diag(A): z^(l)_{i+1} is built from M^{-1} A z^(l)_i
                             nb[r][0] *= __ldg(static_cast<const T *>(csr.dinv) + g0[r]);
                             dg[r] = __ldg(static_cast<const T *>(csr.diag) + g0[r]);
@@ -1347,7 +1403,7 @@ __device__ void plcg_body(const SolveArgs<T> &a, Smem<T> &s, Grp &grp)
                         // (M = I: z^(l)_{i+1} itself)
                         T uM[VEC];
 #pragma unroll
-                        for (int v = 0; v < VEC; ++v) uM[v] = (OP == kOpCsrJacobi) ? un[v] * dg[r] : un[v];
+                        for (int v = 0; v < VEC; ++v) uM[v] = op_is_jacobi(OP) ? un[v] * dg[r] : un[v];
 #pragma unroll
                         for (int q = 0; q <= 2 * L; ++q) {
                             const int src = S ? steady_dot_src<L>(q) : C.dsrc[q];
@@ -1432,7 +1488,7 @@ __device__ void cg_body(const SolveArgs<T> &a, Smem<T> &s, Grp &grp)
     // CSR on the whole grid, FP32: the SpMV sweep stages each unit's entries
     // (as in p(l)-CG).  FP64 CG runs without: its 3 CTAs per SM would not fit
     // the FP64 staging buffer (measured: 2 CTAs with staging are slower).
-    constexpr bool kStage = OP != kOpStencil && std::is_same<Grp, GridGroup<T>>::value && RPT == 1 &&
+    constexpr bool kStage = op_is_csr(OP) && std::is_same<Grp, GridGroup<T>>::value && RPT == 1 &&
                             sizeof(T) == 4;
     extern __shared__ __align__(128) unsigned char plcg_dsm[];
     CsrStage<T> stage(plcg_dsm);
@@ -1498,7 +1554,7 @@ __device__ void cg_body(const SolveArgs<T> &a, Smem<T> &s, Grp &grp)
                 T z[VEC], zero[VEC], zm[VEC];
 #pragma unroll
                 for (int v = 0; v < VEC; ++v) {
-                    if constexpr (OP == kOpCsrJacobi) {
+                    if constexpr (op_is_jacobi(OP)) {
                         z[v] = (T)(a.r[g0 + v] * __ldg(a.dinv64 + g0 + v));
                         zm[v] = z[v] * __ldg(static_cast<const T *>(csr.diag) + g0 + v);
                     } else {
@@ -1518,7 +1574,7 @@ __device__ void cg_body(const SolveArgs<T> &a, Smem<T> &s, Grp &grp)
             CG_SYNC();
             grp.template get_dots<1>(a, s, 0, s.raw);
             rr = s.raw[0];
-        } else if constexpr (OP == kOpCsrJacobi) {
+        } else if constexpr (op_is_jacobi(OP)) {
             // FP64 path: z = M^{-1} r in r's place; rr = (r, M^{-1} r) = rn^2
             for (int64_t u = grp.unit0(); u < nunits; u += grp.ustep()) {
                 const int64_t g = u * UNIT + (int64_t)tid;
@@ -1567,7 +1623,7 @@ __device__ void cg_body(const SolveArgs<T> &a, Smem<T> &s, Grp &grp)
                     } else {
                         op_apply<T, T, VEC, OP>(st, csr, cC, cO, LdAxpy<T>{rc, po, (T)beta}, g0[r], c[r], w[r]);
                     }
-                    if constexpr (OP == kOpCsrJacobi)
+                    if constexpr (op_is_jacobi(OP))
                         mi[r] = __ldg(static_cast<const T *>(csr.dinv) + g0[r]);
                 }
 #pragma unroll
@@ -1575,7 +1631,7 @@ __device__ void cg_body(const SolveArgs<T> &a, Smem<T> &s, Grp &grp)
                     if (g0[r] >= nn) continue;
                     vst<T, VEC>(pn + g0[r], c[r]);
                     d1.add(c[r], w[r]);
-                    if constexpr (OP == kOpCsrJacobi) w[r][0] *= mi[r];   // q = M^{-1} A p
+                    if constexpr (op_is_jacobi(OP)) w[r][0] *= mi[r];   // q = M^{-1} A p
                     vst<T, VEC>(q + g0[r], w[r]);
                 }
                 if (++since_flush == kFlushUnits) { d1.flush(); since_flush = 0; }
@@ -1605,7 +1661,7 @@ __device__ void cg_body(const SolveArgs<T> &a, Smem<T> &s, Grp &grp)
                     vld<T, VEC>(q + g0[r], qv[r]);
                     vld<T, VEC>(xi + g0[r], xv[r]);
                     vld<T, VEC>(rc + g0[r], rv[r]);
-                    if constexpr (OP == kOpCsrJacobi)
+                    if constexpr (op_is_jacobi(OP))
                         vldg<T, VEC>(static_cast<const T *>(csr.diag) + g0[r], dv[r]);
                 }
 #pragma unroll
@@ -1618,7 +1674,7 @@ __device__ void cg_body(const SolveArgs<T> &a, Smem<T> &s, Grp &grp)
                     }
                     vst<T, VEC>(xi + g0[r], xv[r]);
                     vst<T, VEC>(rc + g0[r], rv[r]);
-                    if constexpr (OP == kOpCsrJacobi) {   // rho = (r, z) = sum a_gg z_g^2
+                    if constexpr (op_is_jacobi(OP)) {   // rho = (r, z) = sum a_gg z_g^2
 #pragma unroll
                         for (int v = 0; v < VEC; ++v) dv[r][v] *= rv[r][v];
                         d2.add(dv[r], rv[r]);

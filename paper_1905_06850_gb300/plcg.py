@@ -70,6 +70,8 @@ SIGNATURES = {
     "plcg_create_stencil": (C.c_int, [C.POINTER(plcg_stencil_desc), _VP, C.POINTER(_VP)]),
     "plcg_create_csr": (C.c_int, [C.c_int64, C.c_int64, _VP, _VP, _VP, C.c_int, C.c_int, _VP,
                                   C.POINTER(_VP)]),
+    "plcg_create_var27": (C.c_int, [C.c_int64, C.c_int64, C.c_int64, _VP, C.c_int, C.c_int, _VP,
+                                    C.POINTER(_VP)]),
     "plcg_destroy": (None, [_VP]),
     "plcg_solve": (C.c_int, [_VP, _VP, _VP, C.POINTER(plcg_params), C.POINTER(plcg_result)]),
     "plcg_solve_host": (C.c_int, [_VP, _VP, _VP, C.POINTER(plcg_params), C.POINTER(plcg_result)]),
@@ -179,15 +181,26 @@ def make_params(method="plcg", l=1, shifts=None, interval=(0.0, 8.0), rtol=1e-8,
 
 
 class Matrix:
-    """A device operator (stencil or CSR) owned by the library."""
+    """A device operator (stencil, CSR or structured 27-point) owned by the library."""
 
     def __init__(self, op: dict, prec="fp64", stream=None):
         lib = load()
         self.op = op
-        self.n = int(op["n"]) if op["kind"] == "csr" else \
-            int(op["nx"]) * int(op["ny"]) * (int(op["nz"]) if op["dim"] == 3 else 1)
+        if op["kind"] == "csr":
+            self.n = int(op["n"])
+        elif op["kind"] == "var27":
+            self.n = int(op["nx"]) * int(op["ny"]) * int(op["nz"])
+        else:
+            self.n = int(op["nx"]) * int(op["ny"]) * (int(op["nz"]) if op["dim"] == 3 else 1)
         h = _VP()
-        if op["kind"] == "stencil":
+        if op["kind"] == "var27":
+            coef = np.ascontiguousarray(op["coef"], dtype=np.float64)
+            if coef.shape != (14, self.n):
+                raise ValueError("var27 coef must have shape (14, n)")
+            pc = PLCG_FP32_FP64DOT if prec == "fp32" else PLCG_FP64
+            _check(lib.plcg_create_var27(int(op["nx"]), int(op["ny"]), int(op["nz"]), coef.ctypes.data,
+                                         0, pc, _VP(_stream_ptr(stream)), C.byref(h)))
+        elif op["kind"] == "stencil":
             d = plcg_stencil_desc(dim=int(op["dim"]), points=5 if op["dim"] == 2 else 7,
                                   nx=int(op["nx"]), ny=int(op["ny"]),
                                   nz=int(op["nz"]) if op["dim"] == 3 else 1,
