@@ -77,7 +77,8 @@ struct plcg_matrix {
     int64_t nnz = 0;
     int64_t *rowptr = nullptr;
     int32_t *col = nullptr;
-    void *val = nullptr;
+    void *val = nullptr;         // CSR values; structured 27-point: [14][cstride] coefficients
+    int64_t cstride = 0;
     // Jacobi data (CSR): 1 / a_rr in FP64, 1 / a_rr and a_rr in the stored type
     double *jdinv64 = nullptr;
     void *jdinv = nullptr;
@@ -274,10 +275,17 @@ extern "C" plcg_status plcg_create_var27(int64_t nx, int64_t ny, int64_t nz, con
     const cudaMemcpyKind kind = on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice;
     const size_t vsz = (prec == PLCG_FP64) ? sizeof(double) : sizeof(float);
     const size_t cnt = (size_t)14 * n;
-    cudaError_t e = cudaMalloc(&A->val, cnt * vsz);
+    // the 14 arrays start on 256-byte boundaries (stride rounded up to 64
+    // elements) and the allocation carries 64 elements of zeroed padding, so
+    // the staged sweep can copy 16-byte-rounded segments
+    A->cstride = (n + 63) / 64 * 64;
+    const size_t alloc = ((size_t)14 * A->cstride + 64) * vsz;
+    cudaError_t e = cudaMalloc(&A->val, alloc);
+    if (e == cudaSuccess) e = cudaMemset(A->val, 0, alloc);
     if (e == cudaSuccess) {
         if (prec == PLCG_FP64) {
-            e = cudaMemcpy(A->val, coef, cnt * sizeof(double), kind);
+            e = cudaMemcpy2D(A->val, A->cstride * sizeof(double), coef, n * sizeof(double),
+                             n * sizeof(double), 14, kind);
         } else {
             double *tmp = nullptr;
             const double *src = coef;
@@ -286,7 +294,9 @@ extern "C" plcg_status plcg_create_var27(int64_t nx, int64_t ny, int64_t nz, con
                 if (e == cudaSuccess) e = cudaMemcpy(tmp, coef, cnt * sizeof(double), kind);
                 src = tmp;
             }
-            if (e == cudaSuccess) e = launch_round_to_f32(src, static_cast<float *>(A->val), (int64_t)cnt, nullptr);
+            for (int j = 0; j < 14 && e == cudaSuccess; ++j)
+                e = launch_round_to_f32(src + (size_t)j * n, static_cast<float *>(A->val) + (size_t)j * A->cstride,
+                                        n, nullptr);
             if (e == cudaSuccess) e = cudaDeviceSynchronize();
             if (tmp) cudaFree(tmp);
         }
@@ -400,8 +410,10 @@ static plcg_status build_solve(const plcg_matrix *A, const double *b, double *x,
     const void *func = kernel_ptr(f32, op, vec, cg ? 0 : l, cg);
     if (!func) return fail(PLCG_ERR_UNIMPL, "no kernel for prec=%d op=%d vec=%d l=%d", (int)f32, op, vec, l);
     // CSR kernels stage each unit's entries in dynamic shared memory (FP64
-    // classic CG excepted, see cg_body)
-    const unsigned dsmem = (op_is_csr(op) && (!cg || f32)) ? csr_stage_bytes((unsigned)sizeof(T)) : 0u;
+    // classic CG excepted, see cg_body); the 27-point p(l)-CG kernels stage
+    // coefficient and z tiles
+    const unsigned dsmem = (op_is_csr(op) && (!cg || f32)) ? csr_stage_bytes((unsigned)sizeof(T))
+                         : (op_is_var27(op) && !cg && f32) ? v27_tile_bytes((unsigned)sizeof(T)) : 0u;
     if (dsmem) {
         CUDA_TRY(cudaFuncSetAttribute(func, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)dsmem));
         CUDA_TRY(cudaFuncSetAttribute(func, cudaFuncAttributePreferredSharedMemoryCarveout,
@@ -459,6 +471,10 @@ static plcg_status build_solve(const plcg_matrix *A, const double *b, double *x,
     a.csr.rowptr = A->rowptr;
     a.csr.col = A->col;
     a.csr.val = A->val;
+    a.csr.stride = A->cstride;
+    a.vstride = (int64_t)(vbytes / sizeof(T));   // ring vectors 256-byte aligned
+    a.ws_lo = base;
+    a.ws_hi = base + off;
     if (jac) {
         a.csr.dinv = A->jdinv;
         a.csr.diag = A->jdiag;

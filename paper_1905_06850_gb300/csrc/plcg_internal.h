@@ -76,6 +76,7 @@ struct CsrDesc {
     const void *val;
     const void *dinv;
     const void *diag;
+    int64_t stride;           // structured 27-point: elements between coefficient arrays
 };
 
 // Everything one persistent solve needs (passed by value to the kernel).
@@ -89,6 +90,7 @@ struct SolveArgs {
     const double *dinv64;     // kOpCsrJacobi: FP64 1 / a_rr (natural norms, M^{-1} r)
     double *r;                // FP64 residual b - A x
     T *zring;                 // ring storage of the l+1 bases (p(l)-CG) / p ring (CG)
+    int64_t vstride;          // elements between consecutive ring vectors
     int depth[kMaxL + 1];     // ring depth of basis k
     FastDivU32 ddiv[kMaxL + 1];   // division by depth[k] (ring slots)
     int64_t base[kMaxL + 1];  // offset (in vectors) of basis k's ring
@@ -111,8 +113,18 @@ struct SolveArgs {
     unsigned long long poll_limit;
     int force_timeout;
     int lookahead;            // l >= 2: compute the next iteration's scalars during the sweep
-    unsigned dsmem;           // dynamic shared memory of the launch (CSR entry staging)
+    unsigned dsmem;           // dynamic shared memory of the launch (CSR / 27-point staging)
+    const char *ws_lo, *ws_hi;   // the solve's workspace (bounds for staged copies)
 };
+
+// Structured 27-point tiles: per sweep unit, 36 shared-memory slots of
+// kV27Slot elements -- the diagonal and 13 forward coefficient segments, the
+// 13 backward segments, the 9 line segments of z around the unit.
+constexpr int kV27Slot = 256 + 16;
+constexpr unsigned v27_tile_bytes(unsigned value_bytes)
+{
+    return 16u + 36u * (unsigned)kV27Slot * value_bytes;
+}
 
 // CSR entries (column index + value) each warp of a CSR kernel stages in
 // shared memory for its 32 rows of a sweep unit; warps whose rows have more

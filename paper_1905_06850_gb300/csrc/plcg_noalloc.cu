@@ -110,6 +110,7 @@ plcg_status run(const StencilDesc &st, int64_t n, const double *b, double *x,
                       std::to_string(kScratchBytes) + " bytes (use plcg_solve)");
     a.n = n;
     a.st = st;
+    a.vstride = (int64_t)(vbytes / sizeof(T));
     a.b = b;
     a.x = x;
     a.r = reinterpret_cast<double *>(base + o_r);

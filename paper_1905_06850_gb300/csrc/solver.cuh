@@ -383,11 +383,12 @@ __device__ __forceinline__ constexpr int v27_dx(int k)
 // symmetry; neighbours outside the grid are skipped (Dirichlet).  C is the
 // stored coefficient type.
 template <typename V, typename C, class Ld>
-__device__ __forceinline__ V var27_row(const StencilDesc &st, const C *coef, const Ld &ld, uint32_t g)
+__device__ __forceinline__ V var27_row(const StencilDesc &st, const C *coef, int64_t stride,
+                                       const Ld &ld, uint32_t g)
 {
     const uint32_t nx = (uint32_t)st.nx, ny = (uint32_t)st.ny, nz = (uint32_t)st.nz;
     const uint32_t nxy = nx * ny;
-    const size_t n = (size_t)nxy * nz;
+    const size_t n = (size_t)stride;
     const uint32_t line = (__umulhi(g, st.dnx.m) + g) >> st.dnx.s;
     const uint32_t x = g - line * nx;
     const uint32_t zc = (__umulhi(line, st.dny.m) + line) >> st.dny.s;
@@ -432,6 +433,140 @@ __device__ __forceinline__ V csr_row_staged(const CsrDesc &A, const int32_t *sco
     for (uint32_t k = k0; k < k1; ++k) s = fma((V)sval[k], ld.one((uint32_t)scol[k]), s);
     return s;
 }
+
+// Per-CTA tile of the structured 27-point operator for one sweep unit of
+// rows [r0, r1) (dynamic shared memory: an mbarrier, then 36 slots of
+// kV27Slot elements): slots 0..13 the diagonal and forward coefficients of
+// the unit's rows, 14..26 the backward coefficients (forward array k at rows
+// g - d_k), 27..35 the nine line segments of z around the unit ((dz, dy) in
+// {-1,0,1}^2, x - 1 .. x + 1).  One bulk copy per slot, each rounded out
+// to 16 bytes; the rounding puts element g of a slot at a
+// shift that is fixed for the whole solve (the arrays and ring vectors start
+// on 256-byte boundaries and units on multiples of 4 rows), so the shifts are
+// computed once.  A unit whose copies would leave the arrays' allocations
+// falls back to global loads.
+template <typename T>
+struct Var27Tile {
+    static constexpr int A = 16 / (int)sizeof(T);   // elements per 16 bytes
+    uint64_t *bar;
+    T *slot;
+    uint32_t parity = 0;
+    uint32_t shb = 0, shz = 0;   // 2-bit shifts of the backward and z slots
+    __device__ __forceinline__ explicit Var27Tile(unsigned char *dsm)
+        : bar(reinterpret_cast<uint64_t *>(dsm)), slot(reinterpret_cast<T *>(dsm + 16))
+    {
+    }
+    __device__ __forceinline__ void init(const StencilDesc &st)
+    {
+        if (threadIdx.x == 0) mbar_init(bar, 36);
+        const int nx = st.nx, nxy = st.nx * st.ny;
+        for (int k = 0; k < 13; ++k) {
+            const int off = v27_dz(k) * nxy + v27_dy(k) * nx + v27_dx(k);
+            shb |= (uint32_t)(((-off) % A + A) % A) << (2 * k);
+        }
+        for (int q = 0; q < 9; ++q) {
+            const int d = (q / 3 - 1) * nxy + (q % 3 - 1) * nx;
+            shz |= (uint32_t)(((d - 1) % A + A) % A) << (2 * q);
+        }
+    }
+    __device__ __forceinline__ int sb(int k) const { return (int)((shb >> (2 * k)) & 3u); }
+    __device__ __forceinline__ int sz(int q) const { return (int)((shz >> (2 * q)) & 3u); }
+    // Stage rows [r0, r1).  Threads 0..35 each own one slot: they check that
+    // their 16-byte-rounded range stays inside its allocation ([clo, chi) for
+    // coefficients, [zlo, zhi) for z), the first `nthreads` threads agree on
+    // the result with a barrier reduction (which also orders every read of the
+    // previous unit's tile before the new copies), and the owners issue their
+    // copies, each arriving on the mbarrier (init count 36) with its bytes.
+    // Returns false when the unit is to be read from global memory.
+    __device__ __forceinline__ bool stage(const StencilDesc &st, const T *coef, int64_t cstride,
+                                          const char *clo, const char *chi, const T *z,
+                                          const char *zlo, const char *zhi, uint32_t r0, uint32_t r1,
+                                          int nthreads, unsigned long long limit, int *abort_flag)
+    {
+        const int sl = threadIdx.x;
+        uintptr_t b0 = 0, b1 = 0;
+        int ok = 1;
+        if (sl < 36) {
+            const int64_t nx = st.nx, nxy = (int64_t)st.nx * st.ny;
+            const T *base;
+            int64_t lo, hi;
+            if (sl < 14) {
+                base = coef + sl * cstride;
+                lo = r0;
+                hi = r1;
+            } else if (sl < 27) {
+                const int k = sl - 14;
+                const int64_t off = v27_dz(k) * nxy + v27_dy(k) * nx + v27_dx(k);
+                base = coef + (1 + k) * cstride;
+                lo = (int64_t)r0 - off;
+                hi = (int64_t)r1 - off;
+                if (hi <= 0) lo = hi = 0;   // no row of the unit has this backward neighbour
+            } else {
+                const int q = sl - 27;
+                const int64_t d = (q / 3 - 1) * nxy + (q % 3 - 1) * nx;
+                base = z;
+                lo = (int64_t)r0 + d - 1;
+                hi = (int64_t)r1 + d + 1;
+            }
+            if (hi > lo) {
+                const char *mlo = sl < 27 ? clo : zlo, *mhi = sl < 27 ? chi : zhi;
+                b0 = reinterpret_cast<uintptr_t>(base + lo) & ~uintptr_t(15);
+                b1 = (reinterpret_cast<uintptr_t>(base + hi) + 15) & ~uintptr_t(15);
+                ok = b0 >= reinterpret_cast<uintptr_t>(mlo) && b1 <= reinterpret_cast<uintptr_t>(mhi) &&
+                     b1 - b0 <= (uintptr_t)(kV27Slot * sizeof(T));
+            }
+        }
+        int all;
+        asm volatile("{\n\t.reg .pred p, q;\n\t"
+                     "setp.ne.s32 p, %1, 0;\n\t"
+                     "bar.red.and.pred q, 1, %2, p;\n\t"
+                     "selp.s32 %0, 1, 0, q;\n\t}"
+                     : "=r"(all) : "r"(ok), "r"(nthreads) : "memory");
+        if (!all) return false;
+        if (sl < 36) {
+            fence_proxy_async_smem();
+            const uint32_t bytes = (uint32_t)(b1 - b0);
+            mbar_arrive_expect_tx(bar, bytes);
+            if (bytes) bulk_copy_g2s(slot + sl * kV27Slot, reinterpret_cast<const void *>(b0), bytes, bar);
+        }
+        if (!mbar_wait(bar, parity, limit)) {
+            atomicExch(abort_flag, 1);
+            mbar_wait(bar, parity, limit);
+        }
+        parity ^= 1u;
+        return true;
+    }
+    // (A z)_g for row g = r0 + t of the staged unit (z's centre value in *zc).
+    template <typename V>
+    __device__ __forceinline__ V row(const StencilDesc &st, uint32_t g, int t, V *zc) const
+    {
+        const uint32_t nx = (uint32_t)st.nx, ny = (uint32_t)st.ny, nz = (uint32_t)st.nz;
+        const uint32_t line = (__umulhi(g, st.dnx.m) + g) >> st.dnx.s;
+        const uint32_t x = g - line * nx;
+        const uint32_t zz = (__umulhi(line, st.dny.m) + line) >> st.dny.s;
+        const uint32_t y = line - zz * ny;
+        const bool xm = x > 0, xp = x + 1 < nx, ym = y > 0, yp = y + 1 < ny, zm = zz > 0, zp = zz + 1 < nz;
+        const T *zs = slot + 27 * kV27Slot;
+        auto zat = [&](int dz, int dy, int dx) -> V {
+            const int q = (dz + 1) * 3 + (dy + 1);
+            return (V)zs[q * kV27Slot + t + 1 + dx + sz(q)];
+        };
+        const V c = zat(0, 0, 0);
+        *zc = c;
+        V s = (V)slot[t] * c;
+#pragma unroll
+        for (int k = 0; k < 13; ++k) {
+            const int dz = v27_dz(k), dy = v27_dy(k), dx = v27_dx(k);
+            const bool fwd = (dx > 0 ? xp : dx < 0 ? xm : true) && (dy > 0 ? yp : dy < 0 ? ym : true) &&
+                             (dz > 0 ? zp : true);
+            const bool bwd = (dx > 0 ? xm : dx < 0 ? xp : true) && (dy > 0 ? ym : dy < 0 ? yp : true) &&
+                             (dz > 0 ? zm : true);
+            if (fwd) s = fma((V)slot[(1 + k) * kV27Slot + t], zat(dz, dy, dx), s);
+            if (bwd) s = fma((V)slot[(14 + k) * kV27Slot + t + sb(k)], zat(-dz, -dy, -dx), s);
+        }
+        return s;
+    }
+};
 
 // Per-warp staging of CSR entries in shared memory (dynamic shared memory,
 // layout in plcg_internal.h).  Every warp stages the entries of its own 32
@@ -501,7 +636,7 @@ __device__ __forceinline__ void op_parts(const StencilDesc &st, const CsrDesc &c
     } else if constexpr (op_is_var27(OP)) {
         static_assert(VEC == 1, "27-point rows are one per thread");
         c[0] = ld.one(g0);
-        nb[0] = var27_row<V, C>(st, static_cast<const C *>(csr.val), ld, g0);
+        nb[0] = var27_row<V, C>(st, static_cast<const C *>(csr.val), csr.stride, ld, g0);
     } else {
         static_assert(VEC == 1, "CSR rows are one per thread");
         c[0] = ld.one(g0);
@@ -518,7 +653,7 @@ __device__ __forceinline__ void op_apply(const StencilDesc &st, const CsrDesc &c
     } else if constexpr (op_is_var27(OP)) {
         static_assert(VEC == 1, "27-point rows are one per thread");
         c[0] = ld.one(g0);
-        w[0] = var27_row<V, C>(st, static_cast<const C *>(csr.val), ld, g0);
+        w[0] = var27_row<V, C>(st, static_cast<const C *>(csr.val), csr.stride, ld, g0);
     } else {
         static_assert(VEC == 1, "CSR rows are one per thread");
         c[0] = ld.one(g0);
@@ -613,7 +748,7 @@ __device__ __forceinline__ T *ring(const SolveArgs<T> &a, int k, long long j)
 {
     const uint32_t jj = (uint32_t)j;
     const uint32_t q = (__umulhi(jj, a.ddiv[k].m) + jj) >> a.ddiv[k].s;
-    return a.zring + (a.base[k] + (int64_t)(jj - q * (uint32_t)a.depth[k])) * a.n;
+    return a.zring + (a.base[k] + (int64_t)(jj - q * (uint32_t)a.depth[k])) * a.vstride;
 }
 
 // ------------------------------------------------------------------------
@@ -1033,7 +1168,7 @@ __device__ void residual_sweep(const SolveArgs<T> &a, Smem<T> &s, const Grp &grp
             stencil_apply<double, V64>(a.st, cC, cO, ld, g0, c, w);
         } else if constexpr (op_is_var27(OP)) {
             c[0] = a.x[g0];
-            w[0] = var27_row<double, T>(a.st, static_cast<const T *>(a.csr.val), ld, g0);
+            w[0] = var27_row<double, T>(a.st, static_cast<const T *>(a.csr.val), a.csr.stride, ld, g0);
         } else {
             c[0] = a.x[g0];
             w[0] = csr_row<double, T>(a.csr, ld, g0);
@@ -1099,6 +1234,16 @@ __device__ void plcg_body(const SolveArgs<T> &a, Smem<T> &s, Grp &grp)
     CsrStage<T> stage(plcg_dsm);
     if constexpr (kStage) {
         stage.init();
+        __syncthreads();
+    }
+    // structured 27-point operator on the whole grid, FP32: each sweep unit's
+    // coefficients and z^(l) lines are staged as a shared-memory tile (the
+    // FP64 sweep is bound by the FP64 units and measured faster without)
+    constexpr bool kTile = op_is_var27(OP) && std::is_same<Grp, GridGroup<T>>::value && RPT == 1 &&
+                           sizeof(T) == 4;
+    Var27Tile<T> tile(plcg_dsm);
+    if constexpr (kTile) {
+        tile.init(a.st);
         __syncthreads();
     }
     const int64_t n = a.n;
@@ -1310,6 +1455,13 @@ __device__ void plcg_body(const SolveArgs<T> &a, Smem<T> &s, Grp &grp)
                         const uint32_t w0 = u * usw + (uint32_t)(tid & ~31);
                         stg = stage.stage(csr, w0, min(w0 + 32u, nn), &e0s, a.poll_limit, &a.out->abort);
                     }
+                    if constexpr (kTile) {    // the unit's coefficients and z^(l)_i lines
+                        const char *clo = static_cast<const char *>(csr.val);
+                        const char *chi = clo + (14 * csr.stride + 64) * (int64_t)sizeof(T);
+                        stg = tile.stage(st, static_cast<const T *>(csr.val), csr.stride, clo, chi, C.zl_cur,
+                                         a.ws_lo, a.ws_hi, u * usw, min(u * usw + usw, nn), nsw,
+                                         a.poll_limit, &a.out->abort);
+                    }
                     // -- loads
                     T c[RPT][VEC], nb[RPT][VEC], zp[RPT][VEC], cur[RPT][L][VEC], pk[RPT][L][VEC];
                     T pv[RPT][VEC], xv[RPT][VEC];
@@ -1324,6 +1476,14 @@ __device__ void plcg_body(const SolveArgs<T> &a, Smem<T> &s, Grp &grp)
                             if (stg) {
                                 c[r][0] = C.zl_cur[g0[r]];
                                 nb[r][0] = csr_row_staged<T, T>(csr, stage.col, stage.val, e0s, Ld1<T>{C.zl_cur}, g0[r]);
+                            } else {
+                                op_parts<T, T, VEC, OP>(st, csr, Ld1<T>{C.zl_cur}, g0[r], c[r], nb[r]);
+                            }
+                        } else if constexpr (kTile) {
+                            if (stg) {
+                                T zc;
+                                nb[r][0] = tile.template row<T>(st, g0[r], (int)(g0[r] - u * usw), &zc);
+                                c[r][0] = zc;
                             } else {
                                 op_parts<T, T, VEC, OP>(st, csr, Ld1<T>{C.zl_cur}, g0[r], c[r], nb[r]);
                             }
@@ -1779,6 +1939,7 @@ __device__ __forceinline__ void batch_args(const BatchArgs<T> &ba, const BatchSy
     // workspace: ring vectors, p, rc (type T), then r (FP64)
     const int64_t nv = a.n;
     a.zring = ws;
+    a.vstride = nv;
     int nvec = 0;
     for (int j = 0; j <= kMaxL; ++j) nvec += (j <= a.l) ? a.depth[j] : 0;
     if (a.method == 1) nvec = 3;
