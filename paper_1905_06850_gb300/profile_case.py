@@ -18,7 +18,7 @@ import argparse
 
 def main(argv=None):
     ap = argparse.ArgumentParser(description=__doc__.splitlines()[0])
-    ap.add_argument("--workload", choices=["3d", "2d", "h27", "e3", "batched"], default="3d")
+    ap.add_argument("--workload", choices=["3d", "2d", "h27", "h27v", "e3", "batched"], default="3d")
     ap.add_argument("--nx", type=int, default=128)
     ap.add_argument("--count", type=int, default=512)
     ap.add_argument("--prec", choices=["fp64", "fp32"], default="fp64")
@@ -62,11 +62,14 @@ def main(argv=None):
         c = W.config_2d(nx=args.nx)
     elif args.workload == "h27":
         c = W.config_hetero27(nx=args.nx)
+    elif args.workload == "h27v":
+        c = W.config_hetero27_var27(nx=args.nx)
+        c["interval"] = W.shift_interval(c["op"])
     else:
         c = W.e3_diagonal(args.nx)
     op = c["op"]
     interval = W.jacobi_shift_interval(op) if args.precond == "jacobi" else c["interval"]
-    A = plcg.Matrix(op, prec=args.prec if op["kind"] == "csr" else "fp64")
+    A = plcg.Matrix(op, prec=args.prec if op["kind"] != "stencil" else "fp64")
     b = torch.tensor(c["b"], device=dev)
     for r in range(args.warmup + args.runs):
         x = torch.zeros_like(b)
