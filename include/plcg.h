@@ -170,6 +170,19 @@ plcg_status plcg_create_csr(int64_t n, int64_t nnz, const int64_t *rowptr,
 plcg_status plcg_create_var27(int64_t nx, int64_t ny, int64_t nz, const double *coef,
                               int on_device, int prec, void *stream, plcg_matrix **out);
 
+/* Estimate the spectrum interval the Chebyshev shifts need (Sec. 2.2: the
+ * extreme eigenvalues "can be estimated a priori"): `steps` iterations of
+ * classic CG on the GPU (prm->prec and prm->precond: the operator is A, or
+ * diag(A)^{-1} A with PLCG_PRECOND_JACOBI) from a fixed pseudo-random
+ * right-hand side, whose coefficients give the Lanczos tridiagonal matrix;
+ * *lmin and *lmax are its smallest and largest eigenvalues (Ritz values:
+ * inside the true interval, the largest one close to lambda_max after a few
+ * tens of steps).  steps in [2, 1000].  Runs on the matrix's stream and uses
+ * its workspace and host-entry staging buffers.
+ * Errors: PLCG_ERR_INVALID, PLCG_ERR_NONFINITE, PLCG_ERR_CUDA, PLCG_ERR_NOMEM. */
+plcg_status plcg_estimate_interval(plcg_matrix *A, const plcg_params *prm, int steps, double *lmin,
+                                   double *lmax);
+
 /* Release the matrix, its device copies and workspaces.  NULL is a no-op. */
 void plcg_destroy(plcg_matrix *A);
 

@@ -25,6 +25,27 @@ const void *batched_kernel_ptr(bool f32, int l, bool cg)
     return f32 ? batched_kernel_ptr_f32(l, cg) : batched_kernel_ptr_f64(l, cg);
 }
 
+// v[i] uniform in [-1, 1): SplitMix64 (Steele, Lea, Flood, "Fast splittable
+// pseudorandom number generators", OOPSLA 2014) of (seed + i).
+__global__ void fill_random_kernel(double *v, int64_t n, uint64_t seed)
+{
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
+         i += (int64_t)gridDim.x * blockDim.x) {
+        uint64_t z = seed + (uint64_t)i * 0x9e3779b97f4a7c15ull;
+        z = (z ^ (z >> 30)) * 0xbf58476d1ce4e5b9ull;
+        z = (z ^ (z >> 27)) * 0x94d049bb133111ebull;
+        z ^= z >> 31;
+        v[i] = (double)(z >> 11) * (2.0 / 9007199254740992.0) - 1.0;
+    }
+}
+
+cudaError_t launch_fill_random(double *v, int64_t n, uint64_t seed, cudaStream_t s)
+{
+    const int64_t blocks = (n + 255) / 256;
+    fill_random_kernel<<<(unsigned)(blocks < 65535 ? (blocks > 0 ? blocks : 1) : 65535), 256, 0, s>>>(v, n, seed);
+    return cudaGetLastError();
+}
+
 __global__ void round_to_f32_kernel(const double *src, float *dst, int64_t n)
 {
     for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;

@@ -538,7 +538,8 @@ static plcg_status result_status(const DevResult &o)
 
 template <typename T>
 static plcg_status run_solve(plcg_matrix *A, const double *b, double *x, const plcg_params *prm,
-                             const double *sigma, plcg_result *res)
+                             const double *sigma, plcg_result *res, double *trace = nullptr,
+                             int trace_cap = 0)
 {
     SolveArgs<T> a;
     const void *func = nullptr;
@@ -552,6 +553,8 @@ static plcg_status run_solve(plcg_matrix *A, const double *b, double *x, const p
     st = build_solve<T>(A, b, x, prm, sigma, 0, static_cast<char *>(A->ws.mem), &a, &func, &P,
                         &per_sm, &bytes, &o_out);
     if (st != PLCG_OK) return st;
+    a.trace = trace;
+    a.trace_cap = trace_cap;
     CUDA_TRY(cudaEventRecord(A->ev0, A->stream));
     st = launch_built<T>(a, func, P, A->stream);
     if (st != PLCG_OK) return st;
@@ -649,6 +652,94 @@ extern "C" plcg_status plcg_solve_host(plcg_matrix *A, const double *b, double *
     CUDA_TRY(cudaMemcpyAsync(x, A->x_dev, A->n * sizeof(double), cudaMemcpyDeviceToHost, A->stream));
     CUDA_TRY(cudaStreamSynchronize(A->stream));
     return st;
+}
+
+// ------------------------------------------------------------------ spectrum
+// Number of eigenvalues of the symmetric tridiagonal (d, e) below x (Sturm
+// sequence of the LDL^T pivots; Golub & Van Loan, Matrix Computations, 8.4).
+static int sturm_count(const std::vector<double> &d, const std::vector<double> &e, double x)
+{
+    int cnt = 0;
+    double q = 1.0;
+    for (size_t j = 0; j < d.size(); ++j) {
+        q = (d[j] - x) - (j ? e[j - 1] * e[j - 1] / q : 0.0);
+        if (q == 0.0) q = -1e-300;
+        if (q < 0.0) ++cnt;
+    }
+    return cnt;
+}
+
+// The k-th smallest eigenvalue (k = 0 .. m-1) by bisection on [lo, hi].
+static double tridiag_eig(const std::vector<double> &d, const std::vector<double> &e, int k, double lo,
+                          double hi)
+{
+    for (int it = 0; it < 200 && hi - lo > 1e-13 * std::max(std::fabs(lo), std::fabs(hi)); ++it) {
+        const double mid = 0.5 * (lo + hi);
+        if (sturm_count(d, e, mid) > k) hi = mid;
+        else lo = mid;
+    }
+    return 0.5 * (lo + hi);
+}
+
+extern "C" plcg_status plcg_estimate_interval(plcg_matrix *A, const plcg_params *prm, int steps,
+                                              double *lmin, double *lmax)
+{
+    if (!A || !prm || !lmin || !lmax) return fail(PLCG_ERR_INVALID, "plcg_estimate_interval: NULL argument");
+    if (steps < 2 || steps > 1000) return fail(PLCG_ERR_INVALID, "plcg_estimate_interval: steps must be in [2, 1000]");
+    plcg_params p = *prm;
+    p.method = PLCG_METHOD_CG;
+    p.maxit = steps;
+    p.rtol = 1e-300;
+    p.max_restarts = 0;
+    p.inner_rtol_floor = 1e-300;   // FP32 path: the first inner solve runs all steps
+    plcg_status st = check_params(A, &p);
+    if (st != PLCG_OK) return st;
+    std::lock_guard<std::mutex> lock(A->mu);
+    CUDA_TRY(cudaSetDevice(A->device));
+    if (!A->b_dev) CUDA_TRY(cudaMalloc(&A->b_dev, A->n * sizeof(double)));
+    if (!A->x_dev) CUDA_TRY(cudaMalloc(&A->x_dev, A->n * sizeof(double)));
+    double *trace = nullptr;
+    CUDA_TRY(cudaMalloc(&trace, 2 * (size_t)steps * sizeof(double)));
+    cudaError_t e = launch_fill_random(A->b_dev, A->n, 0x5eed5eedull, A->stream);
+    if (e == cudaSuccess) e = cudaMemsetAsync(A->x_dev, 0, A->n * sizeof(double), A->stream);
+    if (e == cudaSuccess) e = cudaMemsetAsync(trace, 0, 2 * (size_t)steps * sizeof(double), A->stream);
+    if (e != cudaSuccess) {
+        cudaFree(trace);
+        return fail(PLCG_ERR_CUDA, "plcg_estimate_interval: %s", cudaGetErrorString(e));
+    }
+    plcg_result res{};
+    const double nosig[kMaxL] = {0};   // classic CG uses no shifts
+    st = (p.prec == PLCG_FP64) ? run_solve<double>(A, A->b_dev, A->x_dev, &p, nosig, &res, trace, steps)
+                               : run_solve<float>(A, A->b_dev, A->x_dev, &p, nosig, &res, trace, steps);
+    std::vector<double> t(2 * (size_t)steps, 0.0);
+    e = cudaMemcpy(t.data(), trace, t.size() * sizeof(double), cudaMemcpyDeviceToHost);
+    cudaFree(trace);
+    if (e != cudaSuccess) return fail(PLCG_ERR_CUDA, "plcg_estimate_interval: %s", cudaGetErrorString(e));
+    if (st != PLCG_OK && st != PLCG_ERR_MAXIT) return st;
+    // Lanczos tridiagonal of the (preconditioned) operator from the CG
+    // coefficients (Saad, Iterative Methods, Sec. 6.7.3):
+    // T_jj = 1/alpha_j + beta_{j-1}/alpha_{j-1}, T_{j,j+1} = sqrt(beta_j)/alpha_j
+    // the steps the first segment recorded (it ends early only when CG does)
+    int k = 0;
+    while (k < (int)std::min<int64_t>(res.iters, steps) && t[2 * k] != 0.0) ++k;
+    if (k < 1) return fail(PLCG_ERR_INVALID, "plcg_estimate_interval: no CG step completed");
+    std::vector<double> d(k), off(k > 1 ? k - 1 : 0);
+    for (int j = 0; j < k; ++j) {
+        const double al = t[2 * j], be = t[2 * j + 1];
+        if (!(al > 0.0) || !std::isfinite(al) || !(be >= 0.0))
+            return fail(PLCG_ERR_NONFINITE, "plcg_estimate_interval: invalid CG coefficient");
+        d[j] = 1.0 / al + (j ? t[2 * j - 1] / t[2 * j - 2] : 0.0);
+        if (j + 1 < k) off[j] = std::sqrt(be) / al;
+    }
+    double lo = d[0], hi = d[0];   // Gershgorin bracket of T
+    for (int j = 0; j < k; ++j) {
+        const double r = (j ? std::fabs(off[j - 1]) : 0.0) + (j + 1 < k ? std::fabs(off[j]) : 0.0);
+        lo = std::min(lo, d[j] - r);
+        hi = std::max(hi, d[j] + r);
+    }
+    *lmin = tridiag_eig(d, off, 0, lo, hi);
+    *lmax = tridiag_eig(d, off, k - 1, lo, hi);
+    return PLCG_OK;
 }
 
 // ------------------------------------------------------------------ batched

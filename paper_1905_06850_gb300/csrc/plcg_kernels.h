@@ -47,6 +47,9 @@ cudaError_t launch_jacobi_setup(bool f32, const int64_t *rowptr, const int32_t *
 cudaError_t launch_var27_jacobi_setup(bool f32, const void *coef, int64_t n, double *dinv64,
                                       void *dinv, int *bad, cudaStream_t s);
 
+// v[i] = a pseudo-random value in [-1, 1) from (seed, i) (SplitMix64).
+cudaError_t launch_fill_random(double *v, int64_t n, uint64_t seed, cudaStream_t s);
+
 // dst[i] = (float) src[i] on the device.
 cudaError_t launch_round_to_f32(const double *src, float *dst, int64_t n, cudaStream_t s);
 

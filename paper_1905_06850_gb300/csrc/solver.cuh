@@ -1852,6 +1852,10 @@ __device__ void cg_body(const SolveArgs<T> &a, Smem<T> &s, Grp &grp)
             grp.template get_dots<1>(a, s, 1, s.raw);
             const double rr_new = s.raw[0];
             beta = rr_new / rr;
+            if (a.trace && segments == 0 && k < a.trace_cap && grp.leader() && tid == 0) {
+                a.trace[2 * k] = alpha;   // the Lanczos coefficients of the (preconditioned) operator
+                a.trace[2 * k + 1] = beta;
+            }
             rr = rr_new;
             ++k;
         }

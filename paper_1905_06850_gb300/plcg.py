@@ -72,6 +72,8 @@ SIGNATURES = {
                                   C.POINTER(_VP)]),
     "plcg_create_var27": (C.c_int, [C.c_int64, C.c_int64, C.c_int64, _VP, C.c_int, C.c_int, _VP,
                                     C.POINTER(_VP)]),
+    "plcg_estimate_interval": (C.c_int, [_VP, C.POINTER(plcg_params), C.c_int, C.POINTER(C.c_double),
+                                         C.POINTER(C.c_double)]),
     "plcg_destroy": (None, [_VP]),
     "plcg_solve": (C.c_int, [_VP, _VP, _VP, C.POINTER(plcg_params), C.POINTER(plcg_result)]),
     "plcg_solve_host": (C.c_int, [_VP, _VP, _VP, C.POINTER(plcg_params), C.POINTER(plcg_result)]),
@@ -240,6 +242,15 @@ class Matrix:
         if check:
             _check(st)
         return _result(r)
+
+    def estimate_interval(self, steps=30, **kw):
+        """plcg_estimate_interval: (lmin, lmax) Ritz values of `steps` CG steps
+        (kw: prec, precond)."""
+        p, keep = make_params(**kw)
+        lo, hi = C.c_double(), C.c_double()
+        _check(load().plcg_estimate_interval(self.handle, C.byref(p), int(steps), C.byref(lo), C.byref(hi)))
+        del keep
+        return lo.value, hi.value
 
     def solve_host(self, b: np.ndarray, x: np.ndarray, check=True, **kw) -> Result:
         """plcg_solve_host on host float64 arrays (x in: x0, out: solution)."""

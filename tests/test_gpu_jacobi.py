@@ -279,3 +279,45 @@ def test_jacobi_hetero27_full_size(P):
         assert natural_relres(op32, b, x) < 1e-8 * 1.000001
     x, res = gpu_solve(P, op, b, prec="fp32", method="cg", rtol=1e-8, precond="jacobi")
     assert res.ok and natural_relres(op32, b, x) < 1e-8 * 1.000001
+
+
+# ------------------------------------------------------------ shift interval
+@pytest.mark.parametrize("precond", [None, "jacobi"])
+@pytest.mark.parametrize("prec", ["fp64", "fp32"])
+def test_estimate_interval_brackets_the_spectrum(P, precond, prec):
+    """plcg_estimate_interval returns Ritz values of the (preconditioned)
+    operator: inside [lambda_min, lambda_max] (scipy's eigenvalues of the same
+    matrix), the largest within 3% of lambda_max after 40 CG steps."""
+    import scipy.sparse.linalg as sla
+    op = W.hetero27_csr(16, 14, 12, seed=3)
+    opr = W.fp32_rounded(op) if prec == "fp32" else op
+    A = W.to_scipy(opr).tocsr()
+    if precond:
+        import scipy.sparse as sp
+        s = 1.0 / np.sqrt(A.diagonal())
+        A = (sp.diags(s) @ A @ sp.diags(s)).tocsr()   # similar to diag(A)^{-1} A
+    lmax = sla.eigsh(A, k=1, which="LA", return_eigenvectors=False)[0]
+    lmin = sla.eigsh(A, k=1, sigma=0, which="LM", return_eigenvectors=False)[0]
+    M = P.Matrix(op, prec=prec)
+    lo, hi = M.estimate_interval(steps=40, prec=prec, precond=precond)
+    M.close()
+    slack = 1e-6 if prec == "fp64" else 1e-4
+    assert lmin * (1 - slack) <= lo <= hi <= lmax * (1 + slack), (lo, hi, lmin, lmax)
+    assert hi >= 0.97 * lmax
+
+
+def test_estimated_interval_removes_fp32_breakdowns(P):
+    """Chebyshev shifts on the estimated interval [0, 1.02 lambda_max] instead
+    of the Gershgorin bound [0, 2]: the FP32 p(2)-CG with Jacobi runs without
+    square-root breakdowns and matches the oracle on that interval."""
+    M = P.Matrix(H27, prec="fp32")
+    lo, hi = M.estimate_interval(steps=40, prec="fp32", precond="jacobi")
+    M.close()
+    interval = (0.0, 1.02 * hi)
+    oop = W.fp32_rounded(H27)
+    sig = O.chebyshev_shifts(2, *interval)
+    ref = O.plcg(oop, H27_B, l=2, sigma=sig, rtol=1e-8, dots_2l1=False, precond="jacobi")
+    x, res = gpu_solve(P, H27, H27_B, prec="fp32", l=2, interval=interval, rtol=1e-8, precond="jacobi")
+    assert res.ok and res.restarts == 0
+    assert rel(x, ref.x) <= 1e-5
+    assert abs(res.iters - ref.iters) <= max(1, int(0.1 * ref.iters))
