@@ -384,12 +384,24 @@ def other_configs(plcg, W, dev, hbm_peak):
     b = torch.tensor(c["b"], device=dev)
     d = {"n": n, "nnz": nnz}
     jac = {"precond": "jacobi"}
+    # Chebyshev shift intervals [0, 1.02 lambda_max] from plcg_estimate_interval
+    # (30 CG steps on the GPU, once per operator; Sec. 2.2), for A and for
+    # diag(A)^{-1} A (Jacobi)
+    est = {}
+    for key, pk in (("none", None), ("jacobi", "jacobi")):
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        lo, hi = A.estimate_interval(steps=30, prec="fp32", precond=pk)
+        torch.cuda.synchronize()
+        est[key] = {"interval": [0.0, round(1.02 * hi, 6)], "ritz": [lo, hi],
+                    "seconds": round(time.perf_counter() - t0, 5)}
+    d["interval_estimates"] = est
     for name, kw in (("plcg_l1", {"l": 1}), ("plcg_l2", {"l": 2}), ("plcg_l3", {"l": 3}),
                      ("classic_cg", {"method": "cg"}),
                      ("jacobi_plcg_l1", {"l": 1, **jac}), ("jacobi_plcg_l2", {"l": 2, **jac}),
                      ("jacobi_plcg_l3", {"l": 3, **jac}), ("jacobi_classic_cg", {"method": "cg", **jac})):
         # Jacobi: shifts on the spectrum of diag(A)^{-1} A; natural-norm rtol
-        interval = W.jacobi_shift_interval(op) if "precond" in kw else c["interval"]
+        interval = est["jacobi" if "precond" in kw else "none"]["interval"]
         ts = []
         for _ in range(2):
             x = torch.zeros_like(b)
@@ -410,10 +422,10 @@ def other_configs(plcg, W, dev, hbm_peak):
     # forward weights per cell, no column indices), FP32, Jacobi
     c27 = W.config_hetero27_var27(nx=128)
     A = plcg.Matrix(c27["op"], prec="fp32")
-    interval = W.jacobi_shift_interval(op)
-    d = {"n": n, "bytes_per_row_operator": 14 * 4}
+    interval = est["jacobi"]["interval"]   # the same matrix as the CSR form
+    d = {"n": n, "bytes_per_row_operator": 14 * 4, "interval": interval}
     for name, kw in (("jacobi_plcg_l1", {"l": 1}), ("jacobi_plcg_l2", {"l": 2}),
-                     ("jacobi_classic_cg", {"method": "cg"})):
+                     ("jacobi_plcg_l3", {"l": 3}), ("jacobi_classic_cg", {"method": "cg"})):
         ts = []
         for _ in range(2):
             x = torch.zeros_like(b)

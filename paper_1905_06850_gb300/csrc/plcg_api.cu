@@ -505,6 +505,9 @@ static plcg_status build_solve(const plcg_matrix *A, const double *b, double *x,
     // that latency is a visible share of an iteration (smaller systems)
     a.lookahead = (!cg && l >= 2 && n < (int64_t(1) << 22)) ? 1 : 0;
     a.dsmem = dsmem;
+    // staging a warp's CSR entries pays when rows are long; short rows (the
+    // diagonal toy has one entry) read them directly (measured)
+    a.stage = (op_is_csr(op) && A->nnz >= 4 * n) ? 1 : 0;
     return PLCG_OK;
 }
 

@@ -115,6 +115,7 @@ struct SolveArgs {
     int lookahead;            // l >= 2: compute the next iteration's scalars during the sweep
     unsigned dsmem;           // dynamic shared memory of the launch (CSR / 27-point staging)
     const char *ws_lo, *ws_hi;   // the solve's workspace (bounds for staged copies)
+    int stage;                // CSR kernels: stage each unit's entries (rows long enough to pay)
     double *trace;            // CG: alpha_k, beta_k of the first segment (spectrum estimates), or null
     int trace_cap;            // pairs trace can hold
 };

@@ -1453,7 +1453,8 @@ __device__ void plcg_body(const SolveArgs<T> &a, Smem<T> &s, Grp &grp)
                     int64_t e0s = 0;
                     if constexpr (kStage) {   // this warp's 32 rows of the unit
                         const uint32_t w0 = u * usw + (uint32_t)(tid & ~31);
-                        stg = stage.stage(csr, w0, min(w0 + 32u, nn), &e0s, a.poll_limit, &a.out->abort);
+                        if (a.stage)
+                            stg = stage.stage(csr, w0, min(w0 + 32u, nn), &e0s, a.poll_limit, &a.out->abort);
                     }
                     if constexpr (kTile) {    // the unit's coefficients and z^(l)_i lines
                         const char *clo = static_cast<const char *>(csr.val);
@@ -1762,7 +1763,8 @@ __device__ void cg_body(const SolveArgs<T> &a, Smem<T> &s, Grp &grp)
                 int64_t e0s = 0;
                 if constexpr (kStage) {   // this warp's 32 rows of the unit
                     const uint32_t w0 = u * USWEEP + (uint32_t)(tid & ~31);
-                    stg = stage.stage(csr, w0, min(w0 + 32u, nn), &e0s, a.poll_limit, &a.out->abort);
+                    if (a.stage)
+                        stg = stage.stage(csr, w0, min(w0 + 32u, nn), &e0s, a.poll_limit, &a.out->abort);
                 }
 #pragma unroll
                 for (int r = 0; r < RPT; ++r) {
