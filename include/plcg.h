@@ -170,8 +170,8 @@ plcg_status plcg_create_csr(int64_t n, int64_t nnz, const int64_t *rowptr,
 plcg_status plcg_create_var27(int64_t nx, int64_t ny, int64_t nz, const double *coef,
                               int on_device, int prec, void *stream, plcg_matrix **out);
 
-/* Estimate the spectrum interval the Chebyshev shifts need (Sec. 2.2: the
- * extreme eigenvalues "can be estimated a priori"): `steps` iterations of
+/* Estimate the spectrum interval the Chebyshev shifts need (Sec. 2.2 suggests
+ * estimating the extreme eigenvalues beforehand): `steps` iterations of
  * classic CG on the GPU (prm->prec and prm->precond: the operator is A, or
  * diag(A)^{-1} A with PLCG_PRECOND_JACOBI) from a fixed pseudo-random
  * right-hand side, whose coefficients give the Lanczos tridiagonal matrix;
