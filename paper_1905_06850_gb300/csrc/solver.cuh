@@ -143,16 +143,47 @@ __device__ __forceinline__ bool mbar_wait(uint64_t *bar, uint32_t parity, unsign
 // ------------------------------------------------------------------------
 // Reductions (fixed order, so every CTA gets the same bits).
 // ------------------------------------------------------------------------
+// A warp instruction on GB300's FP64 units occupies them for ~16 cycles, so
+// the warp stage is a reduce-scatter butterfly: with NP = ND rounded up to a
+// power of two, step j exchanges half of each lane's NP >> j remaining sums
+// with lane ^ (16 >> j) and adds the other half, until every lane holds one
+// sum; plain butterfly steps finish.  NP - 1 + 5 - log2(NP) FP64 adds per
+// lane instead of 5 ND.  Dot q ends in lane q << (5 - log2(NP)).
+template <int ND>
+__device__ __forceinline__ double warp_reduce_scatter(const double (&v)[ND], int lane)
+{
+    constexpr int P = ND <= 1 ? 0 : ND <= 2 ? 1 : ND <= 4 ? 2 : ND <= 8 ? 3 : ND <= 16 ? 4 : 5;
+    constexpr int NP = 1 << P;
+    double w[NP];
+#pragma unroll
+    for (int q = 0; q < NP; ++q) w[q] = q < ND ? v[q] : 0.0;
+#pragma unroll
+    for (int j = 0; j < P; ++j) {
+        const int o = 16 >> j;
+        const int half = NP >> (j + 1);
+        const bool upper = (lane & o) != 0;   // keep the upper half of the remaining sums
+#pragma unroll
+        for (int q = 0; q < half; ++q) {
+            const double send = upper ? w[q] : w[q + half];
+            const double keep = upper ? w[q + half] : w[q];
+            w[q] = keep + __shfl_xor_sync(0xffffffffu, send, o);
+        }
+    }
+    double t = w[0];
+#pragma unroll
+    for (int o = 16 >> P; o > 0; o >>= 1) t += __shfl_xor_sync(0xffffffffu, t, o);
+    return t;
+}
+
 template <int ND>
 __device__ __forceinline__ void block_sum(double (&v)[ND], double *s_red, double *s_out)
 {
+    constexpr int P = ND <= 1 ? 0 : ND <= 2 ? 1 : ND <= 4 ? 2 : ND <= 8 ? 3 : ND <= 16 ? 4 : 5;
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-#pragma unroll
-    for (int q = 0; q < ND; ++q) {
-        double t = v[q];
-#pragma unroll
-        for (int o = 16; o > 0; o >>= 1) t += __shfl_down_sync(0xffffffffu, t, o);
-        if (lane == 0) s_red[warp * ND + q] = t;
+    const double t = warp_reduce_scatter<ND>(v, lane);
+    if ((lane & ((32 >> P) - 1)) == 0) {
+        const int q = lane >> (5 - P);
+        if (q < ND) s_red[warp * ND + q] = t;
     }
     __syncthreads();
     if (threadIdx.x < ND) {
@@ -1598,7 +1629,17 @@ __device__ void plcg_body(const SolveArgs<T> &a, Smem<T> &s, Grp &grp)
             }
             spmvs++;
             // MPI_Iallreduce(..., req(i)): publish this CTA's partials in slot i mod (l+1)
-            block_sum<2 * L + 1>(acc, s.red, s.out);
+            if (a.dots_2l1) {
+                block_sum<2 * L + 1>(acc, s.red, s.out);
+            } else {
+                // the l+1 dots of Sec. 2.2 (positions l .. 2l); the others are
+                // filled from the symmetry of G when the column is finalised
+                double sub[L + 1];
+#pragma unroll
+                for (int q = 0; q <= L; ++q) sub[q] = acc[L + q];
+                block_sum<L + 1>(sub, s.red, s.out + L);
+                if (tid < L) s.out[tid] = 0.0;
+            }
             grp.put_dots(a, s, (int)(i % (L + 1)), 2 * L + 1);
             PLCG_SYNC();
             if (!la) {   // MPI_Wait(req(i+1-l)) and the scalar step, serially (warp 0)
