@@ -1137,11 +1137,13 @@ __device__ __forceinline__ void scalar_step(Smem<T> &s, Coef<T> &cf, const doubl
 // compensated dot product Dot2 of Ogita, Rump & Oishi, "Accurate sum and dot
 // product", SIAM J. Sci. Comput. 26(6), 2005 -- Dekker's TwoProduct (via FMA)
 // per term and Knuth's TwoSum into a running FP32 pair (s, t) -- flushed
-// into the FP64 sum every kFlushUnits units, so a pair never covers more than
-// kFlushUnits * VEC terms (error O(eps_32^2) of the sum of |terms| per flush)
-// and the FP64 pipe (a small fraction of the FP32 rate on GB300) sees two
-// conversions and two adds per flush instead of three operations per term.
-constexpr int kFlushUnits = 4;
+// into the FP64 sum every kFlushUnits units.  A pair then covers at most
+// kFlushUnits * VEC * RPT <= 512 terms, whose error bound (Ogita et al.,
+// Thm. 5.3) is eps_32 |sum| + gamma_n^2 sum |terms| with gamma_512^2 < 1e-8:
+// below the rounding of the FP32 vectors themselves.  A flush is two
+// conversions and two adds on GB300's FP64 units, where a warp instruction
+// occupies them for ~16 cycles, so flushes are kept rare.
+constexpr int kFlushUnits = 32;
 
 template <typename T, int VEC>
 struct DotAcc {
@@ -1614,7 +1616,8 @@ __device__ void plcg_body(const SolveArgs<T> &a, Smem<T> &s, Grp &grp)
                     }
                     if (++since_flush == kFlushUnits) {
 #pragma unroll
-                        for (int q = 0; q <= 2 * L; ++q) dac[q].flush();
+                        for (int q = 0; q <= 2 * L; ++q)
+                            if (!S || steady_dot_src<L>(q) != 0) dac[q].flush();   // dots in use
                         since_flush = 0;
                     }
                 }
@@ -1624,7 +1627,7 @@ __device__ void plcg_body(const SolveArgs<T> &a, Smem<T> &s, Grp &grp)
             double acc[2 * L + 1];
 #pragma unroll
             for (int q = 0; q <= 2 * L; ++q) {
-                dac[q].flush();
+                if (q >= L || a.dots_2l1) dac[q].flush();   // positions < l: only with 2l+1 dots
                 acc[q] = dac[q].acc;
             }
             spmvs++;
