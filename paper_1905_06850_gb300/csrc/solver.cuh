@@ -222,28 +222,41 @@ __device__ __forceinline__ void grid_partials_sum(const double *part, int stride
     partials_sum<ND>(part, (int)gridDim.x, stride, s_red, s_out);
 }
 
-// One warp: sum over `count` CTAs of part[c * stride + q], q < ND, in a fixed
-// order; lane 0 writes dst[q] (shared memory), then the warp syncs.
-template <int ND>
+// One warp: sum over `count` CTAs of part[c * stride + q] for Q0 <= q < ND
+// in a fixed order (lane-strided partial sums, then the reduce-scatter
+// butterfly); dst[q] (shared memory) gets the sums, 0 for q < Q0; then the
+// warp syncs.
+template <int ND, int Q0 = 0>
 __device__ __forceinline__ void warp_partials_sum(const double *part, int count, int stride,
                                                   double *dst)
 {
+    constexpr int NA = ND - Q0;
+    constexpr int P = NA <= 1 ? 0 : NA <= 2 ? 1 : NA <= 4 ? 2 : NA <= 8 ? 3 : NA <= 16 ? 4 : 5;
     const int lane = threadIdx.x & 31;
-    double v[ND];
+    double v[NA];
 #pragma unroll
-    for (int q = 0; q < ND; ++q) v[q] = 0.0;
+    for (int q = 0; q < NA; ++q) v[q] = 0.0;
     for (int c = lane; c < count; c += 32) {
 #pragma unroll
-        for (int q = 0; q < ND; ++q) v[q] += __ldcg(part + (size_t)c * stride + q);
+        for (int q = 0; q < NA; ++q) v[q] += __ldcg(part + (size_t)c * stride + Q0 + q);
     }
-#pragma unroll
-    for (int q = 0; q < ND; ++q) {
-        double t = v[q];
-#pragma unroll
-        for (int o = 16; o > 0; o >>= 1) t += __shfl_down_sync(0xffffffffu, t, o);
-        if (lane == 0) dst[q] = t;
+    const double t = warp_reduce_scatter<NA>(v, lane);
+    if ((lane & ((32 >> P) - 1)) == 0) {
+        const int q = lane >> (5 - P);
+        if (q < NA) dst[Q0 + q] = t;
     }
+    if (lane < Q0) dst[lane] = 0.0;
     __syncwarp();
+}
+
+// The dots of the partial ring a scalar step needs: all 2l+1 positions with
+// the 2l+1-dot variant, positions l .. 2l with the l+1 dots of Sec. 2.2.
+template <int ND>
+__device__ __forceinline__ void warp_dots_sum(const double *part, int count, int stride, bool all,
+                                              double *dst)
+{
+    if (all) warp_partials_sum<ND, 0>(part, count, stride, dst);
+    else warp_partials_sum<ND, (ND - 1) / 2>(part, count, stride, dst);
 }
 
 // ------------------------------------------------------------------------
@@ -808,7 +821,11 @@ struct GridGroup {
     template <int ND>
     __device__ __forceinline__ void get_dots(const SolveArgs<T> &a, Smem<T> &s, int slot, double *dst)
     {
-        grid_partials_sum<ND>(a.part + (size_t)slot * gridDim.x * kMaxDots, kMaxDots, s.red, dst);
+        // warp 0 sums (few FP64 instructions: GB300's FP64 units are narrow),
+        // the CTA barrier publishes the result
+        if (threadIdx.x < 32)
+            warp_partials_sum<ND>(a.part + (size_t)slot * gridDim.x * kMaxDots, (int)gridDim.x, kMaxDots, dst);
+        __syncthreads();
     }
     // one warp sums ring slot `slot` over the CTAs into dst (every CTA's warp
     // adds in the same order, so all CTAs get the same bits)
@@ -816,7 +833,8 @@ struct GridGroup {
     __device__ __forceinline__ void get_dots_warp(const SolveArgs<T> &a, Smem<T> &, int slot,
                                                   double *dst)
     {
-        warp_partials_sum<ND>(a.part + (size_t)slot * gridDim.x * kMaxDots, (int)gridDim.x, kMaxDots, dst);
+        warp_dots_sum<ND>(a.part + (size_t)slot * gridDim.x * kMaxDots, (int)gridDim.x, kMaxDots,
+                          a.dots_2l1 != 0, dst);
     }
     __device__ __forceinline__ void put_norms(const SolveArgs<T> &a, Smem<T> &s)
     {
@@ -897,13 +915,14 @@ struct GangGroup {
     template <int ND>
     __device__ __forceinline__ void get_dots(const SolveArgs<T> &, Smem<T> &s, int slot, double *dst)
     {
-        partials_sum<ND>(part + (size_t)slot * G * kMaxDots, G, kMaxDots, s.red, dst);
+        if (threadIdx.x < 32) warp_partials_sum<ND>(part + (size_t)slot * G * kMaxDots, G, kMaxDots, dst);
+        __syncthreads();
     }
     template <int ND>
-    __device__ __forceinline__ void get_dots_warp(const SolveArgs<T> &, Smem<T> &, int slot,
+    __device__ __forceinline__ void get_dots_warp(const SolveArgs<T> &a, Smem<T> &, int slot,
                                                   double *dst)
     {
-        warp_partials_sum<ND>(part + (size_t)slot * G * kMaxDots, G, kMaxDots, dst);
+        warp_dots_sum<ND>(part + (size_t)slot * G * kMaxDots, G, kMaxDots, a.dots_2l1 != 0, dst);
     }
     __device__ __forceinline__ void put_norms(const SolveArgs<T> &, Smem<T> &s)
     {
