@@ -130,4 +130,32 @@ cudaError_t launch_var27_jacobi_setup(bool f32, const void *coef, int64_t n, dou
     return cudaGetLastError();
 }
 
+// Zero the forward coefficient coef[1+k][c] of every cell c whose neighbour
+// c + d_k lies outside the grid (such entries do not act: Dirichlet).
+template <typename V>
+__global__ void var27_zero_outside_kernel(V *val, int64_t cstride, StencilDesc st)
+{
+    const int64_t nx = st.nx, ny = st.ny, nz = st.nz, n = nx * ny * nz;
+    for (int64_t c = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; c < n;
+         c += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t x = c % nx, y = (c / nx) % ny, z = c / (nx * ny);
+        for (int k = 0; k < 13; ++k) {
+            const int64_t xn = x + v27_dx(k), yn = y + v27_dy(k), zn = z + v27_dz(k);
+            if (xn < 0 || xn >= nx || yn < 0 || yn >= ny || zn >= nz) val[(1 + k) * cstride + c] = V(0);
+        }
+    }
+}
+
+cudaError_t launch_var27_zero_outside(bool f32, void *val, int64_t cstride, const StencilDesc &st, cudaStream_t s)
+{
+    const int64_t n = (int64_t)st.nx * st.ny * st.nz;
+    const int64_t blocks = (n + 255) / 256;
+    const unsigned g = (unsigned)(blocks < 65535 ? (blocks > 0 ? blocks : 1) : 65535);
+    if (f32)
+        var27_zero_outside_kernel<float><<<g, 256, 0, s>>>(static_cast<float *>(val), cstride, st);
+    else
+        var27_zero_outside_kernel<double><<<g, 256, 0, s>>>(static_cast<double *>(val), cstride, st);
+    return cudaGetLastError();
+}
+
 }  // namespace plcg

@@ -69,6 +69,8 @@ struct Workspace {
     size_t bytes = 0;
 };
 
+static inline size_t align_up(size_t v, size_t a) { return (v + a - 1) / a * a; }
+
 struct plcg_matrix {
     int kind = kOpStencil;
     int64_t n = 0;
@@ -79,6 +81,8 @@ struct plcg_matrix {
     int32_t *col = nullptr;
     void *val = nullptr;         // CSR values; structured 27-point: [14][cstride] coefficients
     int64_t cstride = 0;
+    void *val_alloc = nullptr;   // structured 27-point: the allocation val points into
+    size_t val_bytes = 0;        // ... and its size
     // Jacobi data (CSR): 1 / a_rr in FP64, 1 / a_rr and a_rr in the stored type
     double *jdinv64 = nullptr;
     void *jdinv = nullptr;
@@ -275,13 +279,16 @@ extern "C" plcg_status plcg_create_var27(int64_t nx, int64_t ny, int64_t nz, con
     const cudaMemcpyKind kind = on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice;
     const size_t vsz = (prec == PLCG_FP64) ? sizeof(double) : sizeof(float);
     const size_t cnt = (size_t)14 * n;
-    // the 14 arrays start on 256-byte boundaries (stride rounded up to 64
-    // elements) and the allocation carries 64 elements of zeroed padding, so
-    // the staged sweep can copy 16-byte-rounded segments
-    A->cstride = (n + 63) / 64 * 64;
-    const size_t alloc = ((size_t)14 * A->cstride + 64) * vsz;
-    cudaError_t e = cudaMalloc(&A->val, alloc);
-    if (e == cudaSuccess) e = cudaMemset(A->val, 0, alloc);
+    // the 14 arrays start on 256-byte boundaries, with v27_halo(nx, ny) zero
+    // elements before the first and at least as many after each (the stride
+    // is n rounded up to 64 elements plus the halo), so the staged sweep's
+    // 16-byte-rounded copies of backward coefficients stay inside zeros
+    const int64_t halo = v27_halo(nx, ny);
+    A->cstride = (n + 63) / 64 * 64 + halo;
+    A->val_bytes = ((size_t)halo + (size_t)14 * A->cstride + 64) * vsz;
+    cudaError_t e = cudaMalloc(&A->val_alloc, A->val_bytes);
+    if (e == cudaSuccess) e = cudaMemset(A->val_alloc, 0, A->val_bytes);
+    A->val = static_cast<char *>(A->val_alloc) + halo * vsz;
     if (e == cudaSuccess) {
         if (prec == PLCG_FP64) {
             e = cudaMemcpy2D(A->val, A->cstride * sizeof(double), coef, n * sizeof(double),
@@ -301,13 +308,18 @@ extern "C" plcg_status plcg_create_var27(int64_t nx, int64_t ny, int64_t nz, con
             if (tmp) cudaFree(tmp);
         }
     }
+    // entries towards cells outside the grid are ignored: store them as zero,
+    // so that the tiled sweep applies every row without boundary tests
+    if (e == cudaSuccess) e = launch_var27_zero_outside(prec != PLCG_FP64, A->val, A->cstride, A->st, nullptr);
+    if (e == cudaSuccess) e = cudaDeviceSynchronize();
     // Jacobi data: the diagonal is coef[0]; its inverse is formed here
     int *bad = nullptr;
     A->jdiag = A->val;
     if (e == cudaSuccess) e = cudaMalloc(&A->jdinv64, n * sizeof(double));
     if (e == cudaSuccess) {
+        // padded to 256 bytes: the tiled sweep bulk-copies 16-byte groups
         if (prec == PLCG_FP64) A->jdinv = A->jdinv64;
-        else e = cudaMalloc(&A->jdinv, n * vsz);
+        else e = cudaMalloc(&A->jdinv, align_up(n * vsz, 256));
     }
     if (e == cudaSuccess) e = cudaMalloc(&bad, sizeof(int));
     if (e == cudaSuccess) e = cudaMemset(bad, 0, sizeof(int));
@@ -335,7 +347,7 @@ extern "C" void plcg_destroy(plcg_matrix *A)
     cudaFree(A->rowptr);
     cudaFree(A->col);
     if (A->jdiag != A->val) cudaFree(A->jdiag);
-    cudaFree(A->val);
+    cudaFree(A->val_alloc ? A->val_alloc : A->val);
     if (A->jdinv != A->jdinv64) cudaFree(A->jdinv);
     cudaFree(A->jdinv64);
     cudaFree(A->ws.mem);
@@ -385,7 +397,6 @@ static plcg_status ensure_ws(plcg_matrix *A, size_t bytes)
     return PLCG_OK;
 }
 
-static inline size_t align_up(size_t v, size_t a) { return (v + a - 1) / a * a; }
 
 // Layout of one solve's workspace and its kernel arguments.  With base ==
 // nullptr only the sizes are computed; *bytes is the workspace size and
@@ -413,7 +424,8 @@ static plcg_status build_solve(const plcg_matrix *A, const double *b, double *x,
     // classic CG excepted, see cg_body); the 27-point p(l)-CG kernels stage
     // coefficient and z tiles
     const unsigned dsmem = (op_is_csr(op) && (!cg || f32)) ? csr_stage_bytes((unsigned)sizeof(T))
-                         : (op_is_var27(op) && !cg && f32) ? v27_tile_bytes((unsigned)sizeof(T)) : 0u;
+                         : (op_is_var27(op) && !cg && f32)
+                             ? v27_tile_bytes((unsigned)sizeof(T), l, op_is_jacobi(op)) : 0u;
     if (dsmem) {
         CUDA_TRY(cudaFuncSetAttribute(func, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)dsmem));
         CUDA_TRY(cudaFuncSetAttribute(func, cudaFuncAttributePreferredSharedMemoryCarveout,
@@ -449,9 +461,14 @@ static plcg_status build_solve(const plcg_matrix *A, const double *b, double *x,
     // 128-bit access needs n * sizeof(T) to be a multiple of 16
     if (((size_t)n * sizeof(T)) % 16 != 0 && vec > 1)
         return fail(PLCG_ERR_INVALID, "internal: vector length not 16-byte aligned");
-    const size_t vbytes = align_up((size_t)n * sizeof(T), 256);
+    // structured 27-point operators: a zero halo before the first ring vector
+    // and at least one after every vector (the stride includes it), zeroed by
+    // the kernel at the start of each solve, so that the tiles' z-line copies
+    // stay inside the vector and zeros
+    const int64_t halo = op_is_var27(op) ? v27_halo(A->st.nx, A->st.ny) : 0;
+    const size_t vbytes = align_up((size_t)(n + halo) * sizeof(T), 256);
     size_t off = 0;
-    const size_t o_ring = off; off += vbytes * nvec;
+    const size_t o_ring = off; off += (size_t)halo * sizeof(T) + vbytes * nvec;
     const size_t o_p = off; off += vbytes;
     const size_t o_rc = off; off += vbytes;
     const size_t o_r = off; off += align_up((size_t)n * sizeof(double), 256);
@@ -475,6 +492,10 @@ static plcg_status build_solve(const plcg_matrix *A, const double *b, double *x,
     a.vstride = (int64_t)(vbytes / sizeof(T));   // ring vectors 256-byte aligned
     a.ws_lo = base;
     a.ws_hi = base + off;
+    if (A->val_alloc) {
+        a.cf_lo = static_cast<const char *>(A->val_alloc);
+        a.cf_hi = a.cf_lo + A->val_bytes;
+    }
     if (jac) {
         a.csr.dinv = A->jdinv;
         a.csr.diag = A->jdiag;
@@ -483,7 +504,9 @@ static plcg_status build_solve(const plcg_matrix *A, const double *b, double *x,
     a.b = b;
     a.x = x;
     a.r = reinterpret_cast<double *>(base + o_r);
-    a.zring = reinterpret_cast<T *>(base + o_ring);
+    a.zring = reinterpret_cast<T *>(base + o_ring + (size_t)halo * sizeof(T));
+    a.halo = halo;
+    a.nring = nvec;
     a.p = reinterpret_cast<T *>(base + o_p);
     a.rc = reinterpret_cast<T *>(base + o_rc);
     a.part = reinterpret_cast<double *>(base + o_part);

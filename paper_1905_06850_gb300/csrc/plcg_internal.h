@@ -115,6 +115,10 @@ struct SolveArgs {
     int lookahead;            // l >= 2: compute the next iteration's scalars during the sweep
     unsigned dsmem;           // dynamic shared memory of the launch (CSR / 27-point staging)
     const char *ws_lo, *ws_hi;   // the solve's workspace (bounds for staged copies)
+    const char *cf_lo, *cf_hi;   // structured 27-point: the coefficient allocation (same)
+    int64_t halo;             // structured 27-point: zero elements before ring vector 0 (and
+                              // at least as many after every ring vector)
+    int nring;                // ring vectors in zring
     int stage;                // CSR kernels: stage each unit's entries (rows long enough to pay)
     double *trace;            // CG: alpha_k, beta_k of the first segment (spectrum estimates), or null
     int trace_cap;            // pairs trace can hold
@@ -122,11 +126,35 @@ struct SolveArgs {
 
 // Structured 27-point tiles: per sweep unit, 36 shared-memory slots of
 // kV27Slot elements -- the diagonal and 13 forward coefficient segments, the
-// 13 backward segments, the 9 line segments of z around the unit.
+// 13 backward segments, the 9 line segments of z around the unit -- and, for
+// l <= 3, v27_vec_slots(l, jacobi) slots of the vector operands the
+// steady-state p(l)-CG sweep streams (z^(l)_{i-1}, the l current and l
+// previous z^(k), p, the iterate and, with Jacobi, 1/a_gg and a_gg).
+// kV27Buf buffers, each with its mbarrier: the unit being computed and the
+// next kV27Buf - 1 in flight.
 constexpr int kV27Slot = 256 + 16;
-constexpr unsigned v27_tile_bytes(unsigned value_bytes)
+constexpr int kV27Buf = 2;
+
+// The 13 forward offsets (dz, dy, dx) of the structured 27-point operator,
+// lexicographic (the order of its coefficient arrays 1..13).
+PLCG_HD constexpr int v27_dz(int k) { return k < 4 ? 0 : 1; }
+PLCG_HD constexpr int v27_dy(int k) { return k == 0 ? 0 : k < 4 ? 1 : k < 7 ? -1 : k < 10 ? 0 : 1; }
+PLCG_HD constexpr int v27_dx(int k) { return k == 0 ? 1 : k < 4 ? k - 2 : (k - 4) % 3 - 1; }
+
+// Zero elements kept before the structured 27-point operator's coefficient
+// arrays and its solves' ring vectors, and at least as many after each of
+// them: more than the largest offset nx*ny + nx + 1 plus the 16-byte rounding
+// of a staged copy, in whole 256-byte groups.  A tile's copies then never
+// leave an array and its zero margins.
+PLCG_HD constexpr int64_t v27_halo(int64_t nx, int64_t ny) { return (nx * ny + nx + 8 + 63) / 64 * 64; }
+constexpr int v27_vec_slots(int l, bool jacobi)
 {
-    return 16u + 36u * (unsigned)kV27Slot * value_bytes;
+    return l <= 3 ? 2 * l + 3 + (jacobi ? 2 : 0) : 0;
+}
+constexpr unsigned v27_tile_bytes(unsigned value_bytes, int l, bool jacobi)
+{
+    return 16u * ((kV27Buf + 1) / 2) +
+           (unsigned)kV27Buf * (36u + (unsigned)v27_vec_slots(l, jacobi)) * (unsigned)kV27Slot * value_bytes;
 }
 
 // CSR entries (column index + value) each warp of a CSR kernel stages in

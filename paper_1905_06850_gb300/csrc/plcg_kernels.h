@@ -51,6 +51,8 @@ cudaError_t launch_var27_jacobi_setup(bool f32, const void *coef, int64_t n, dou
 cudaError_t launch_fill_random(double *v, int64_t n, uint64_t seed, cudaStream_t s);
 
 // dst[i] = (float) src[i] on the device.
+cudaError_t launch_var27_zero_outside(bool f32, void *val, int64_t cstride, const StencilDesc &st,
+                                      cudaStream_t s);
 cudaError_t launch_round_to_f32(const double *src, float *dst, int64_t n, cudaStream_t s);
 
 }  // namespace plcg

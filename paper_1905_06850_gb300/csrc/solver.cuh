@@ -108,6 +108,14 @@ __device__ __forceinline__ void fence_proxy_async_smem()
     asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
 }
 
+// The same for every state space: also orders generic-proxy writes to global
+// memory that this thread has observed (another CTA's stores of the previous
+// iteration, acquired through the grid barrier) before its async-proxy reads.
+__device__ __forceinline__ void fence_proxy_async_all()
+{
+    asm volatile("fence.proxy.async;" ::: "memory");
+}
+
 __device__ __forceinline__ void mbar_arrive_expect_tx(uint64_t *bar, uint32_t bytes)
 {
     asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;"
@@ -408,18 +416,6 @@ __device__ __forceinline__ void stencil_apply(const StencilDesc &st, V cC, V cO,
     for (int v = 0; v < VEC; ++v) w[v] = fma(cO, nb[v], cC * c[v]);
 }
 
-// The 13 forward offsets (dz, dy, dx) of the structured 27-point operator,
-// lexicographic (the order of its coefficient arrays 1..13).
-__device__ __forceinline__ constexpr int v27_dz(int k) { return k < 4 ? 0 : 1; }
-__device__ __forceinline__ constexpr int v27_dy(int k)
-{
-    return k == 0 ? 0 : k < 4 ? 1 : k < 7 ? -1 : k < 10 ? 0 : 1;
-}
-__device__ __forceinline__ constexpr int v27_dx(int k)
-{
-    return k == 0 ? 1 : k < 4 ? k - 2 : (k - 4) % 3 - 1;
-}
-
 // Row g of the structured symmetric 27-point operator (VEC = 1): the full
 // (A z)_g = a_gg z_g + sum over the 13 forward offsets d of
 // w_d(g) z_{g+d} + w_d(g-d) z_{g-d}, where w_d(c) = coef[1+k][c] is the
@@ -478,31 +474,40 @@ __device__ __forceinline__ V csr_row_staged(const CsrDesc &A, const int32_t *sco
     return s;
 }
 
-// Per-CTA tile of the structured 27-point operator for one sweep unit of
-// rows [r0, r1) (dynamic shared memory: an mbarrier, then 36 slots of
-// kV27Slot elements): slots 0..13 the diagonal and forward coefficients of
-// the unit's rows, 14..26 the backward coefficients (forward array k at rows
-// g - d_k), 27..35 the nine line segments of z around the unit ((dz, dy) in
-// {-1,0,1}^2, x - 1 .. x + 1).  One bulk copy per slot, each rounded out
-// to 16 bytes; the rounding puts element g of a slot at a
-// shift that is fixed for the whole solve (the arrays and ring vectors start
-// on 256-byte boundaries and units on multiples of 4 rows), so the shifts are
-// computed once.  A unit whose copies would leave the arrays' allocations
-// falls back to global loads.
-template <typename T>
+// Per-CTA tiles of the structured 27-point operator, one per sweep unit of
+// rows [r0, r1) (dynamic shared memory: kV27Buf mbarriers in 16-byte pairs,
+// then kV27Buf buffers of 36 + NV slots of kV27Slot elements): slots 0..13 the diagonal and forward
+// coefficients of the unit's rows, 14..26 the backward coefficients (forward
+// array k at rows g - d_k), 27..35 the nine line segments of z around the
+// unit ((dz, dy) in {-1,0,1}^2, x - 1 .. x + 1), 36.. the unit's rows of NV
+// vector operands (the steady-state sweep's; other sweeps load those from
+// global memory).  One bulk copy per slot, each rounded out to 16 bytes; the
+// rounding puts element g of an operator slot at a shift that is fixed for
+// the whole solve (the arrays and ring vectors start on 256-byte boundaries
+// and units on multiples of 4 rows), so the shifts are computed once; vector
+// slots start at their first row.  The sweep keeps the next kV27Buf - 1
+// units' copies in flight while it computes from the current buffer.  A unit whose
+// operator copies would leave the arrays' allocations falls back to global
+// loads (vectors and the inverse diagonal are padded to 256 bytes, so their
+// rounded copies always stay inside).
+template <typename T, int NV>
 struct Var27Tile {
     static constexpr int A = 16 / (int)sizeof(T);   // elements per 16 bytes
-    uint64_t *bar;
-    T *slot;
-    uint32_t parity = 0;
-    uint32_t shb = 0, shz = 0;   // 2-bit shifts of the backward and z slots
+    static constexpr int kSlots = 36 + NV;
+    static constexpr int kBuf = kSlots * kV27Slot;   // elements per buffer
+    static constexpr int kHdr = 16 * ((kV27Buf + 1) / 2);
+    uint64_t *bar;                                   // bar[0 .. kV27Buf-1]
+    T *slot0;
+    uint32_t parity = 0;          // bit b: the phase buffer b waits for next
+    uint32_t shb = 0, shz = 0;    // 2-bit shifts of the backward and z slots
     __device__ __forceinline__ explicit Var27Tile(unsigned char *dsm)
-        : bar(reinterpret_cast<uint64_t *>(dsm)), slot(reinterpret_cast<T *>(dsm + 16))
+        : bar(reinterpret_cast<uint64_t *>(dsm)), slot0(reinterpret_cast<T *>(dsm + kHdr))
     {
     }
     __device__ __forceinline__ void init(const StencilDesc &st)
     {
-        if (threadIdx.x == 0) mbar_init(bar, 36);
+        if (threadIdx.x == 0)
+            for (int b = 0; b < kV27Buf; ++b) mbar_init(bar + b, kSlots);
         const int nx = st.nx, nxy = st.nx * st.ny;
         for (int k = 0; k < 13; ++k) {
             const int off = v27_dz(k) * nxy + v27_dy(k) * nx + v27_dx(k);
@@ -515,22 +520,35 @@ struct Var27Tile {
     }
     __device__ __forceinline__ int sb(int k) const { return (int)((shb >> (2 * k)) & 3u); }
     __device__ __forceinline__ int sz(int q) const { return (int)((shz >> (2 * q)) & 3u); }
-    // Stage rows [r0, r1).  Threads 0..35 each own one slot: they check that
+    // Vector slot j of buffer buf (element t = row r0 + t).
+    __device__ __forceinline__ const T *vec(int buf, int j) const
+    {
+        return slot0 + buf * kBuf + (36 + j) * kV27Slot;
+    }
+    // Start staging rows [r0, r1) in buffer buf (`want` false: nothing to
+    // stage, the barrier alone; `vecs`: also the vector slots, vsrc(j) giving
+    // vector j).  Threads 0..35 each own one operator slot: they check that
     // their 16-byte-rounded range stays inside its allocation ([clo, chi) for
     // coefficients, [zlo, zhi) for z), the first `nthreads` threads agree on
-    // the result with a barrier reduction (which also orders every read of the
-    // previous unit's tile before the new copies), and the owners issue their
-    // copies, each arriving on the mbarrier (init count 36) with its bytes.
-    // Returns false when the unit is to be read from global memory.
-    __device__ __forceinline__ bool stage(const StencilDesc &st, const T *coef, int64_t cstride,
-                                          const char *clo, const char *chi, const T *z,
-                                          const char *zlo, const char *zhi, uint32_t r0, uint32_t r1,
-                                          int nthreads, unsigned long long limit, int *abort_flag)
+    // the result with a barrier reduction (which also orders every read of
+    // the buffer's previous unit before the new copies: those reads have
+    // completed into registers, and the async-proxy writes follow the
+    // barrier), and threads
+    // 0..kSlots-1 issue their copies, each arriving on the buffer's mbarrier
+    // (init count kSlots) with its bytes.  Returns false when the unit is to
+    // be read from global memory; otherwise every thread calls wait() before
+    // reading the tile.
+    template <class VSrc>
+    __device__ __forceinline__ bool issue(int buf, bool want, bool vecs, const VSrc &vsrc, const StencilDesc &st,
+                                          const T *coef, int64_t cstride, const char *clo, const char *chi,
+                                          const T *z, const char *zlo, const char *zhi, uint32_t r0,
+                                          uint32_t r1, int nthreads)
     {
         const int sl = threadIdx.x;
         uintptr_t b0 = 0, b1 = 0;
         int ok = 1;
-        if (sl < 36) {
+        if (sl < 36 && !want) ok = 0;
+        if (sl < 36 && want) {
             const int64_t nx = st.nx, nxy = (int64_t)st.nx * st.ny;
             const T *base;
             int64_t lo, hi;
@@ -542,9 +560,8 @@ struct Var27Tile {
                 const int k = sl - 14;
                 const int64_t off = v27_dz(k) * nxy + v27_dy(k) * nx + v27_dx(k);
                 base = coef + (1 + k) * cstride;
-                lo = (int64_t)r0 - off;
+                lo = (int64_t)r0 - off;   // may start in the zero halo before the arrays
                 hi = (int64_t)r1 - off;
-                if (hi <= 0) lo = hi = 0;   // no row of the unit has this backward neighbour
             } else {
                 const int q = sl - 27;
                 const int64_t d = (q / 3 - 1) * nxy + (q % 3 - 1) * nx;
@@ -559,6 +576,10 @@ struct Var27Tile {
                 ok = b0 >= reinterpret_cast<uintptr_t>(mlo) && b1 <= reinterpret_cast<uintptr_t>(mhi) &&
                      b1 - b0 <= (uintptr_t)(kV27Slot * sizeof(T));
             }
+        } else if (NV > 0 && sl >= 36 && sl < kSlots && want && vecs) {
+            const T *base = vsrc(sl - 36);
+            b0 = reinterpret_cast<uintptr_t>(base + r0);
+            b1 = (reinterpret_cast<uintptr_t>(base + r1) + 15) & ~uintptr_t(15);
         }
         int all;
         asm volatile("{\n\t.reg .pred p, q;\n\t"
@@ -567,29 +588,34 @@ struct Var27Tile {
                      "selp.s32 %0, 1, 0, q;\n\t}"
                      : "=r"(all) : "r"(ok), "r"(nthreads) : "memory");
         if (!all) return false;
-        if (sl < 36) {
-            fence_proxy_async_smem();
+        if (sl < kSlots) {
             const uint32_t bytes = (uint32_t)(b1 - b0);
-            mbar_arrive_expect_tx(bar, bytes);
-            if (bytes) bulk_copy_g2s(slot + sl * kV27Slot, reinterpret_cast<const void *>(b0), bytes, bar);
+            mbar_arrive_expect_tx(bar + buf, bytes);
+            if (bytes)
+                bulk_copy_g2s(slot0 + buf * kBuf + sl * kV27Slot, reinterpret_cast<const void *>(b0), bytes,
+                              bar + buf);
         }
-        if (!mbar_wait(bar, parity, limit)) {
-            atomicExch(abort_flag, 1);
-            mbar_wait(bar, parity, limit);
-        }
-        parity ^= 1u;
         return true;
     }
-    // (A z)_g for row g = r0 + t of the staged unit (z's centre value in *zc).
-    template <typename V>
-    __device__ __forceinline__ V row(const StencilDesc &st, uint32_t g, int t, V *zc) const
+    // Wait for the copies issue() started (bounded: on timeout the abort flag
+    // is raised and the wait repeated once, so no copy is left in flight).
+    __device__ __forceinline__ void wait(int buf, unsigned long long limit, int *abort_flag)
     {
-        const uint32_t nx = (uint32_t)st.nx, ny = (uint32_t)st.ny, nz = (uint32_t)st.nz;
-        const uint32_t line = (__umulhi(g, st.dnx.m) + g) >> st.dnx.s;
-        const uint32_t x = g - line * nx;
-        const uint32_t zz = (__umulhi(line, st.dny.m) + line) >> st.dny.s;
-        const uint32_t y = line - zz * ny;
-        const bool xm = x > 0, xp = x + 1 < nx, ym = y > 0, yp = y + 1 < ny, zm = zz > 0, zp = zz + 1 < nz;
+        const uint32_t ph = (parity >> buf) & 1u;
+        if (!mbar_wait(bar + buf, ph, limit)) {
+            atomicExch(abort_flag, 1);
+            mbar_wait(bar + buf, ph, limit);
+        }
+        parity ^= 1u << buf;
+    }
+    // (A z)_g for row g = r0 + t of the unit staged in buffer buf (z's centre
+    // value in *zc).  No boundary tests: entries towards cells outside the
+    // grid are stored as zero and every z value a copy brings in is finite
+    // (z itself, or the zero halos around the ring vectors).
+    template <typename V>
+    __device__ __forceinline__ V row(int buf, int t, V *zc) const
+    {
+        const T *slot = slot0 + buf * kBuf;
         const T *zs = slot + 27 * kV27Slot;
         auto zat = [&](int dz, int dy, int dx) -> V {
             const int q = (dz + 1) * 3 + (dy + 1);
@@ -601,12 +627,8 @@ struct Var27Tile {
 #pragma unroll
         for (int k = 0; k < 13; ++k) {
             const int dz = v27_dz(k), dy = v27_dy(k), dx = v27_dx(k);
-            const bool fwd = (dx > 0 ? xp : dx < 0 ? xm : true) && (dy > 0 ? yp : dy < 0 ? ym : true) &&
-                             (dz > 0 ? zp : true);
-            const bool bwd = (dx > 0 ? xm : dx < 0 ? xp : true) && (dy > 0 ? ym : dy < 0 ? yp : true) &&
-                             (dz > 0 ? zm : true);
-            if (fwd) s = fma((V)slot[(1 + k) * kV27Slot + t], zat(dz, dy, dx), s);
-            if (bwd) s = fma((V)slot[(14 + k) * kV27Slot + t + sb(k)], zat(-dz, -dy, -dx), s);
+            s = fma((V)slot[(1 + k) * kV27Slot + t], zat(dz, dy, dx), s);
+            s = fma((V)slot[(14 + k) * kV27Slot + t + sb(k)], zat(-dz, -dy, -dx), s);
         }
         return s;
     }
@@ -1293,10 +1315,25 @@ __device__ void plcg_body(const SolveArgs<T> &a, Smem<T> &s, Grp &grp)
     // FP64 sweep is bound by the FP64 units and measured faster without)
     constexpr bool kTile = op_is_var27(OP) && std::is_same<Grp, GridGroup<T>>::value && RPT == 1 &&
                            sizeof(T) == 4;
-    Var27Tile<T> tile(plcg_dsm);
+    constexpr int kNV = kTile ? v27_vec_slots(L, op_is_jacobi(OP)) : 0;
+    Var27Tile<T, kNV> tile(plcg_dsm);
     if constexpr (kTile) {
         tile.init(a.st);
         __syncthreads();
+        // zero the halo before ring vector 0 and the span after every ring
+        // vector (rows n .. vstride-1): the tiles' z-line copies reach into
+        // them and multiply what they find by zero coefficients (the grid
+        // barrier after the first residual sweep orders these stores before
+        // any copy)
+        const int64_t span = a.vstride - a.n, nz = a.halo + (int64_t)a.nring * span;
+        for (int64_t e = (int64_t)blockIdx.x * kBlock + threadIdx.x; e < nz; e += (int64_t)gridDim.x * kBlock) {
+            if (e < a.halo) {
+                a.zring[e - a.halo] = T(0);
+            } else {
+                const int64_t i = (e - a.halo) / span;
+                a.zring[i * a.vstride + a.n + (e - a.halo - i * span)] = T(0);
+            }
+        }
     }
     const int64_t n = a.n;
     const int64_t nunits = (n + UNIT - 1) / UNIT;
@@ -1493,6 +1530,41 @@ __device__ void plcg_body(const SolveArgs<T> &a, Smem<T> &s, Grp &grp)
                 const int k6 = S ? 2 : C.k6;
                 const bool prev0 = S || C.prev0;
                 int since_flush = 0;
+                // 27-point tiles: the first unit's copies start here, each
+                // following unit's at the top of the one before it
+                const char *tclo = a.cf_lo, *tchi = a.cf_hi;
+                int tb = 0;             // buffer of the current unit
+                uint32_t stg_q = 0;     // bit b: buffer b's unit is staged (copies in flight or landed)
+                // the steady sweep's vector operands ride along in the tile
+                constexpr bool SV = S && kNV > 0;
+                auto vsrc = [&](int j) -> const T * {
+                    if (j == 0) return C.zl_prev;
+                    if (j <= L) return C.cur[j - 1];
+                    if (j <= 2 * L) return C.prv[j - 1 - L];
+                    if (j == 2 * L + 1) return pvec;
+                    if (j == 2 * L + 2) return xi;
+                    if (j == 2 * L + 3) return static_cast<const T *>(csr.dinv);
+                    return static_cast<const T *>(csr.diag);
+                };
+                // stage unit uu (if it exists) in buffer bb
+                auto tile_issue = [&](int bb, uint32_t uu) {
+                    const bool more = uu < nunits_s;
+                    const bool on = tile.issue(bb, more, SV, vsrc, st, static_cast<const T *>(csr.val), csr.stride,
+                                               tclo, tchi, C.zl_cur, a.ws_lo, a.ws_hi, more ? uu * usw : 0u,
+                                               more ? min(uu * usw + usw, nn) : 0u, nsw);
+                    stg_q = (stg_q & ~(1u << bb)) | ((on ? 1u : 0u) << bb);
+                };
+                if constexpr (kTile) {   // the first kV27Buf - 1 units
+                    // z^(l)_i and the vectors were written by generic stores
+                    // before the grid barrier that began this sweep; nothing
+                    // the copies read is written during it.  One proxy fence
+                    // per issuing thread orders those stores before all of
+                    // the sweep's copies.
+                    if (tid < Var27Tile<T, kNV>::kSlots) fence_proxy_async_all();
+                    if ((uint32_t)grp.unit0() < nunits_s)
+                        for (int bb = 0; bb < kV27Buf - 1; ++bb)
+                            tile_issue(bb, (uint32_t)grp.unit0() + (uint32_t)bb * (uint32_t)grp.ustep());
+                }
                 for (uint32_t u = (uint32_t)grp.unit0(); u < nunits_s; u += (uint32_t)grp.ustep()) {
                     uint32_t g0[RPT];
                     bool ok[RPT];
@@ -1508,12 +1580,11 @@ __device__ void plcg_body(const SolveArgs<T> &a, Smem<T> &s, Grp &grp)
                         if (a.stage)
                             stg = stage.stage(csr, w0, min(w0 + 32u, nn), &e0s, a.poll_limit, &a.out->abort);
                     }
-                    if constexpr (kTile) {    // the unit's coefficients and z^(l)_i lines
-                        const char *clo = static_cast<const char *>(csr.val);
-                        const char *chi = clo + (14 * csr.stride + 64) * (int64_t)sizeof(T);
-                        stg = tile.stage(st, static_cast<const T *>(csr.val), csr.stride, clo, chi, C.zl_cur,
-                                         a.ws_lo, a.ws_hi, u * usw, min(u * usw + usw, nn), nsw,
-                                         a.poll_limit, &a.out->abort);
+                    if constexpr (kTile) {    // the copies kV27Buf - 1 units ahead; this unit's tile
+                        stg = (stg_q >> tb) & 1u;
+                        tile_issue((tb + kV27Buf - 1) % kV27Buf,
+                                   u + (uint32_t)(kV27Buf - 1) * (uint32_t)grp.ustep());
+                        if (stg) tile.wait(tb, a.poll_limit, &a.out->abort);
                     }
                     // -- loads
                     T c[RPT][VEC], nb[RPT][VEC], zp[RPT][VEC], cur[RPT][L][VEC], pk[RPT][L][VEC];
@@ -1533,17 +1604,32 @@ __device__ void plcg_body(const SolveArgs<T> &a, Smem<T> &s, Grp &grp)
                                 op_parts<T, T, VEC, OP>(st, csr, Ld1<T>{C.zl_cur}, g0[r], c[r], nb[r]);
                             }
                         } else if constexpr (kTile) {
-                            if (stg) {
-                                T zc;
-                                nb[r][0] = tile.template row<T>(st, g0[r], (int)(g0[r] - u * usw), &zc);
-                                c[r][0] = zc;
-                            } else {
-                                op_parts<T, T, VEC, OP>(st, csr, Ld1<T>{C.zl_cur}, g0[r], c[r], nb[r]);
-                            }
+                            // K1 from the tile after the loads below
                         } else {
                             op_parts<T, T, VEC, OP>(st, csr, Ld1<T>{C.zl_cur}, g0[r], c[r], nb[r]);
                         }
-                        if constexpr (op_is_jacobi(OP)) {
+                        if constexpr (kTile) {
+                            if (SV && stg) {   // the steady sweep's vectors, from the tile
+                                const int t = (int)(g0[r] - u * usw);
+                                zp[r][0] = tile.vec(tb, 0)[t];
+#pragma unroll
+                                for (int k = 0; k < L; ++k) {
+                                    cur[r][k][0] = tile.vec(tb, 1 + k)[t];
+                                    pk[r][k][0] = tile.vec(tb, 1 + L + k)[t];
+                                }
+                                pv[r][0] = tile.vec(tb, 2 * L + 1)[t];
+                                xv[r][0] = tile.vec(tb, 2 * L + 2)[t];
+                                if constexpr (op_is_jacobi(OP)) {
+                                    c[r][0] = tile.vec(tb, 2 * L + 3)[t];   // 1 / a_gg for now
+                                    dg[r] = tile.vec(tb, 2 * L + 4)[t];
+                                }
+                                continue;
+                            }
+                            if constexpr (op_is_jacobi(OP)) {
+                                c[r][0] = __ldg(static_cast<const T *>(csr.dinv) + g0[r]);   // 1 / a_gg for now
+                                dg[r] = __ldg(static_cast<const T *>(csr.diag) + g0[r]);
+                            }
+                        } else if constexpr (op_is_jacobi(OP)) {
                             // K1 with M = diag(A): z^(l)_{i+1} is built from M^{-1} A z^(l)_i
                             nb[r][0] *= __ldg(static_cast<const T *>(csr.dinv) + g0[r]);
                             dg[r] = __ldg(static_cast<const T *>(csr.diag) + g0[r]);
@@ -1565,6 +1651,21 @@ __device__ void plcg_body(const SolveArgs<T> &a, Smem<T> &s, Grp &grp)
                         if (k6 == 2) {
                             vld<T, VEC>(pvec + g0[r], pv[r]);
                             vld<T, VEC>(xi + g0[r], xv[r]);
+                        }
+                    }
+                    if constexpr (kTile) {   // K1 from the tile
+#pragma unroll
+                        for (int r = 0; r < RPT; ++r) {
+                            if (!ok[r]) continue;
+                            const T di = c[r][0];
+                            if (stg) {
+                                T zc;
+                                nb[r][0] = tile.template row<T>(tb, (int)(g0[r] - u * usw), &zc);
+                                c[r][0] = zc;
+                            } else {
+                                op_parts<T, T, VEC, OP>(st, csr, Ld1<T>{C.zl_cur}, g0[r], c[r], nb[r]);
+                            }
+                            if constexpr (op_is_jacobi(OP)) nb[r][0] *= di;
                         }
                     }
 #pragma unroll
@@ -1639,6 +1740,7 @@ __device__ void plcg_body(const SolveArgs<T> &a, Smem<T> &s, Grp &grp)
                             if (!S || steady_dot_src<L>(q) != 0) dac[q].flush();   // dots in use
                         since_flush = 0;
                     }
+                    tb = (tb + 1) % kV27Buf;
                 }
             };
             if (steady) sweep(std::true_type{});
@@ -1952,8 +2054,15 @@ finish:
 // Single-system kernels: the whole grid solves one system (cooperative
 // launch, so that every CTA is resident and the grid barrier can complete).
 // ------------------------------------------------------------------------
+// CTAs per SM the register budget is sized for: three for FP32 with l <= 2,
+// two otherwise; the 27-point tiles' buffers (about 47 KB each) leave room
+// for one CTA per SM with four of them (two with two).
+template <typename T, int L, int OP>
+constexpr int kPlcgMinBlocks = (sizeof(T) == 4 && op_is_var27(OP)) ? (kV27Buf > 2 ? 1 : 2)
+                             : (sizeof(T) == 4 && L <= 2) ? 3 : 2;
+
 template <typename T, int L, int VEC, int OP>
-__global__ void __launch_bounds__(kBlock, (sizeof(T) == 4 && L <= 2) ? 3 : 2)
+__global__ void __launch_bounds__(kBlock, (kPlcgMinBlocks<T, L, OP>))
 plcg_kernel(SolveArgs<T> a)
 {
     __shared__ Smem<T> s;
