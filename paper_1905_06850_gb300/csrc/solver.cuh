@@ -101,16 +101,9 @@ __device__ __forceinline__ void mbar_init(uint64_t *bar, uint32_t count)
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
 }
 
-// The issuing thread's generic-proxy view of the buffer (the previous unit's
-// reads, ordered before it by a CTA barrier) precedes the async-proxy writes.
-__device__ __forceinline__ void fence_proxy_async_smem()
-{
-    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-}
-
-// The same for every state space: also orders generic-proxy writes to global
-// memory that this thread has observed (another CTA's stores of the previous
-// iteration, acquired through the grid barrier) before its async-proxy reads.
+// Orders generic-proxy writes that this thread has observed (another CTA's
+// global stores of the previous iteration, acquired through the grid
+// barrier) before its later async-proxy (bulk copy) reads.
 __device__ __forceinline__ void fence_proxy_async_all()
 {
     asm volatile("fence.proxy.async;" ::: "memory");
@@ -676,7 +669,8 @@ struct CsrStage {
         __syncwarp();
         if (on) {
             if ((threadIdx.x & 31) == 0) {
-                fence_proxy_async_smem();
+                // the lanes' reads of the previous rows' entries were consumed
+                // before the __syncwarp above, so the copy cannot overtake them
                 const uint32_t cb = (uint32_t)cnt * 4u, vb = (uint32_t)cnt * (uint32_t)sizeof(T);
                 mbar_arrive_expect_tx(bar, cb + vb);
                 bulk_copy_g2s(col, csr.col + *e0s, cb, bar);
