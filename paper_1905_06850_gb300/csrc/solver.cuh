@@ -727,9 +727,9 @@ __device__ __forceinline__ void op_apply(const StencilDesc &st, const CsrDesc &c
 template <typename T>
 struct Coef {
     int mode;                 // 0: fill (i < l), 1: recurrences (i >= l)
-    int k6;                   // 0: none, 1: p_0 = v_0 / eta_0, 2: x and p update
+    int k6;                   // 0: none, 1: phat_0 = v_0, 2: x and phat update (phat_m = eta_m p_m)
     int end;                  // -1: continue, else SegEnd
-    int fmode;                // final sweep: 0 x += f1 p; 1 lucky (m >= 1); 2 lucky (m = 0)
+    int fmode;                // final sweep: 0 x += f1 phat; 1 lucky (m >= 1); 2 lucky (m = 0)
     int prev0;                // z^(0)_{m-1} exists
     int ncopy;
     long long kseg;           // k of the iterate the segment returns (when end >= 0)
@@ -1082,17 +1082,19 @@ __device__ __forceinline__ void scalar_step_body(Smem<T> &s, Coef<T> &cf, const 
                 cf.pv = (T)(1.0 / gm);
                 cf.f2 = (T)rn;
             } else {
+                // p_{m-1} = phat_{m-1} / eta_{m-1}; p_m = (v_m - delta_{m-1} p_{m-1}) / eta_m
+                const double iep = s.ieta[(m - 1) & 1];
                 cf.fmode = 1;
-                cf.f1 = (T)s.zeta[(m - 1) & 1];
+                cf.f1 = (T)(s.zeta[(m - 1) & 1] * iep);
                 cf.pv = (T)iem;
-                cf.pp = (T)(-dm1 * iem);
+                cf.pp = (T)(-dm1 * iem * iep);
                 cf.f2 = (T)zm;
             }
             cf.end = kSegLucky;
             cf.kseg = m + 1;
         } else {             // breakdown: keep x_m and restart
             cf.fmode = 0;
-            cf.f1 = (T)((m >= 1) ? s.zeta[(m - 1) & 1] : 0.0);
+            cf.f1 = (T)((m >= 1) ? s.zeta[(m - 1) & 1] * s.ieta[(m - 1) & 1] : 0.0);
             cf.end = kSegBreakdown;
             cf.kseg = m;
         }
@@ -1115,17 +1117,19 @@ __device__ __forceinline__ void scalar_step_body(Smem<T> &s, Coef<T> &cf, const 
     cf.prev0 = (m >= 1);
 #pragma unroll
     for (int k = 0; k < L; ++k) cf.ak[k] = (T)((a.sigma[k] - gm) * invd);
+    // K6 on the scaled direction phat_m = eta_m p_m (one FMA per row fewer):
+    // phat_0 = v_0, phat_m = v_m - (delta_{m-1} / eta_{m-1}) phat_{m-1},
+    // x_m = x_{m-1} + (zeta_{m-1} / eta_{m-1}) phat_{m-1}
     if (i == L) {
         s.eta[0] = gm;
         s.zeta[0] = rn;
         s.ieta[0] = 1.0 / gm;
         cf.k6 = 1;
-        cf.pv = (T)s.ieta[0];
     } else {
+        const double iep = s.ieta[(m - 1) & 1];
         cf.k6 = 2;
-        cf.zx = (T)s.zeta[(m - 1) & 1];
-        cf.pv = (T)iem;
-        cf.pp = (T)(-dm1 * iem);
+        cf.zx = (T)(s.zeta[(m - 1) & 1] * iep);
+        cf.pp = (T)(-dm1 * iep);
         s.eta[m & 1] = em;
         s.ieta[m & 1] = iem;
         s.zeta[m & 1] = zm;
@@ -1689,12 +1693,12 @@ __device__ void plcg_body(const SolveArgs<T> &a, Smem<T> &s, Grp &grp)
                         // K6: p and the iterate (Algorithm 1, K6)
                         if (k6 == 1) {
 #pragma unroll
-                            for (int v = 0; v < VEC; ++v) pv[r][v] = C.pv * cur[r][0][v];
+                            for (int v = 0; v < VEC; ++v) pv[r][v] = cur[r][0][v];
                         } else if (k6 == 2) {
 #pragma unroll
                             for (int v = 0; v < VEC; ++v) {
                                 xv[r][v] = fma(C.zx, pv[r][v], xv[r][v]);
-                                pv[r][v] = fma(C.pv, cur[r][0][v], C.pp * pv[r][v]);
+                                pv[r][v] = fma(C.pp, pv[r][v], cur[r][0][v]);
                             }
                         }
                         // -- stores
