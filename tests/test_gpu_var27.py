@@ -161,14 +161,16 @@ def test_var27_fp32_tiles_ragged_grids(P, dims):
     lines and, in the steady state, the vector operands) and applies rows
     without boundary tests (out-of-grid entries stored as zero, zero halos
     around the arrays): ragged and degenerate grids, units that straddle the
-    grid's ends, l = 1..3 with and without Jacobi, refined to rtol 1e-10."""
+    grid's ends, l = 1..5 with and without Jacobi (l > 3 stages the operator
+    only), refined to rtol 1e-10."""
     import scipy.sparse.linalg as spl
     op = W.hetero27_var27(*dims, seed=7 + sum(dims))
     n = W.op_size(op)
     b = np.random.default_rng(n + 1).standard_normal(n)
     A = W.to_scipy(W.fp32_rounded(op)).tocsc()
     xs = spl.spsolve(A, b)
-    for kw in ({"l": 1}, {"l": 2}, {"l": 3}, {"l": 1, "precond": "jacobi"}, {"l": 3, "precond": "jacobi"}):
+    for kw in ({"l": 1}, {"l": 2}, {"l": 3}, {"l": 1, "precond": "jacobi"}, {"l": 3, "precond": "jacobi"},
+               {"l": 4}, {"l": 5, "precond": "jacobi"}):   # l > 3: tiles without vector slots
         oop = W.fp32_rounded(op)
         interval = W.jacobi_shift_interval(oop) if "precond" in kw else W.shift_interval(oop)
         x, res = gpu_solve(P, op, b, prec="fp32", interval=interval, rtol=1e-10, max_restarts=64, **kw)
