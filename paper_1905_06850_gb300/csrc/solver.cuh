@@ -734,6 +734,7 @@ struct Coef {
     int ncopy;
     long long kseg;           // k of the iterate the segment returns (when end >= 0)
     T sig, invd, al, bm;
+    T uc, unb;                // K4 coefficients of z^(l)_i and of the SpMV's neighbour part
     T ak[kMaxL];
     T zx, pv, pp;
     T f1, f2;
@@ -755,7 +756,7 @@ struct Coef {
 template <typename T, int L>
 struct SweepCoef {
     int mode, k6, prev0, ncopy;
-    T sig, invd, al, bm, zx, pv, pp;
+    T sig, invd, al, bm, uc, unb, zx, pv, pp;
     T ak[L];
     int dsrc[2 * L + 1];
     const T *zl_cur, *zl_prev;
@@ -764,7 +765,8 @@ struct SweepCoef {
     T *nw[L];
     __device__ __forceinline__ SweepCoef(const Coef<T> &c)
         : mode(c.mode), k6(c.k6), prev0(c.prev0), ncopy(c.ncopy), sig(c.sig), invd(c.invd),
-          al(c.al), bm(c.bm), zx(c.zx), pv(c.pv), pp(c.pp), zl_cur(c.zl_cur), zl_prev(c.zl_prev),
+          al(c.al), bm(c.bm), uc(c.uc), unb(c.unb), zx(c.zx), pv(c.pv), pp(c.pp), zl_cur(c.zl_cur),
+          zl_prev(c.zl_prev),
           zl_new(c.zl_new)
     {
 #pragma unroll
@@ -1012,7 +1014,7 @@ __device__ __forceinline__ void step_vectors(Coef<T> &cf, const SolveArgs<T> &a,
 template <typename T, int L>
 __device__ __forceinline__ void scalar_step_body(Smem<T> &s, Coef<T> &cf, const double *raw,
                                                  const SolveArgs<T> &a, int i, double rn,
-                                                 double tau, long long budget)
+                                                 double tau, long long budget, T kc, T kn)
 {
     cf.end = -1;
     cf.fmode = 0;
@@ -1114,6 +1116,10 @@ __device__ __forceinline__ void scalar_step_body(Smem<T> &s, Coef<T> &cf, const 
     cf.invd = (T)invd;
     cf.al = (T)(-gm * invd);
     cf.bm = (T)((m >= 1) ? -dm1 * invd : 0.0);
+    // (A z)_g = kc z_g + kn nb_g: K4's coefficients of z^(l)_i and nb, once
+    // here instead of per row in the sweep
+    cf.uc = fma(kc, cf.invd, cf.al);
+    cf.unb = kn * cf.invd;
     cf.prev0 = (m >= 1);
 #pragma unroll
     for (int k = 0; k < L; ++k) cf.ak[k] = (T)((a.sigma[k] - gm) * invd);
@@ -1152,9 +1158,9 @@ __device__ __forceinline__ void scalar_step_body(Smem<T> &s, Coef<T> &cf, const 
 template <typename T, int L>
 __device__ __noinline__ void scalar_step_call(Smem<T> &s, Coef<T> &cf, const double *raw,
                                               const SolveArgs<T> &a, int i, double rn, double tau,
-                                              long long budget)
+                                              long long budget, T kc, T kn)
 {
-    scalar_step_body<T, L>(s, cf, raw, a, i, rn, tau, budget);
+    scalar_step_body<T, L>(s, cf, raw, a, i, rn, tau, budget, kc, kn);
 }
 
 // The scalar step inline, except in the FP32 whole-grid kernels: there the
@@ -1165,10 +1171,10 @@ __device__ __noinline__ void scalar_step_call(Smem<T> &s, Coef<T> &cf, const dou
 template <typename T, int L, bool OOL>
 __device__ __forceinline__ void scalar_step(Smem<T> &s, Coef<T> &cf, const double *raw,
                                             const SolveArgs<T> &a, int i, double rn, double tau,
-                                            long long budget)
+                                            long long budget, T kc, T kn)
 {
-    if constexpr (OOL) scalar_step_call<T, L>(s, cf, raw, a, i, rn, tau, budget);
-    else scalar_step_body<T, L>(s, cf, raw, a, i, rn, tau, budget);
+    if constexpr (OOL) scalar_step_call<T, L>(s, cf, raw, a, i, rn, tau, budget, kc, kn);
+    else scalar_step_body<T, L>(s, cf, raw, a, i, rn, tau, budget, kc, kn);
 }
 
 // Per-thread accumulator of one dot product over the units a thread sweeps.
@@ -1436,7 +1442,7 @@ __device__ void plcg_body(const SolveArgs<T> &a, Smem<T> &s, Grp &grp)
         // l iterations later) with the local work, on one GPU.
         const bool la = (L >= 2) && a.lookahead;
         const int nsw = la ? kBlock - 32 : kBlock;   // threads that sweep
-        if (tid == 0) scalar_step<T, L, kOolScalar>(s, s.cfb[0], s.raw, a, 0, rn, tau, budget);
+        if (tid == 0) scalar_step<T, L, kOolScalar>(s, s.cfb[0], s.raw, a, 0, rn, tau, budget, kc, kn);
         __syncthreads();
         for (long long i = 0;; ++i) {
             const Coef<T> &cf = s.cfb[i & 1];
@@ -1493,7 +1499,8 @@ __device__ void plcg_body(const SolveArgs<T> &a, Smem<T> &s, Grp &grp)
                 if (i + 1 >= L)
                     grp.template get_dots_warp<2 * L + 1>(a, s, (int)((i + 1 - L) % (L + 1)), s.raw2);
                 if ((tid & 31) == 0)
-                    scalar_step<T, L, kOolScalar>(s, s.cfb[(i + 1) & 1], s.raw2, a, (int)(i + 1), rn, tau, budget);
+                    scalar_step<T, L, kOolScalar>(s, s.cfb[(i + 1) & 1], s.raw2, a, (int)(i + 1), rn, tau, budget,
+                                                  kc, kn);
                 __syncwarp();
             }
             // ---- one full iteration sweep: K1, K4, K5 (partials), K6.  A thread
@@ -1678,7 +1685,7 @@ __device__ void plcg_body(const SolveArgs<T> &a, Smem<T> &s, Grp &grp)
                         } else {
                             // K4: z^(l)_{i+1} = (A z^(l)_i - gamma z^(l)_i - delta' z^(l)_{i-1}) / delta
                             // and z^(k)_{i-l+k+1}, k < l (Algorithm 1, K4)
-                            const T uc = fma(kc, C.invd, C.al), un_nb = kn * C.invd;
+                            const T uc = C.uc, un_nb = C.unb;
 #pragma unroll
                             for (int v = 0; v < VEC; ++v)
                                 un[v] = fma(uc, c[r][v], fma(un_nb, nb[r][v], C.bm * zp[r][v]));
@@ -1769,7 +1776,8 @@ __device__ void plcg_body(const SolveArgs<T> &a, Smem<T> &s, Grp &grp)
                     if (i + 1 >= L)
                         grp.template get_dots_warp<2 * L + 1>(a, s, (int)((i + 1 - L) % (L + 1)), s.raw);
                     if (tid == 0)
-                        scalar_step<T, L, kOolScalar>(s, s.cfb[(i + 1) & 1], s.raw, a, (int)(i + 1), rn, tau, budget);
+                        scalar_step<T, L, kOolScalar>(s, s.cfb[(i + 1) & 1], s.raw, a, (int)(i + 1), rn, tau,
+                                                      budget, kc, kn);
                 }
                 __syncthreads();
             }
