@@ -6,11 +6,13 @@
 
 namespace plcg {
 
-const void *kptr_f64_csr(int l, bool cg)
+const void *kptr_f64_csr(int l, bool cg, bool sc)
 {
     if (cg) return reinterpret_cast<const void *>(&cg_kernel<double, 1, kOpCsr>);
     switch (l) {
-    case 1: return reinterpret_cast<const void *>(&plcg_kernel<double, 1, 1, kOpCsr>);
+    case 1:   // sc: the scaled-basis variant (large systems)
+        return sc ? reinterpret_cast<const void *>(&plcg_kernel<double, 1, 1, kOpCsr, true>)
+                  : reinterpret_cast<const void *>(&plcg_kernel<double, 1, 1, kOpCsr>);
     case 2: return reinterpret_cast<const void *>(&plcg_kernel<double, 2, 1, kOpCsr>);
     case 3: return reinterpret_cast<const void *>(&plcg_kernel<double, 3, 1, kOpCsr>);
     case 4: return reinterpret_cast<const void *>(&plcg_kernel<double, 4, 1, kOpCsr>);

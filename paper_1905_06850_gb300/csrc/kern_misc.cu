@@ -4,14 +4,14 @@
 
 namespace plcg {
 
-const void *kernel_ptr(bool f32, int op, int vec, int l, bool cg)
+const void *kernel_ptr(bool f32, int op, int vec, int l, bool cg, bool sc)
 {
     if (!f32) {
-        if (op == kOpCsr) return kptr_f64_csr(l, cg);
-        if (op == kOpCsrJacobi) return kptr_f64_csrj(l, cg);
-        if (op == kOpVar27) return kptr_f64_v27(l, cg);
-        if (op == kOpVar27Jacobi) return kptr_f64_v27j(l, cg);
-        return vec == 2 ? kptr_f64_st2(l, cg) : kptr_f64_st1(l, cg);
+        if (op == kOpCsr) return kptr_f64_csr(l, cg, sc);
+        if (op == kOpCsrJacobi) return kptr_f64_csrj(l, cg, sc);
+        if (op == kOpVar27) return kptr_f64_v27(l, cg, sc);
+        if (op == kOpVar27Jacobi) return kptr_f64_v27j(l, cg, sc);
+        return vec == 2 ? kptr_f64_st2(l, cg, sc) : kptr_f64_st1(l, cg, sc);
     }
     if (op == kOpCsr) return kptr_f32_csr(l, cg);
     if (op == kOpCsrJacobi) return kptr_f32_csrj(l, cg);

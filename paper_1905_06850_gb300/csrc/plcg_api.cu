@@ -418,7 +418,10 @@ static plcg_status build_solve(const plcg_matrix *A, const double *b, double *x,
         const int want = 16 / (int)sizeof(T);
         vec = (A->st.nx % want == 0) ? want : 1;
     }
-    const void *func = kernel_ptr(f32, op, vec, cg ? 0 : l, cg);
+    // FP64 p(1)-CG on 2^19 rows or more: the scaled-basis kernel (two FP64
+    // multiplies per row fewer; below that the longer scalar step costs more)
+    const bool sc = !f32 && !cg && l == 1 && n >= (int64_t(1) << 19);
+    const void *func = kernel_ptr(f32, op, vec, cg ? 0 : l, cg, sc);
     if (!func) return fail(PLCG_ERR_UNIMPL, "no kernel for prec=%d op=%d vec=%d l=%d", (int)f32, op, vec, l);
     // CSR kernels stage each unit's entries in dynamic shared memory (FP64
     // classic CG excepted, see cg_body); the 27-point p(l)-CG kernels stage

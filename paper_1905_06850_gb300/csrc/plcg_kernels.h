@@ -10,7 +10,7 @@ namespace plcg {
 
 // Address of the persistent solver for (FP32 path?, operator, vector width,
 // pipeline length l, classic CG?); nullptr when not instantiated.
-const void *kernel_ptr(bool f32, int op, int vec, int l, bool cg);
+const void *kernel_ptr(bool f32, int op, int vec, int l, bool cg, bool sc = false);
 
 // Address of the batched kernel for p(l)-CG (l = 1..4) or classic CG.
 const void *batched_kernel_ptr(bool f32, int l, bool cg);
@@ -18,17 +18,17 @@ const void *batched_kernel_ptr_f32(int l, bool cg);
 const void *batched_kernel_ptr_f64(int l, bool cg);
 
 // Per-translation-unit getters used by kernel_ptr.
-const void *kptr_f64_st2(int l, bool cg);
-const void *kptr_f64_st1(int l, bool cg);
-const void *kptr_f64_csr(int l, bool cg);
+const void *kptr_f64_st2(int l, bool cg, bool sc);
+const void *kptr_f64_st1(int l, bool cg, bool sc);
+const void *kptr_f64_csr(int l, bool cg, bool sc);
 const void *kptr_f32_st4(int l, bool cg);
 const void *kptr_f32_st1(int l, bool cg);
 const void *kptr_f32_csr(int l, bool cg);
-const void *kptr_f64_csrj(int l, bool cg);
+const void *kptr_f64_csrj(int l, bool cg, bool sc);
 const void *kptr_f32_csrj(int l, bool cg);
-const void *kptr_f64_v27(int l, bool cg);
+const void *kptr_f64_v27(int l, bool cg, bool sc);
 const void *kptr_f32_v27(int l, bool cg);
-const void *kptr_f64_v27j(int l, bool cg);
+const void *kptr_f64_v27j(int l, bool cg, bool sc);
 const void *kptr_f32_v27j(int l, bool cg);
 
 // Sets the thread-local message returned by plcg_last_error().

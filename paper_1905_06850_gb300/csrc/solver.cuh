@@ -736,6 +736,8 @@ struct Coef {
     T sig, invd, al, bm;
     T uc, unb;                // K4 coefficients of z^(l)_i and of the SpMV's neighbour part
     T ak[kMaxL];
+    T wu[kMaxL], wb[kMaxL];   // K4, basis k < l: coefficients of z^(k+1) and of z^(k)_{prev}
+    int unit;                 // scaled bases: unb and wu[0] are exactly 1 (steady sweep form)
     T zx, pv, pp;
     T f1, f2;
     int dsrc[kMaxDots];       // 0 off, 1 memory, 2 new u, 3 new v, 4 z^(l)_i, 5 z^(l)_{i-1}
@@ -757,7 +759,8 @@ template <typename T, int L>
 struct SweepCoef {
     int mode, k6, prev0, ncopy;
     T sig, invd, al, bm, uc, unb, zx, pv, pp;
-    T ak[L];
+    T ak[L], wu[L], wb[L];
+    int unit;
     int dsrc[2 * L + 1];
     const T *zl_cur, *zl_prev;
     T *zl_new;
@@ -767,11 +770,13 @@ struct SweepCoef {
         : mode(c.mode), k6(c.k6), prev0(c.prev0), ncopy(c.ncopy), sig(c.sig), invd(c.invd),
           al(c.al), bm(c.bm), uc(c.uc), unb(c.unb), zx(c.zx), pv(c.pv), pp(c.pp), zl_cur(c.zl_cur),
           zl_prev(c.zl_prev),
-          zl_new(c.zl_new)
+          zl_new(c.zl_new), unit(c.unit)
     {
 #pragma unroll
         for (int k = 0; k < L; ++k) {
             ak[k] = c.ak[k];
+            wu[k] = c.wu[k];
+            wb[k] = c.wb[k];
             cur[k] = c.cur[k];
             prv[k] = c.prv[k];
             nw[k] = c.nw[k];
@@ -790,6 +795,9 @@ struct Smem {
     double Ginv[kMaxL + 1];          // 1 / g_{c,c} of those columns
     double gam[kMaxL + 1], del[kMaxL + 1], idel[kMaxL + 1];   // gamma_j, delta_j, 1 / delta_j
     double eta[2], zeta[2], ieta[2]; // eta_m, zeta_m, 1 / eta_m
+    double scs[4], sct[4];           // scaled bases: s_j of z^(l)_j, t_j of z^(0)_j (j mod 4)
+    double iscs[4], isct[4];         // ... and their reciprocals
+    double ikn;                      // 1 / kn
     double bring[kMaxL + 1][kMaxDots];   // one-CTA group: reduced dots of the last l+1 iterations
     double bnorm[2];
     double raw2[kMaxDots];           // the scalar warp's copy of a reduced dot column
@@ -1011,7 +1019,23 @@ __device__ __forceinline__ void step_vectors(Coef<T> &cf, const SolveArgs<T> &a,
     }
 }
 
+// Scaled bases (FP64, l = 1).  The sweep stores Z_j = z^(1)_j / s_j and
+// W_j = z^(0)_j / t_j, and the direction P_m = phat_m / t_m, with the scales
+// chosen so that K4 needs no multiply: s_{i+1} = s_i kn / delta_m and
+// t_{m+1} = s_i / delta_m, times a power of two (2^e, 2^f) only when the
+// product leaves [2^-256, 2^256]; with (A z)_g = kc z_g + kn nb_g,
+//   Z_{i+1} = nb(Z_i) + ((kc - gamma_m) / kn) Z_i - (delta_{m-1} s_{i-1} / (kn s_i)) Z_{i-1}
+//   W_{m+1} = Z_i + (sigma_0 - gamma_m)(t_m / s_i) W_m - delta_{m-1} (t_{m-1} / s_i) W_{m-1}
+// (each divided by 2^e or 2^f when that is not 1: the general sweep form
+// then).  The host picks this variant (SC) for 2^19 rows or more: below
+// that the step's extra latency outweighs two FP64 multiplies per row.
+// The K5 dots of scaled vectors are multiplied back by their scales here,
+// so G, gamma, delta, eta and zeta are those of the unscaled algorithm; K6
+// folds t into its scalars.  Same iterates in exact arithmetic.
 template <typename T, int L>
+constexpr bool kScaledBases = (sizeof(T) == 8 && L == 1);
+
+template <typename T, int L, bool SC>
 __device__ __forceinline__ void scalar_step_body(Smem<T> &s, Coef<T> &cf, const double *raw,
                                                  const SolveArgs<T> &a, int i, double rn,
                                                  double tau, long long budget, T kc, T kn)
@@ -1019,16 +1043,35 @@ __device__ __forceinline__ void scalar_step_body(Smem<T> &s, Coef<T> &cf, const 
     cf.end = -1;
     cf.fmode = 0;
     cf.ncopy = 0;
+    cf.unit = 0;
     const int m = i - L;
     step_vectors<T, L>(cf, a, i);
+    constexpr bool kScaled = SC && kScaledBases<T, L>;
+    const bool scl = kScaled && kn != T(0);
     if (i < L) {
         cf.mode = 0;
         cf.k6 = 0;
         cf.sig = (T)a.sigma[i];
+        if (kScaled && i == 0) {   // a segment starts from unscaled vectors
+            s.scs[0] = s.scs[1] = s.iscs[0] = s.iscs[1] = 1.0;
+            s.sct[0] = s.isct[0] = 1.0;
+            s.ikn = scl ? 1.0 / (double)kn : 0.0;
+        }
         return;
     }
     const int c = i - L + 1;
     double *col = s.G[c % (L + 1)];
+    // scales of this step (l = 1: c = i, m = i - 1): s_i, s_{i-1}, t_m, t_{m-1}
+    // (with reciprocals kept beside them: no division on the step's path)
+    double s_i = 1.0, s_im1 = 1.0, t_m = 1.0, t_mm1 = 1.0, is_i = 1.0, it_m = 1.0;
+    if (scl) {
+        s_i = s.scs[i & 3];
+        is_i = s.iscs[i & 3];
+        s_im1 = s.scs[(i - 1) & 3];
+        t_m = s.sct[m & 3];
+        it_m = s.isct[m & 3];
+        t_mm1 = (m >= 1) ? s.sct[(m - 1) & 3] : 1.0;
+    }
     auto g = [&](int j, int cc) -> double {
         if (j < 0 || j < cc - 2 * L || j > cc) return 0.0;
         return s.G[cc % (L + 1)][j - cc + 2 * L];
@@ -1037,9 +1080,14 @@ __device__ __forceinline__ void scalar_step_body(Smem<T> &s, Coef<T> &cf, const 
     auto del = [&](int j) -> double { return j < 0 ? 0.0 : s.del[j % (L + 1)]; };
     auto idel = [&](int j) -> double { return s.idel[j % (L + 1)]; };
     auto gam = [&](int j) -> double { return s.gam[j % (L + 1)]; };
-    // raw column c (dots of iteration i-l): position q is row c-2l+q
+    // raw column c (dots of iteration i-l): position q is row c-2l+q; scaled
+    // bases: u_c = s_c Z_c against t_{c-2} W, t_{c-1} W, s_c Z (l = 1)
 #pragma unroll
-    for (int q = 0; q <= 2 * L; ++q) col[q] = (c - 2 * L + q >= 0) ? raw[q] : 0.0;
+    for (int q = 0; q <= 2 * L; ++q) {
+        double v = (c - 2 * L + q >= 0) ? raw[q] : 0.0;
+        if (scl) v *= s_i * (q == 2 * L ? s_i : q == 2 * L - 1 ? t_m : t_mm1);
+        col[q] = v;
+    }
     const int lo = (c - 2 * L > 0) ? c - 2 * L : 0;
     if (!a.dots_2l1)   // Sec. 2.2: g_{j,c} = g_{c-l,j+l} for j = c-2l .. c-l-1
         for (int j = lo; j <= c - L - 1; ++j) col[j - c + 2 * L] = g(c - L, j + L);
@@ -1085,18 +1133,19 @@ __device__ __forceinline__ void scalar_step_body(Smem<T> &s, Coef<T> &cf, const 
                 cf.f2 = (T)rn;
             } else {
                 // p_{m-1} = phat_{m-1} / eta_{m-1}; p_m = (v_m - delta_{m-1} p_{m-1}) / eta_m
+                // (scaled bases: v_m = t_m W_m, phat_{m-1} = t_{m-1} P_{m-1})
                 const double iep = s.ieta[(m - 1) & 1];
                 cf.fmode = 1;
-                cf.f1 = (T)(s.zeta[(m - 1) & 1] * iep);
-                cf.pv = (T)iem;
-                cf.pp = (T)(-dm1 * iem * iep);
+                cf.f1 = (T)(s.zeta[(m - 1) & 1] * iep * t_mm1);
+                cf.pv = (T)(iem * t_m);
+                cf.pp = (T)(-dm1 * iem * iep * t_mm1);
                 cf.f2 = (T)zm;
             }
             cf.end = kSegLucky;
             cf.kseg = m + 1;
         } else {             // breakdown: keep x_m and restart
             cf.fmode = 0;
-            cf.f1 = (T)((m >= 1) ? s.zeta[(m - 1) & 1] * s.ieta[(m - 1) & 1] : 0.0);
+            cf.f1 = (T)((m >= 1) ? s.zeta[(m - 1) & 1] * s.ieta[(m - 1) & 1] * t_mm1 : 0.0);
             cf.end = kSegBreakdown;
             cf.kseg = m;
         }
@@ -1113,16 +1162,45 @@ __device__ __forceinline__ void scalar_step_body(Smem<T> &s, Coef<T> &cf, const 
     s.del[m % (L + 1)] = dm;
     s.idel[m % (L + 1)] = invd;
     cf.mode = 1;
-    cf.invd = (T)invd;
-    cf.al = (T)(-gm * invd);
-    cf.bm = (T)((m >= 1) ? -dm1 * invd : 0.0);
-    // (A z)_g = kc z_g + kn nb_g: K4's coefficients of z^(l)_i and nb, once
-    // here instead of per row in the sweep
-    cf.uc = fma(kc, cf.invd, cf.al);
-    cf.unb = kn * cf.invd;
     cf.prev0 = (m >= 1);
+    if (scl) {
+        // scaled bases: the new scales, 2^e and 2^f keeping them in range
+        const double bs = invd * (double)kn * s_i, bt = invd * s_i;
+        int e = 0, f = 0;
+        if (!(fabs(bs) >= 0x1p-256 && fabs(bs) <= 0x1p256)) e = -ilogb(bs);
+        if (!(fabs(bt) >= 0x1p-256 && fabs(bt) <= 0x1p256)) f = -ilogb(bt);
+        auto pow2 = [](int k) -> double {   // 2^k, |k| < 1000
+            return __longlong_as_double((long long)(1023 + k) << 52);
+        };
+        const double pe = pow2(-e), pf = pow2(-f), ivk = pe * s.ikn;
+        s.scs[(i + 1) & 3] = bs * pow2(e);
+        s.iscs[(i + 1) & 3] = dm * s.ikn * is_i * pe;
+        s.sct[(m + 1) & 3] = bt * pow2(f);
+        s.isct[(m + 1) & 3] = dm * is_i * pf;
+        cf.invd = (T)ivk;
+        cf.al = (T)(-gm * ivk);
+        cf.uc = (T)(((double)kc - gm) * ivk);
+        cf.unb = (T)pe;
+        cf.bm = (T)((m >= 1) ? -dm1 * (s_im1 * is_i) * ivk : 0.0);
+        cf.ak[0] = (T)((a.sigma[0] - gm) * (t_m * is_i) * pf);
+        cf.wu[0] = (T)pf;
+        cf.wb[0] = (T)((m >= 1) ? -dm1 * (t_mm1 * is_i) * pf : 0.0);
+        cf.unit = (e == 0 && f == 0);
+    } else {
+        cf.invd = (T)invd;
+        cf.al = (T)(-gm * invd);
+        cf.bm = (T)((m >= 1) ? -dm1 * invd : 0.0);
+        // (A z)_g = kc z_g + kn nb_g: K4's coefficients of z^(l)_i and nb, once
+        // here instead of per row in the sweep
+        cf.uc = fma(kc, cf.invd, cf.al);
+        cf.unb = kn * cf.invd;
 #pragma unroll
-    for (int k = 0; k < L; ++k) cf.ak[k] = (T)((a.sigma[k] - gm) * invd);
+        for (int k = 0; k < L; ++k) {
+            cf.ak[k] = (T)((a.sigma[k] - gm) * invd);
+            cf.wu[k] = cf.invd;
+            cf.wb[k] = cf.bm;
+        }
+    }
     // K6 on the scaled direction phat_m = eta_m p_m (one FMA per row fewer):
     // phat_0 = v_0, phat_m = v_m - (delta_{m-1} / eta_{m-1}) phat_{m-1},
     // x_m = x_{m-1} + (zeta_{m-1} / eta_{m-1}) phat_{m-1}
@@ -1134,8 +1212,9 @@ __device__ __forceinline__ void scalar_step_body(Smem<T> &s, Coef<T> &cf, const 
     } else {
         const double iep = s.ieta[(m - 1) & 1];
         cf.k6 = 2;
-        cf.zx = (T)(s.zeta[(m - 1) & 1] * iep);
-        cf.pp = (T)(-dm1 * iep);
+        // scaled bases: P_m = phat_m / t_m = W_m - (delta_{m-1}/eta_{m-1})(t_{m-1}/t_m) P_{m-1}
+        cf.zx = (T)(s.zeta[(m - 1) & 1] * iep * t_mm1);
+        cf.pp = (T)(-dm1 * iep * (t_mm1 * it_m));
         s.eta[m & 1] = em;
         s.ieta[m & 1] = iem;
         s.zeta[m & 1] = zm;
@@ -1155,12 +1234,12 @@ __device__ __forceinline__ void scalar_step_body(Smem<T> &s, Coef<T> &cf, const 
     }
 }
 
-template <typename T, int L>
+template <typename T, int L, bool SC>
 __device__ __noinline__ void scalar_step_call(Smem<T> &s, Coef<T> &cf, const double *raw,
                                               const SolveArgs<T> &a, int i, double rn, double tau,
                                               long long budget, T kc, T kn)
 {
-    scalar_step_body<T, L>(s, cf, raw, a, i, rn, tau, budget, kc, kn);
+    scalar_step_body<T, L, SC>(s, cf, raw, a, i, rn, tau, budget, kc, kn);
 }
 
 // The scalar step inline, except in the FP32 whole-grid kernels: there the
@@ -1168,13 +1247,13 @@ __device__ __noinline__ void scalar_step_call(Smem<T> &s, Coef<T> &cf, const dou
 // changes its register allocation enough to cost ~15% at 256^3 (measured);
 // the out-of-line call costs ~0.3 us per iteration, which the FP64 and
 // one-CTA paths (latency-bound on small systems) keep.
-template <typename T, int L, bool OOL>
+template <typename T, int L, bool OOL, bool SC>
 __device__ __forceinline__ void scalar_step(Smem<T> &s, Coef<T> &cf, const double *raw,
                                             const SolveArgs<T> &a, int i, double rn, double tau,
                                             long long budget, T kc, T kn)
 {
-    if constexpr (OOL) scalar_step_call<T, L>(s, cf, raw, a, i, rn, tau, budget, kc, kn);
-    else scalar_step_body<T, L>(s, cf, raw, a, i, rn, tau, budget, kc, kn);
+    if constexpr (OOL) scalar_step_call<T, L, SC>(s, cf, raw, a, i, rn, tau, budget, kc, kn);
+    else scalar_step_body<T, L, SC>(s, cf, raw, a, i, rn, tau, budget, kc, kn);
 }
 
 // Per-thread accumulator of one dot product over the units a thread sweeps.
@@ -1299,12 +1378,15 @@ __device__ __forceinline__ constexpr int steady_dot_src(int q)
 // ------------------------------------------------------------------------
 // p(l)-CG: a whole solve on one group (grid or CTA).
 // ------------------------------------------------------------------------
-template <typename T, int L, int VEC, int OP, class Grp, int RPT = 1>
+template <typename T, int L, int VEC, int OP, class Grp, int RPT = 1, bool SC = false>
 __device__ void plcg_body(const SolveArgs<T> &a, Smem<T> &s, Grp &grp)
 {
     constexpr int UNIT = kBlock * VEC;
     constexpr bool kF32 = (sizeof(T) == 4);
     constexpr bool kOolScalar = kF32 && std::is_same<Grp, GridGroup<T>>::value;
+    // FP64 p(1)-CG keeps its bases scaled (see scalar_step_body): two FP64
+    // multiplies per row fewer in the FP64-bound sweep
+    constexpr bool kScaled = SC && kScaledBases<T, L>;
     // CSR on the whole grid: each sweep unit's entries are bulk-copied into
     // shared memory (one contiguous range per unit) before its rows are read
     constexpr bool kStage = op_is_csr(OP) && std::is_same<Grp, GridGroup<T>>::value && RPT == 1;
@@ -1442,7 +1524,7 @@ __device__ void plcg_body(const SolveArgs<T> &a, Smem<T> &s, Grp &grp)
         // l iterations later) with the local work, on one GPU.
         const bool la = (L >= 2) && a.lookahead;
         const int nsw = la ? kBlock - 32 : kBlock;   // threads that sweep
-        if (tid == 0) scalar_step<T, L, kOolScalar>(s, s.cfb[0], s.raw, a, 0, rn, tau, budget, kc, kn);
+        if (tid == 0) scalar_step<T, L, kOolScalar, SC>(s, s.cfb[0], s.raw, a, 0, rn, tau, budget, kc, kn);
         __syncthreads();
         for (long long i = 0;; ++i) {
             const Coef<T> &cf = s.cfb[i & 1];
@@ -1499,7 +1581,7 @@ __device__ void plcg_body(const SolveArgs<T> &a, Smem<T> &s, Grp &grp)
                 if (i + 1 >= L)
                     grp.template get_dots_warp<2 * L + 1>(a, s, (int)((i + 1 - L) % (L + 1)), s.raw2);
                 if ((tid & 31) == 0)
-                    scalar_step<T, L, kOolScalar>(s, s.cfb[(i + 1) & 1], s.raw2, a, (int)(i + 1), rn, tau, budget,
+                    scalar_step<T, L, kOolScalar, SC>(s, s.cfb[(i + 1) & 1], s.raw2, a, (int)(i + 1), rn, tau, budget,
                                                   kc, kn);
                 __syncwarp();
             }
@@ -1686,16 +1768,26 @@ __device__ void plcg_body(const SolveArgs<T> &a, Smem<T> &s, Grp &grp)
                             // K4: z^(l)_{i+1} = (A z^(l)_i - gamma z^(l)_i - delta' z^(l)_{i-1}) / delta
                             // and z^(k)_{i-l+k+1}, k < l (Algorithm 1, K4)
                             const T uc = C.uc, un_nb = C.unb;
-#pragma unroll
-                            for (int v = 0; v < VEC; ++v)
-                                un[v] = fma(uc, c[r][v], fma(un_nb, nb[r][v], C.bm * zp[r][v]));
-#pragma unroll
-                            for (int k = 0; k < L; ++k)
+                            if (kScaled && S && C.unit) {
+                                // scaled bases, steady state: the coefficients of nb
+                                // and of z^(l)_i in the z^(0) recurrence are 1
 #pragma unroll
                                 for (int v = 0; v < VEC; ++v) {
-                                    const T up = (k == L - 1) ? c[r][v] : cur[r][k + 1][v];
-                                    nw[k][v] = fma(up, C.invd, fma(C.ak[k], cur[r][k][v], C.bm * pk[r][k][v]));
+                                    un[v] = fma(uc, c[r][v], fma(C.bm, zp[r][v], nb[r][v]));
+                                    nw[0][v] = fma(C.ak[0], cur[r][0][v], fma(C.wb[0], pk[r][0][v], c[r][v]));
                                 }
+                            } else {
+#pragma unroll
+                                for (int v = 0; v < VEC; ++v)
+                                    un[v] = fma(uc, c[r][v], fma(un_nb, nb[r][v], C.bm * zp[r][v]));
+#pragma unroll
+                                for (int k = 0; k < L; ++k)
+#pragma unroll
+                                    for (int v = 0; v < VEC; ++v) {
+                                        const T up = (k == L - 1) ? c[r][v] : cur[r][k + 1][v];
+                                        nw[k][v] = fma(up, C.wu[k], fma(C.ak[k], cur[r][k][v], C.wb[k] * pk[r][k][v]));
+                                    }
+                            }
                         }
                         // K6: p and the iterate (Algorithm 1, K6)
                         if (k6 == 1) {
@@ -1776,7 +1868,7 @@ __device__ void plcg_body(const SolveArgs<T> &a, Smem<T> &s, Grp &grp)
                     if (i + 1 >= L)
                         grp.template get_dots_warp<2 * L + 1>(a, s, (int)((i + 1 - L) % (L + 1)), s.raw);
                     if (tid == 0)
-                        scalar_step<T, L, kOolScalar>(s, s.cfb[(i + 1) & 1], s.raw, a, (int)(i + 1), rn, tau,
+                        scalar_step<T, L, kOolScalar, SC>(s, s.cfb[(i + 1) & 1], s.raw, a, (int)(i + 1), rn, tau,
                                                       budget, kc, kn);
                 }
                 __syncthreads();
@@ -2067,13 +2159,13 @@ template <typename T, int L, int OP>
 constexpr int kPlcgMinBlocks = (sizeof(T) == 4 && op_is_var27(OP)) ? (kV27Buf > 2 ? 1 : 2)
                              : (sizeof(T) == 4 && L <= 2) ? 3 : 2;
 
-template <typename T, int L, int VEC, int OP>
+template <typename T, int L, int VEC, int OP, bool SC = false>
 __global__ void __launch_bounds__(kBlock, (kPlcgMinBlocks<T, L, OP>))
 plcg_kernel(SolveArgs<T> a)
 {
     __shared__ Smem<T> s;
     GridGroup<T> grp;
-    plcg_body<T, L, VEC, OP>(a, s, grp);
+    plcg_body<T, L, VEC, OP, GridGroup<T>, 1, SC>(a, s, grp);
 }
 
 template <typename T, int VEC, int OP>
