@@ -48,14 +48,16 @@ def lap3d():
     return c
 
 
-@pytest.mark.parametrize("k", [1, 2, 20, 170, 330])
-def test_3d_iterates_across_rescales(P, lap3d, k):
+@pytest.mark.parametrize("k,dots_2l1", [(1, False), (2, False), (20, False), (170, False), (330, False),
+                                        (170, True)])
+def test_3d_iterates_across_rescales(P, lap3d, k, dots_2l1):
     """x_k element-wise: before the first rescale (k < 160) and after one
-    and two (k = 170, 330)."""
+    and two (k = 170, 330); with 2l+1 dots the third dot's scale too."""
     c = lap3d
     sig = O.chebyshev_shifts(1, *c["interval"])
-    ref = O.plcg(c["op"], c["b"], l=1, sigma=sig, rtol=1e-14, maxit=k, dots_2l1=False)
-    x, res = gpu_solve(P, c["op"], c["b"], l=1, rtol=1e-14, maxit=k, interval=c["interval"])
+    ref = O.plcg(c["op"], c["b"], l=1, sigma=sig, rtol=1e-14, maxit=k, dots_2l1=dots_2l1)
+    x, res = gpu_solve(P, c["op"], c["b"], l=1, rtol=1e-14, maxit=k, interval=c["interval"],
+                       dots_2l1=dots_2l1)
     assert res.status == P.PLCG_ERR_MAXIT and res.iters == k
     assert rel(x, ref.x) <= 1e-11, (k, rel(x, ref.x))
 
