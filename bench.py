@@ -43,6 +43,20 @@ def dist_env():
     return rank, world, local
 
 
+def aggregate_over_ranks(t_local: float, units_local: float, world: int, device=None):
+    """Whole-job figures of a timed region: the slowest rank's time (MAX) and
+    the units all ranks processed (SUM); one process: the local values."""
+    if world <= 1:
+        return float(t_local), float(units_local)
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([float(t_local)], dtype=torch.float64, device=device)
+    u = torch.tensor([float(units_local)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    dist.all_reduce(u, op=dist.ReduceOp.SUM)
+    return float(t.item()), float(u.item())
+
+
 # ---------------------------------------------------------------- clocks
 class ClockSampler:
     """nvidia-smi samples (every 200 ms) while the timed region runs."""
@@ -196,15 +210,11 @@ def run_ours(args):
             results.append(solve_once(xs[args.warmup + s]))
         ev1.record(stream)
         barrier()
-    t_total = ev0.elapsed_time(ev1) * 1e-3
-    if world > 1:
-        t = torch.tensor([t_total], device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        t_total = float(t.item())
     iters = [r.iters for r in results]
+    # max over ranks of the device time, iterations summed over ranks
+    t_total, total_iters = aggregate_over_ranks(ev0.elapsed_time(ev1) * 1e-3, sum(iters), world, dev)
     if not args.maxit:
         assert all(r.ok for r in results), [r.status for r in results]
-    total_iters = sum(iters) * world
     value = total_iters / t_total
     ms_per_step = t_total / args.steps * 1e3
     kern_s = [r.seconds for r in results]
@@ -295,15 +305,15 @@ def run_ours(args):
         bh = torch.tensor(b_np).pin_memory()
         xh = torch.zeros(n, dtype=torch.float64).pin_memory()
         A.solve_host(bh.numpy(), xh.numpy(), l=L_HEAD, interval=interval, rtol=RTOL)
-        torch.cuda.synchronize()
+        barrier()
         t0 = time.perf_counter()
         k_e2e = 0
         for _ in range(max(1, args.steps // 2)):
             xh.zero_()
             r = A.solve_host(bh.numpy(), xh.numpy(), l=L_HEAD, interval=interval, rtol=RTOL)
             k_e2e += r.iters
-        t_e2e = time.perf_counter() - t0
-        e2e = {"value": round(k_e2e * world / t_e2e, 1), "unit": UNIT,
+        t_e2e, k_all = aggregate_over_ranks(time.perf_counter() - t0, k_e2e, world, dev)
+        e2e = {"value": round(k_all / t_e2e, 1), "unit": UNIT,
                "h2d_bytes_per_step": 2 * 8 * n, "d2h_bytes_per_step": 8 * n,
                "steps": max(1, args.steps // 2)}
 
