@@ -223,16 +223,21 @@ plcg_status plcg_solve_batched(int count, plcg_matrix *const *A,
  *   desc, prm, res: as for plcg_create_stencil / plcg_solve (res may be
  *   NULL; res->seconds is 0).  b, x: device FP64[n], 16-byte aligned, owned
  *   by the caller (x in: x0, out: the solution).  stream: cudaStream_t.
+ * The solve runs as plcg_solve runs it for the same operator and parameters
+ * (the same checks, shifts, kernel, launch shape and kernel arguments, the
+ * debug hooks included), so its iterates and status are those of plcg_solve.
  * The solver's scratch is one fixed __device__ array of 32 MiB inside the
  * library, held by every GPU that loads it until the process exits; a solve
  * whose scratch would not fit (roughly n > 400k for FP64 l = 1) returns
  * PLCG_ERR_INVALID and names both sizes.  The call performs no cudaMalloc,
  * cudaFree or other allocation.  Its first call on a device looks up that
  * array's device address (cudaGetSymbolAddress), so make the first call on
- * each device before any stream capture.  All calls share the one array,
- * which keeps the previous call's contents (the parts that must start at
- * zero are cleared by each call); calls whose kernels overlap on the GPU
- * race with each other.  Returns the solve status like plcg_solve. */
+ * each device before any stream capture.  The call is synchronous: it
+ * returns after the solve has finished on the stream and its result record
+ * has been read back.  All calls share the one array, which keeps the
+ * previous call's contents (the parts that must start at zero are cleared
+ * by each call); calls whose kernels overlap on the GPU race with each
+ * other.  Returns the solve status like plcg_solve. */
 plcg_status plcg_solve_stencil_noalloc(const plcg_stencil_desc *desc, const double *b,
                                        double *x, const plcg_params *prm,
                                        plcg_result *res, void *stream);
@@ -296,6 +301,22 @@ void plcg_debug_set_poll_limit(uint64_t polls);
  * there are thread blocks, so the first wait runs out and the solve returns
  * PLCG_ERR_TIMEOUT (exercises the bounded-wait path); 0: off. */
 void plcg_debug_force_barrier_timeout(int on);
+
+/* Launch shape and flags of the calling thread's last single-system solve
+ * launch (plcg_solve, plcg_solve_host, plcg_estimate_interval,
+ * plcg_solve_stencil_noalloc), so that tests can check that two entry
+ * points launch the same way; all zero before the first launch. */
+typedef struct {
+    uint64_t kernel;            /* identifies the kernel instantiation          */
+    int grid_ctas;              /* thread blocks of the cooperative launch      */
+    unsigned dyn_smem;          /* dynamic shared memory bytes per block        */
+    int lookahead;              /* 1: each iteration's scalars are computed
+                                   during the previous sweep (l >= 2)           */
+    int staged;                 /* 1: CSR entries staged in shared memory       */
+    uint64_t poll_limit;        /* bound of every device-side wait (polls)      */
+    int force_timeout;          /* the plcg_debug_force_barrier_timeout setting */
+} plcg_launch_info;
+void plcg_debug_last_launch(plcg_launch_info *out);
 
 #ifdef __cplusplus
 }

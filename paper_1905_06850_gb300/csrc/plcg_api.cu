@@ -128,24 +128,22 @@ static plcg_status matrix_common_init(plcg_matrix *A, void *stream)
     return PLCG_OK;
 }
 
-extern "C" plcg_status plcg_create_stencil(const plcg_stencil_desc *d, void *stream,
-                                           plcg_matrix **out)
+// Validates a stencil description and fills the operator fields of *A (kind,
+// n, st); no CUDA call.
+static plcg_status stencil_from_desc(const plcg_stencil_desc *d, plcg_matrix *A)
 {
-    if (!d || !out) return fail(PLCG_ERR_INVALID, "plcg_create_stencil: NULL argument");
-    *out = nullptr;
     if (!((d->dim == 2 && d->points == 5) || (d->dim == 3 && d->points == 7)))
         return fail(PLCG_ERR_INVALID, "stencil: need dim 2 with 5 points or dim 3 with 7 points");
     const int64_t nz = (d->dim == 3) ? d->nz : 1;
     if (d->nx < 1 || d->ny < 1 || nz < 1)
         return fail(PLCG_ERR_INVALID, "stencil: grid sizes must be >= 1");
-    const int64_t n = d->nx * d->ny * nz;
-    if (n >= (int64_t(1) << 31) || d->nx >= (1 << 30) || d->ny >= (1 << 30) || nz >= (1 << 30))
+    if (d->nx >= (1 << 30) || d->ny >= (1 << 30) || nz >= (1 << 30) ||
+        d->nx * d->ny * nz >= (int64_t(1) << 31))
         return fail(PLCG_ERR_INVALID, "stencil: n must be < 2^31");
     if (!std::isfinite(d->center) || !std::isfinite(d->off) || !std::isfinite(d->diag_shift))
         return fail(PLCG_ERR_INVALID, "stencil: non-finite coefficient");
-    plcg_matrix *A = new plcg_matrix();
     A->kind = kOpStencil;
-    A->n = n;
+    A->n = d->nx * d->ny * nz;
     A->st.dim = d->dim;
     A->st.nx = (int)d->nx;
     A->st.ny = (int)d->ny;
@@ -154,7 +152,20 @@ extern "C" plcg_status plcg_create_stencil(const plcg_stencil_desc *d, void *str
     A->st.off = d->off;
     A->st.dnx = make_fastdiv((uint32_t)d->nx);
     A->st.dny = make_fastdiv((uint32_t)d->ny);
-    plcg_status st = matrix_common_init(A, stream);
+    return PLCG_OK;
+}
+
+extern "C" plcg_status plcg_create_stencil(const plcg_stencil_desc *d, void *stream,
+                                           plcg_matrix **out)
+{
+    if (!d || !out) return fail(PLCG_ERR_INVALID, "plcg_create_stencil: NULL argument");
+    *out = nullptr;
+    plcg_matrix tmp;
+    plcg_status st = stencil_from_desc(d, &tmp);
+    if (st != PLCG_OK) return st;
+    plcg_matrix *A = new plcg_matrix();
+    stencil_from_desc(d, A);
+    st = matrix_common_init(A, stream);
     if (st != PLCG_OK) { plcg_destroy(A); return st; }
     *out = A;
     return PLCG_OK;
@@ -537,6 +548,15 @@ static plcg_status build_solve(const plcg_matrix *A, const double *b, double *x,
     return PLCG_OK;
 }
 
+// Launch shape and flags of the calling thread's last single-solve launch
+// (plcg_debug_last_launch).
+static thread_local plcg_launch_info g_last_launch{};
+
+extern "C" void plcg_debug_last_launch(plcg_launch_info *out)
+{
+    if (out) *out = g_last_launch;
+}
+
 // Clear the barrier counter and result record, then launch the persistent
 // solver cooperatively (every CTA resident) on `stream`; returns at once.
 template <typename T>
@@ -546,6 +566,13 @@ static plcg_status launch_built(const SolveArgs<T> &a0, const void *func, int64_
     SolveArgs<T> a = a0;
     CUDA_TRY(cudaMemsetAsync(a.bar, 0, 256, stream));
     CUDA_TRY(cudaMemsetAsync(a.out, 0, sizeof(DevResult), stream));
+    g_last_launch.kernel = (uint64_t)reinterpret_cast<uintptr_t>(func);
+    g_last_launch.grid_ctas = (int)P;
+    g_last_launch.dyn_smem = a.dsmem;
+    g_last_launch.lookahead = a.lookahead;
+    g_last_launch.staged = a.stage;
+    g_last_launch.poll_limit = a.poll_limit;
+    g_last_launch.force_timeout = a.force_timeout;
     void *args[] = {&a};
     CUDA_TRY(cudaLaunchCooperativeKernel(func, dim3((unsigned)P), dim3(kBlock), args, a.dsmem, stream));
     return PLCG_OK;
@@ -658,6 +685,67 @@ extern "C" plcg_status plcg_solve(plcg_matrix *A, const double *b, double *x,
     CUDA_TRY(cudaSetDevice(A->device));
     if (prm->prec == PLCG_FP64) return run_solve<double>(A, b, x, prm, sigma, res);
     return run_solve<float>(A, b, x, prm, sigma, res);
+}
+
+// A solve whose workspace is the caller's [base, base + cap): the argument
+// checks, shifts, kernel choice, launch shape and kernel arguments of
+// plcg_solve (build_solve), with no allocation.  Synchronous; res->seconds = 0.
+template <typename T>
+static plcg_status run_solve_fixed(const plcg_matrix *A, const double *b, double *x,
+                                   const plcg_params *prm, const double *sigma, char *base,
+                                   size_t cap, const char *who, plcg_result *res)
+{
+    SolveArgs<T> a;
+    const void *func = nullptr;
+    int64_t P = 0;
+    int per_sm = 0;
+    size_t bytes = 0, o_out = 0;
+    plcg_status st = build_solve<T>(A, b, x, prm, sigma, 0, nullptr, &a, &func, &P, &per_sm, &bytes, &o_out);
+    if (st != PLCG_OK) return st;
+    if (bytes > cap)
+        return fail(PLCG_ERR_INVALID,
+                    "%s: this solve needs %zu bytes of scratch; the fixed no-allocation scratch holds %zu bytes "
+                    "(use plcg_solve)", who, bytes, cap);
+    st = build_solve<T>(A, b, x, prm, sigma, 0, base, &a, &func, &P, &per_sm, &bytes, &o_out);
+    if (st != PLCG_OK) return st;
+    st = launch_built<T>(a, func, P, A->stream);
+    if (st != PLCG_OK) return st;
+    DevResult o;
+    CUDA_TRY(cudaMemcpyAsync(&o, a.out, sizeof(DevResult), cudaMemcpyDeviceToHost, A->stream));
+    CUDA_TRY(cudaStreamSynchronize(A->stream));
+    if (res) {
+        res->status = o.status;
+        res->iters = o.iters;
+        res->spmvs = o.spmvs;
+        res->restarts = o.restarts;
+        res->refinements = o.refinements;
+        res->recursive_relres = o.recursive_relres;
+        res->true_relres = o.true_relres;
+        res->seconds = 0.0;   // no CUDA events are recorded on this path
+        res->latency = 0.0;
+    }
+    return result_status(o);
+}
+
+plcg_status plcg::solve_stencil_fixed(const plcg_stencil_desc *d, const double *b, double *x,
+                                      const plcg_params *prm, plcg_result *res, void *stream,
+                                      char *base, size_t cap, const char *who)
+{
+    if (!d || !b || !x || !prm) return fail(PLCG_ERR_INVALID, "%s: NULL argument", who);
+    plcg_matrix A;   // a host-side description only: no device data, no allocation
+    plcg_status st = stencil_from_desc(d, &A);
+    if (st != PLCG_OK) return st;
+    st = check_params(&A, prm);
+    if (st != PLCG_OK) return st;
+    if ((reinterpret_cast<uintptr_t>(b) | reinterpret_cast<uintptr_t>(x)) & 15)
+        return fail(PLCG_ERR_INVALID, "b and x must be 16-byte aligned");
+    A.stream = static_cast<cudaStream_t>(stream);
+    CUDA_TRY(cudaGetDevice(&A.device));
+    CUDA_TRY(cudaDeviceGetAttribute(&A.num_sms, cudaDevAttrMultiProcessorCount, A.device));
+    double sigma[kMaxL] = {0};
+    if (prm->method == PLCG_METHOD_PLCG) resolve_shifts(&A, prm, prm->lmin, prm->lmax, sigma);
+    if (prm->prec == PLCG_FP64) return run_solve_fixed<double>(&A, b, x, prm, sigma, base, cap, who, res);
+    return run_solve_fixed<float>(&A, b, x, prm, sigma, base, cap, who, res);
 }
 
 extern "C" plcg_status plcg_solve_host(plcg_matrix *A, const double *b, double *x,

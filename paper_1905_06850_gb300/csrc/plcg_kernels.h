@@ -6,6 +6,8 @@
 
 #include <string>
 
+#include "../../include/plcg.h"
+
 namespace plcg {
 
 // Address of the persistent solver for (FP32 path?, operator, vector width,
@@ -33,6 +35,15 @@ const void *kptr_f32_v27j(int l, bool cg);
 
 // Sets the thread-local message returned by plcg_last_error().
 void set_last_error(const std::string &msg);
+
+// A stencil solve run exactly as plcg_solve would run it (argument checks,
+// shifts, kernel, launch shape, kernel arguments), but with its workspace in
+// the caller's device memory [base, base + cap) instead of an allocation.
+// A solve whose workspace would exceed cap returns PLCG_ERR_INVALID naming
+// both sizes (`who` prefixes the messages).  Synchronous.
+plcg_status solve_stencil_fixed(const plcg_stencil_desc *desc, const double *b, double *x,
+                                const plcg_params *prm, plcg_result *res, void *stream, char *base,
+                                size_t cap, const char *who);
 
 // Jacobi data of a CSR matrix: dinv64 = 1 / diag (FP64), dinv and diag in
 // the stored value type (float if f32); *bad = 1 if a diagonal entry is not

@@ -63,6 +63,12 @@ class plcg_result(C.Structure):
                 ("seconds", C.c_double), ("latency", C.c_double)]
 
 
+class plcg_launch_info(C.Structure):
+    _fields_ = [("kernel", C.c_uint64), ("grid_ctas", C.c_int), ("dyn_smem", C.c_uint),
+                ("lookahead", C.c_int), ("staged", C.c_int), ("poll_limit", C.c_uint64),
+                ("force_timeout", C.c_int)]
+
+
 # every symbol include/plcg.h declares, with (restype, argtypes)
 _VP = C.c_void_p
 SIGNATURES = {
@@ -91,6 +97,7 @@ SIGNATURES = {
     "plcg_version": (C.c_char_p, []),
     "plcg_debug_set_poll_limit": (None, [C.c_uint64]),
     "plcg_debug_force_barrier_timeout": (None, [C.c_int]),
+    "plcg_debug_last_launch": (None, [C.POINTER(plcg_launch_info)]),
 }
 
 _lib = None
@@ -114,6 +121,13 @@ def load(path: str = LIB_PATH):
 
 def last_error() -> str:
     return load().plcg_last_error().decode()
+
+
+def last_launch() -> dict:
+    """plcg_debug_last_launch: shape and flags of this thread's last solve launch."""
+    info = plcg_launch_info()
+    load().plcg_debug_last_launch(C.byref(info))
+    return {name: getattr(info, name) for name, _ in info._fields_}
 
 
 class PlcgError(RuntimeError):

@@ -51,7 +51,7 @@ def test_struct_layouts_match_header(tmp_path):
     if not shutil.which("gcc"):
         pytest.skip("gcc not available")
     structs = {"plcg_params": plcg.plcg_params, "plcg_result": plcg.plcg_result,
-               "plcg_stencil_desc": plcg.plcg_stencil_desc}
+               "plcg_stencil_desc": plcg.plcg_stencil_desc, "plcg_launch_info": plcg.plcg_launch_info}
     lines = ['#include <stdio.h>', '#include <stddef.h>', '#include "plcg.h"', 'int main(void) {']
     for name, st in structs.items():
         lines.append(f'printf("{name} %zu\\n", sizeof({name}));')
