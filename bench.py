@@ -163,6 +163,49 @@ def dp_flops_per_point(l: int) -> int:
     return 8 + 6 * l + 10
 
 
+# ---------------------------------------------------------------- oracle errors
+class OracleErrors:
+    """FP64 oracle solves run on the host cores while the GPU legs run (a
+    process pool created with the spawn method before the first GPU call);
+    ``error(key, x)`` is ||x - x_oracle|| / ||x_oracle|| and the oracle's
+    iteration count, once the job has finished."""
+
+    def __init__(self, enabled: bool):
+        self.pool = None
+        self.futures = {}
+        if enabled:
+            from oracle import jobs
+            self.pool = jobs.pool()
+            self.run = jobs.run
+
+    def submit(self, key, **job):
+        if self.pool is not None and key not in self.futures:
+            self.futures[key] = self.pool.submit(self.run, dict(job, key=key))
+
+    def result(self, key):
+        f = self.futures.get(key)
+        if f is None:
+            return None
+        _, x, iters, restarts, secs = f.result()
+        return x, iters, restarts, secs
+
+    def annotate(self, entry: dict, key: str, x_gpu) -> dict:
+        """Adds err_vs_oracle, the oracle's iterations and restarts to entry."""
+        r = self.result(key)
+        if r is None:
+            entry["err_vs_oracle"] = None
+            return entry
+        x, iters, restarts, _ = r
+        entry["err_vs_oracle"] = float(np.linalg.norm(x_gpu - x) / max(np.linalg.norm(x), 1e-300))
+        entry["oracle_iters"] = iters
+        entry["oracle_restarts"] = restarts
+        return entry
+
+    def close(self):
+        if self.pool is not None:
+            self.pool.shutdown(wait=False, cancel_futures=True)
+
+
 # ---------------------------------------------------------------- our arm
 def run_ours(args):
     import torch
@@ -171,6 +214,12 @@ def run_ours(args):
     from paper_1905_06850_gb300 import workloads as W
 
     rank, world, local = dist_env()
+    # FP64 oracle solves for the error of every FP32 result: rank 0, started
+    # before the first GPU call
+    orc = OracleErrors(rank == 0 and not args.quick and not args.no_oracle_errors)
+    for l in (1, 2):
+        orc.submit(f"3d.l{l}", workload={"kind": "3d", "nx": args.nx}, method="plcg", l=l,
+                   interval=(0.0, 12.0), rtol=RTOL)
     if world > 1:
         dist.init_process_group("nccl" if torch.cuda.is_available() else "gloo")
     torch.cuda.set_device(local)
@@ -230,7 +279,12 @@ def run_ours(args):
     achieved_gbs = bytes_launch / statistics.mean(kern_s) / 1e9
     dp_flops = statistics.mean(iters) * dp_flops_per_point(L_HEAD) * n
     achieved_dp_tf = dp_flops / statistics.mean(kern_s) / 1e12
-    dp_peak_tf = 1.25   # nominal FP64 rate of GB300 (units x clock)
+    # FP64 peak: measured on this GPU (independent FMA chains on every
+    # resident thread, plcg_measure_fp64_fma_rate); nominal 1.25 if that fails
+    try:
+        dp_peak_tf, dp_src = round(plcg.measure_fp64_fma_rate() / 1e12, 4), "measured (plcg_measure_fp64_fma_rate)"
+    except Exception as exc:   # noqa: BLE001
+        dp_peak_tf, dp_src = 1.25, f"nominal (measurement failed: {exc})"
     # measured DRAM traffic per launch: bytes per row per sweep of an ncu
     # capture (smaller grid, same kernel) x rows x sweeps (iterations + 2
     # residual sweeps) of this solve
@@ -238,19 +292,20 @@ def run_ours(args):
     traffic = None if rec is None else round(rec["dram_bytes_per_point_iter"] * n * (statistics.mean(iters) + 2))
     hbm_frac = achieved_gbs / hbm_peak
     dp_frac = achieved_dp_tf / dp_peak_tf
+    # both fractions of the FP64 sweep: the HBM one (algorithmic bytes over the
+    # measured copy bandwidth) and the FP64 one (the paper's flop count over
+    # the measured FMA rate); "bound" names the larger
+    hbm_part = {"bound": "hbm", "achieved": round(achieved_gbs, 1), "peak": hbm_peak, "unit": "GB/s",
+                "frac": round(hbm_frac, 4), "peak_source": hbm_src,
+                "bytes_per_iter": bytes_iter}
+    alu_part = {"bound": "alu", "achieved": round(achieved_dp_tf, 4), "peak": dp_peak_tf,
+                "unit": "TFLOP/s", "frac": round(dp_frac, 4), "peak_source": dp_src,
+                "flops_per_row_iter": dp_flops_per_point(args.l),
+                "ncu_fp64_pipe_pct": None if rec is None else rec.get("fp64_pipe_pct")}
     if dp_frac >= hbm_frac:
-        roofline = {"bound": "alu", "achieved": round(achieved_dp_tf, 4), "peak": dp_peak_tf,
-                    "unit": "TFLOP/s", "frac": round(dp_frac, 4), "traffic": traffic,
-                    "peak_source": "nominal FP64 1.25 TFLOP/s (GB300 FP64 units x clock; a DFMA "
-                                   "microbenchmark reaches 1.01)",
-                    "flops_per_row_iter": dp_flops_per_point(args.l),
-                    "ncu_fp64_pipe_pct": None if rec is None else rec.get("fp64_pipe_pct"),
-                    "hbm": {"achieved_gbs": round(achieved_gbs, 1), "peak_gbs": hbm_peak,
-                            "frac": round(hbm_frac, 4), "peak_source": hbm_src}}
+        roofline = dict(alu_part, traffic=traffic, hbm=hbm_part)
     else:
-        roofline = {"bound": "hbm", "achieved": round(achieved_gbs, 1), "peak": hbm_peak,
-                    "unit": "GB/s", "frac": round(hbm_frac, 4), "traffic": traffic,
-                    "peak_source": hbm_src}
+        roofline = dict(hbm_part, traffic=traffic, alu=alu_part)
 
     extra = {}
     if rank == 0 and not args.quick:
@@ -279,7 +334,8 @@ def run_ours(args):
             A.solve(b, xf, l=l, interval=interval, rtol=RTOL, prec="fp32")
             xf.zero_()
             r = A.solve(b, xf, l=l, interval=interval, rtol=RTOL, prec="fp32")
-            err = float(np.linalg.norm(b_np - W.rhs(op, xf.cpu().numpy())) / np.linalg.norm(b_np))
+            xf_np = xf.cpu().numpy()
+            err = float(np.linalg.norm(b_np - W.rhs(op, xf_np)) / np.linalg.norm(b_np))
             byt = r.iters * passes_per_iter(l, "plcg") * 4 * n
             rec32 = profiled_record("plcg_3d_fp32_l1.json") if l == 1 else None
             mp[f"l{l}"] = {"iters": r.iters, "refinements": r.refinements,
@@ -290,6 +346,7 @@ def run_ours(args):
                            "hbm_gbs": round(byt / r.seconds / 1e9, 1),
                            "hbm_frac": round(byt / r.seconds / 1e9 / hbm_peak, 4),
                            "true_relres": err}
+            mp[f"l{l}"]["_x"] = xf_np
         xf = torch.zeros(n, dtype=torch.float64, device=dev)
         r = A.solve(b, xf, method="cg", rtol=RTOL, prec="fp32")
         mp["classic_cg"] = {"iters": r.iters, "time_to_rtol_s": round(r.seconds, 5),
@@ -297,7 +354,7 @@ def run_ours(args):
         extra["fp32_fp64corr"] = mp
 
     if rank == 0 and not args.quick and not args.no_configs:
-        extra["other_configs"] = other_configs(plcg, W, dev, hbm_peak)
+        extra["other_configs"] = other_configs(plcg, W, dev, hbm_peak, orc)
 
     # end to end through the host-pointer entry point (pinned host buffers)
     e2e = None
@@ -321,7 +378,14 @@ def run_ours(args):
         dist.barrier()
     if rank != 0:
         return
+    if "fp32_fp64corr" in extra:
+        for l in (1, 2):
+            ent = extra["fp32_fp64corr"][f"l{l}"]
+            orc.annotate(ent, f"3d.l{l}", ent.pop("_x"))
+    finish_oracle_errors(extra.get("other_configs"), orc)
+    orc.close()
     cpu = cpu_baseline(op, b_np, interval) if not args.quick else None
+    cpu_cfgs = cpu_baseline_configs() if not args.quick and not args.no_configs else None
     line = {
         "metric": METRIC, "value": round(value, 2), "unit": UNIT, "n_gpus": world,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(ms_per_step, 3),
@@ -336,6 +400,7 @@ def run_ours(args):
         "hbm_gbs": round(achieved_gbs, 1),
         "roofline": roofline,
         "cpu_baseline": cpu,
+        "cpu_baseline_configs": cpu_cfgs,
         "e2e": e2e,
         "gpu_launches": args.steps,
         "clocks": clk.summary(),
@@ -344,7 +409,7 @@ def run_ours(args):
     print(json.dumps(line), flush=True)
 
 
-def other_configs(plcg, W, dev, hbm_peak):
+def other_configs(plcg, W, dev, hbm_peak, orc):
     """Time-to-rtol on the other workloads: the 2D 100^2 Laplacian (FP64,
     latency-bound), the diagonal toy of Sec. 4 (100^2 and 2000^2), the 27-point heterogeneous CSR on 128^3 (FP32 with FP64
     correction; unpreconditioned and with Jacobi) and the batch of 4096 shifted 2D Poisson systems (FP32 with
@@ -386,13 +451,15 @@ def other_configs(plcg, W, dev, hbm_peak):
                        "us_per_iter": round(min(ts) / r.iters * 1e6, 2)}
         A.close()
         out[f"e3_diag_{N}_fp64_rtol1e-6"] = d
-    # ---- 27-point heterogeneous CSR 128^3, FP32 vectors/values, FP64 correction
+    # ---- 27-point heterogeneous CSR 128^3 (M = I as specified, and Jacobi):
+    # FP32 values and vectors with FP64 dots/scalars/refinement ("fp32"), and
+    # FP32 values under FP64 vectors ("fp32_matrix"); error of every result
+    # against the FP64 oracle on the same FP32-rounded operator
     c = W.config_hetero27(nx=128)
     op = c["op"]
     n, nnz = op["n"], int(op["rowptr"][-1])
     A = plcg.Matrix(op, prec="fp32")
     b = torch.tensor(c["b"], device=dev)
-    d = {"n": n, "nnz": nnz}
     jac = {"precond": "jacobi"}
     # Chebyshev shift intervals [0, 1.02 lambda_max] from plcg_estimate_interval
     # (30 CG steps on the GPU, once per operator; Sec. 2.2), for A and for
@@ -405,29 +472,43 @@ def other_configs(plcg, W, dev, hbm_peak):
         torch.cuda.synchronize()
         est[key] = {"interval": [0.0, round(1.02 * hi, 6)], "ritz": [lo, hi],
                     "seconds": round(time.perf_counter() - t0, 5)}
-    d["interval_estimates"] = est
-    for name, kw in (("plcg_l1", {"l": 1}), ("plcg_l2", {"l": 2}), ("plcg_l3", {"l": 3}),
-                     ("classic_cg", {"method": "cg"}),
-                     ("jacobi_plcg_l1", {"l": 1, **jac}), ("jacobi_plcg_l2", {"l": 2, **jac}),
-                     ("jacobi_plcg_l3", {"l": 3, **jac}), ("jacobi_classic_cg", {"method": "cg", **jac})):
-        # Jacobi: shifts on the spectrum of diag(A)^{-1} A; natural-norm rtol
-        interval = est["jacobi" if "precond" in kw else "none"]["interval"]
-        ts = []
-        for _ in range(2):
-            x = torch.zeros_like(b)
-            r = A.solve(b, x, interval=interval, rtol=1e-8, prec="fp32", max_restarts=64,
-                        check=False, **kw)
-            ts.append(r.seconds)
-        ll = kw.get("l", 1)
-        vec_passes = 10 if "method" in kw else 3 * (ll + 1) + 4
-        vec_passes += 2 if "precond" in kw else 0   # 1/a_gg and a_gg
-        byt = r.iters * (vec_passes * 4 * n + 8 * nnz + 8 * n)
-        d[name] = {"status": r.status, "iters": r.iters, "restarts": r.restarts,
-                   "refinements": r.refinements, "time_to_rtol_s": round(min(ts), 5),
-                   "hbm_gbs": round(byt / min(ts) / 1e9, 1),
-                   "hbm_frac": round(byt / min(ts) / 1e9 / hbm_peak, 4)}
+    cases = (("plcg_l1", {"l": 1}), ("plcg_l2", {"l": 2}), ("plcg_l3", {"l": 3}),
+             ("classic_cg", {"method": "cg"}),
+             ("jacobi_plcg_l1", {"l": 1, **jac}), ("jacobi_plcg_l2", {"l": 2, **jac}),
+             ("jacobi_plcg_l3", {"l": 3, **jac}), ("jacobi_classic_cg", {"method": "cg", **jac}))
+    # square-root breakdowns (Sec. 2.2) are frequent on this operator without a
+    # preconditioner -- the FP64 oracle itself restarts 50-100 times at l = 2, 3 --
+    # so every solve gets a restart budget that covers them
+    restarts = 1000
+    for name, kw in cases:
+        iv = est["jacobi" if "precond" in kw else "none"]["interval"]
+        orc.submit(f"h27.{name}", workload={"kind": "h27", "nx": 128}, method=kw.get("method", "plcg"),
+                   l=kw.get("l", 1), interval=tuple(iv), rtol=1e-8, precond=kw.get("precond"),
+                   max_restarts=restarts)
+    for prec in ("fp32", "fp32_matrix"):
+        d = {"n": n, "nnz": nnz, "prec": prec, "max_restarts": restarts}
+        if prec == "fp32":
+            d["interval_estimates"] = est
+        vb = 4 if prec == "fp32" else 8   # vector element bytes
+        for name, kw in cases:
+            interval = est["jacobi" if "precond" in kw else "none"]["interval"]
+            ts = []
+            for _ in range(2):
+                x = torch.zeros_like(b)
+                r = A.solve(b, x, interval=interval, rtol=1e-8, prec=prec, max_restarts=restarts,
+                            check=False, **kw)
+                ts.append(r.seconds)
+            ll = kw.get("l", 1)
+            vec_passes = 10 if "method" in kw else 3 * (ll + 1) + 4
+            jac_bytes = (vb + 4) if "precond" in kw else 0   # 1/a_gg (vector type) and a_gg (FP32)
+            byt = r.iters * (vec_passes * vb * n + 8 * nnz + 8 * n + jac_bytes * n)
+            d[name] = {"status": r.status, "iters": r.iters, "restarts": r.restarts,
+                       "refinements": r.refinements, "time_to_rtol_s": round(min(ts), 5),
+                       "hbm_gbs": round(byt / min(ts) / 1e9, 1),
+                       "hbm_frac": round(byt / min(ts) / 1e9 / hbm_peak, 4),
+                       "_x": x.cpu().numpy(), "_okey": f"h27.{name}"}
+        out["h27_csr_128_fp32" if prec == "fp32" else "h27_csr_128_fp32_matrix"] = d
     A.close()
-    out["h27_csr_128_fp32"] = d
     # ---- the same operator in the structured 27-point layout (diagonal + 13
     # forward weights per cell, no column indices), FP32, Jacobi
     c27 = W.config_hetero27_var27(nx=128)
@@ -447,7 +528,8 @@ def other_configs(plcg, W, dev, hbm_peak):
         byt = r.iters * (vec_passes * 4 * n + 14 * 4 * n)
         d[name] = {"status": r.status, "iters": r.iters, "restarts": r.restarts,
                    "time_to_rtol_s": round(min(ts), 5), "hbm_gbs": round(byt / min(ts) / 1e9, 1),
-                   "hbm_frac": round(byt / min(ts) / 1e9 / hbm_peak, 4)}
+                   "hbm_frac": round(byt / min(ts) / 1e9 / hbm_peak, 4),
+                   "_x": x.cpu().numpy(), "_okey": f"h27.{name}"}   # the same matrix as the CSR form
     A.close()
     out["h27_var27_128_fp32"] = d
     # ---- batched: 4096 shifted 2D Poisson systems, FP32 with FP64 correction
@@ -459,9 +541,14 @@ def other_configs(plcg, W, dev, hbm_peak):
     unknowns = sum(W.op_size(s_["op"]) for s_ in systems)
     d = {"systems": len(systems), "unknowns": unknowns}
     from paper_1905_06850_gb300 import autotune
+    sample = list(range(0, len(systems), len(systems) // 16))[:16]   # systems checked against the oracle
     for name, kw in (("plcg_l1", {"l": 1}), ("plcg_l2", {"l": 2}), ("plcg_l3", {"l": 3}),
                      ("classic_cg", {"method": "cg"})):
-        sched, _ = autotune.tune_batched(mats, bs, lo, hi, prec="fp32", rtol=1e-8, **kw)
+        for i in sample:
+            orc.submit(f"batched.{name}.{i}", workload={"kind": "batched", "count": len(systems), "index": i},
+                       method=kw.get("method", "plcg"), l=kw.get("l", 1), interval=systems[i]["interval"],
+                       rtol=1e-8)
+        sched, shape, _ = autotune.tune_batched(mats, bs, lo, hi, prec="fp32", rtol=1e-8, **kw)
         best = None
         for _ in range(2):
             xs = [torch.zeros_like(b_) for b_ in bs]
@@ -470,6 +557,7 @@ def other_configs(plcg, W, dev, hbm_peak):
             t = res[0].seconds
             best = t if best is None else min(best, t)
         its = np.array([r.iters for r in res])
+        lat = np.array([r.latency for r in res]) * 1e3   # launch start -> each system's result
         ok = sum(r.status == 0 for r in res)
         ll = kw.get("l", 1)
         vec_passes = 10 if "method" in kw else 3 * (ll + 1) + 4
@@ -477,11 +565,17 @@ def other_configs(plcg, W, dev, hbm_peak):
         d[name] = {"status": st, "converged": ok, "batch_time_s": round(best, 5),
                    "schedule": {"gang_size": sched[0], "large_work_factor": sched[1],
                                 "max_gang_fraction": sched[2]},
+                   "launch_shape": {"ctas_per_sm": shape[0], "rows_per_thread": shape[1]},
+                   "system_completion_ms": {"p50": round(float(np.percentile(lat, 50)), 3),
+                                            "p99": round(float(np.percentile(lat, 99)), 3),
+                                            "max": round(float(lat.max()), 3)},
                    "solves_per_s": round(len(systems) / best, 1),
                    "iters_mean": round(float(its.mean()), 1), "iters_max": int(its.max()),
                    "hbm_gbs": round(byt / best / 1e9, 1),
-                   "hbm_frac": round(byt / best / 1e9 / hbm_peak, 4)}
+                   "hbm_frac": round(byt / best / 1e9 / hbm_peak, 4),
+                   "_xs": {i: xs[i].cpu().numpy() for i in sample}, "_okey": f"batched.{name}"}
     autotune.set_schedule(0)
+    autotune.set_launch(0, 0)
     for m in mats:
         m.close()
     out["batched_4096_2d_fp32"] = d
@@ -575,6 +669,32 @@ def serving(plcg, W, dev):
             "note": "FP32 vectors with FP64 correction, p(1)-CG, rtol 1e-8; CSR sizes bucketed"}
 
 
+def finish_oracle_errors(configs, orc):
+    """Replaces the kept GPU solutions of the other workloads by their error
+    against the FP64 oracle (err_vs_oracle, with the oracle's iterations and
+    restarts; batched: the largest error over the sampled systems)."""
+    if not configs:
+        return
+    for d in configs.values():
+        if not isinstance(d, dict):
+            continue
+        for ent in d.values():
+            if not isinstance(ent, dict):
+                continue
+            if "_x" in ent:
+                orc.annotate(ent, ent.pop("_okey"), ent.pop("_x"))
+                if ent.get("oracle_iters"):
+                    ent["iters_vs_oracle"] = round(ent["iters"] / ent["oracle_iters"], 4)
+            elif "_xs" in ent:
+                key, errs = ent.pop("_okey"), []
+                for i, x in ent.pop("_xs").items():
+                    tmp = orc.annotate({}, f"{key}.{i}", x)
+                    if tmp.get("err_vs_oracle") is not None:
+                        errs.append(tmp["err_vs_oracle"])
+                ent["err_vs_oracle"] = max(errs) if errs else None
+                ent["err_vs_oracle_systems"] = len(errs)
+
+
 # ---------------------------------------------------------------- CPU oracle
 def cpu_baseline(op, b, interval, iters=12):
     """The FP64 oracle (serial C, as it stands) on a bounded sample of the same
@@ -587,6 +707,52 @@ def cpu_baseline(op, b, interval, iters=12):
     return {"value": round(r.iters / dt, 3), "unit": UNIT, "cores": 1, "kind": "oracle",
             "sample": f"{r.iters} iterations of p(1)-CG on the full {op['nx']}^3 system "
                       f"(serial C oracle, plus its 2 residual evaluations), {dt:.1f} s"}
+
+
+def cpu_baseline_configs():
+    """The serial FP64 oracle (as it stands) on the other workloads, each on a
+    bounded sample: the whole 2D 100^2 solve (p(1)-CG and CG, rtol 1e-6), 10
+    iterations of p(2)-CG on the 27-point heterogeneous CSR 128^3, and 16
+    systems of the 4096-system batch (p(1)-CG, rtol 1e-8) scaled to solves/s
+    of the batch's size mix."""
+    from oracle import oracle as O
+    from paper_1905_06850_gb300 import workloads as W
+    out = {"host_cores": os.cpu_count(), "cores_used": 1, "kind": "oracle"}
+    try:
+        with open("/proc/cpuinfo") as f:
+            models = [ln.split(":", 1)[1].strip() for ln in f if ln.lower().startswith(("model name", "cpu part"))]
+        out["cpu"] = models[0] if models else None
+    except OSError:
+        out["cpu"] = None
+    c = W.config_2d()
+    d = {}
+    for name, kw in (("plcg_l1", {"l": 1, "sigma": O.chebyshev_shifts(1, *c["interval"])}), ("classic_cg", {})):
+        t0 = time.perf_counter()
+        r = O.plcg(c["op"], c["b"], rtol=c["rtol"], dots_2l1=False, **kw) if kw else O.cg(c["op"], c["b"], rtol=c["rtol"])
+        dt = time.perf_counter() - t0
+        d[name] = {"iters": r.iters, "time_to_rtol_s": round(dt, 5), "iters_per_s": round(r.iters / dt, 1)}
+    out["2d_100_fp64_rtol1e-6"] = d
+    c = W.config_hetero27(nx=128)
+    sig = O.chebyshev_shifts(2, *c["interval"])
+    t0 = time.perf_counter()
+    r = O.plcg(c["op"], c["b"], l=2, sigma=sig, rtol=1e-8, maxit=10, dots_2l1=False)
+    dt = time.perf_counter() - t0
+    out["h27_csr_128"] = {"iters_per_s": round(r.iters / dt, 2), "sample": "10 iterations of p(2)-CG (FP64)",
+                          "seconds": round(dt, 2)}
+    systems = W.batched_systems(4096)
+    pick = list(range(0, 4096, 256))
+    t0 = time.perf_counter()
+    unknowns = 0
+    for i in pick:
+        s_ = systems[i]
+        O.plcg(s_["op"], s_["b"], l=1, sigma=O.chebyshev_shifts(1, *s_["interval"]), rtol=1e-8, dots_2l1=False)
+        unknowns += W.op_size(s_["op"])
+    dt = time.perf_counter() - t0
+    total = sum(W.op_size(s_["op"]) for s_ in systems)
+    out["batched_4096_2d"] = {"sample": f"{len(pick)} systems (every 256th), p(1)-CG, rtol 1e-8",
+                              "seconds": round(dt, 2),
+                              "solves_per_s_scaled": round(len(systems) / (dt * total / unknowns), 2)}
+    return out
 
 
 def run_reference(args):
@@ -634,6 +800,8 @@ def main():
     ap.add_argument("--prec", default="fp64", choices=["fp64", "fp32"])
     ap.add_argument("--l", type=int, default=L_HEAD)
     ap.add_argument("--no-configs", action="store_true", help="skip the other workloads")
+    ap.add_argument("--no-oracle-errors", action="store_true",
+                    help="skip the FP64 oracle solves that state each FP32 result's error")
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3

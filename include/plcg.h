@@ -51,9 +51,16 @@ typedef enum {
 
 typedef enum {
     PLCG_FP64 = 0,              /* vectors, dots and scalars in FP64            */
-    PLCG_FP32_FP64DOT = 1       /* FP32 vectors and matrix values; FP64 dot
+    PLCG_FP32_FP64DOT = 1,      /* FP32 vectors and matrix values; FP64 dot
                                    accumulation, scalar recurrences, true
                                    residual and an FP64 outer refinement loop   */
+    PLCG_FP32_MATRIX = 2        /* FP32 matrix values (a CSR or structured
+                                   27-point matrix created with
+                                   PLCG_FP32_FP64DOT) under FP64 vectors, dots
+                                   and scalars: the FP64 algorithm on the
+                                   FP32-rounded operator, with the matrix
+                                   traffic of the FP32 path (stencils:
+                                   PLCG_ERR_UNIMPL)                              */
 } plcg_precision;
 
 typedef enum {
@@ -122,7 +129,9 @@ typedef struct {
                                    both in the natural norm)                      */
     double seconds;             /* device time of the solve (CUDA events)        */
     double latency;             /* serving: seconds from plcg_submit to completion;
-                                   other entry points: = seconds                 */
+                                   plcg_solve_batched: seconds from the batch
+                                   launch's start to this system's completion
+                                   (device timer); other entry points: = seconds */
 } plcg_result;
 
 /* Fill *p with the defaults listed in plcg_params. */
@@ -286,6 +295,23 @@ void plcg_server_destroy(plcg_server *S);
  * PLCG_ERR_INVALID. */
 plcg_status plcg_set_batched_schedule(int gang_size, double large_work_factor,
                                       double max_gang_fraction);
+
+/* Measurement helper (the paper has no counterpart): the FP64 FMA
+ * throughput of the current device, in FLOP/s (2 per FMA), from a kernel of
+ * independent FMA chains on every resident thread (best of 3 timed launches
+ * after a warm-up, CUDA events).  It is the FP64 peak the FP64 sweeps are
+ * compared with.  Allocates and frees a small output buffer.
+ * Errors: PLCG_ERR_INVALID (NULL), PLCG_ERR_CUDA. */
+plcg_status plcg_measure_fp64_fma_rate(double *flops_per_s);
+
+/* Launch shape of plcg_solve_batched's FP32 solves (set by an autotuner;
+ * process-wide): the kernel variant whose registers are sized for
+ * ctas_per_sm (3 or 4) thread blocks per SM, and rows_per_thread (1, 2 or 4)
+ * row groups per thread in the one-block-per-system path.  0, 0 restores
+ * each method's default (4 blocks per SM; 4 row groups for p(1)-CG and
+ * classic CG, 1 for l >= 2).  FP64 batched solves always use the defaults.
+ * Errors: PLCG_ERR_INVALID. */
+plcg_status plcg_set_batched_launch(int ctas_per_sm, int rows_per_thread);
 
 /* Thread-local message describing the last failure in this thread. */
 const char *plcg_last_error(void);

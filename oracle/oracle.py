@@ -1,7 +1,8 @@
 """ctypes front end of the FP64 CPU oracle (``plcg_oracle.c``).
 
 THIS IS TEST INFRASTRUCTURE: only ``tests/``, ``__graft_entry__.smoke()`` and
-the CPU-baseline leg of ``bench.py`` may import it.  It does not import the
+``bench.py`` (its CPU-baseline leg, and the statement of each FP32 result's
+error against the FP64 oracle, outside every timed region) may import it.  It does not import the
 CUDA library or its binding, and the CUDA library does not import it.
 
 The operator is described by a plain dict, the same description the seeded
@@ -244,3 +245,40 @@ def plcg(op, b, x0=None, l=1, sigma=None, rtol=1e-8, maxit=100000, dots_2l1=True
         raise ValueError("need exactly l shifts")
     return _solve("orc_plcg", op, b, x0, l, sigma, rtol, maxit, dots_2l1, max_restarts,
                   trace_cap, precond)
+
+
+def refined(op, b, method="plcg", l=1, sigma=None, rtol=1e-8, floor=1e-4, maxit=100000,
+            dots_2l1=False, max_restarts=8) -> Result:
+    """The FP32 path's outer refinement loop (the paper has none; it is the
+    reading the FP32-with-FP64-correction path follows), restated in FP64
+    around the FP64 solvers: r = b - A x; stop when ||r|| < rtol ||b||;
+    otherwise solve A d = r from d = 0 to the absolute tolerance
+    max(floor ||r||, rtol ||b|| / 2) and set x += d.  Every inner solve
+    starts a new Krylov space (a restart in the sense of Sec. 2.2), so this
+    gives the iteration count of the FP32 path's segment structure without
+    its FP32 rounding.  M = I.  Returns a Result whose iters sums the inner
+    solves and whose segments counts them."""
+    x = np.zeros_like(np.asarray(b, dtype=np.float64))
+    nb = float(np.linalg.norm(b))
+    iters = segments = restarts = 0
+    while True:
+        r = np.asarray(b, dtype=np.float64) - apply(op, x)
+        rn = float(np.linalg.norm(r))
+        if rn < rtol * nb or iters >= maxit or nb == 0.0:
+            status = ORC_OK if (rn < rtol * nb or nb == 0.0) else ORC_ERR_MAXIT
+            return Result(x=x, status=status, iters=iters, spmvs=0, dots=0, restarts=restarts,
+                          segments=segments, recursive_relres=rn / nb if nb else 0.0,
+                          true_relres=rn / nb if nb else 0.0, trace={})
+        inner = max(floor * rn, 0.5 * rtol * nb) / rn
+        if method == "cg":
+            s = cg(op, r, rtol=inner, maxit=maxit - iters, max_restarts=max_restarts)
+        else:
+            s = plcg(op, r, l=l, sigma=sigma, rtol=inner, maxit=maxit - iters, dots_2l1=dots_2l1,
+                     max_restarts=max_restarts)
+        x = x + s.x
+        iters += s.iters
+        restarts += s.restarts
+        segments += 1
+        if s.status not in (ORC_OK, ORC_ERR_MAXIT):
+            return Result(x=x, status=s.status, iters=iters, spmvs=0, dots=0, restarts=restarts,
+                          segments=segments, recursive_relres=0.0, true_relres=rn / nb, trace={})

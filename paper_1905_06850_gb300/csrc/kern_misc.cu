@@ -4,8 +4,16 @@
 
 namespace plcg {
 
-const void *kernel_ptr(bool f32, int op, int vec, int l, bool cg, bool sc)
+const void *kernel_ptr(bool f32, int op, int vec, int l, bool cg, bool sc, bool c32)
 {
+    if (c32) {   // FP64 vectors, FP32 matrix values (stored-matrix operators only)
+        if (f32) return nullptr;
+        if (op == kOpCsr) return kptr_m_csr(l, cg, sc);
+        if (op == kOpCsrJacobi) return kptr_m_csrj(l, cg, sc);
+        if (op == kOpVar27) return kptr_m_v27(l, cg, sc);
+        if (op == kOpVar27Jacobi) return kptr_m_v27j(l, cg, sc);
+        return nullptr;
+    }
     if (!f32) {
         if (op == kOpCsr) return kptr_f64_csr(l, cg, sc);
         if (op == kOpCsrJacobi) return kptr_f64_csrj(l, cg, sc);
@@ -20,9 +28,10 @@ const void *kernel_ptr(bool f32, int op, int vec, int l, bool cg, bool sc)
     return vec == 4 ? kptr_f32_st4(l, cg) : kptr_f32_st1(l, cg);
 }
 
-const void *batched_kernel_ptr(bool f32, int l, bool cg)
+const void *batched_kernel_ptr(bool f32, int l, bool cg, int ctas_per_sm, int rows_per_thread)
 {
-    return f32 ? batched_kernel_ptr_f32(l, cg) : batched_kernel_ptr_f64(l, cg);
+    if (f32) return batched_kernel_ptr_f32(l, cg, ctas_per_sm, rows_per_thread);
+    return (ctas_per_sm == 0 && rows_per_thread == 0) ? batched_kernel_ptr_f64(l, cg) : nullptr;
 }
 
 // v[i] uniform in [-1, 1): SplitMix64 (Steele, Lea, Flood, "Fast splittable
@@ -158,4 +167,67 @@ cudaError_t launch_var27_zero_outside(bool f32, void *val, int64_t cstride, cons
     return cudaGetLastError();
 }
 
+
+// ------------------------------------------------------------------ FP64 rate
+// FP64 FMA throughput of the device: every thread runs 8 independent FMA
+// chains (x <- x * a + c), enough in flight per warp to keep the FP64 units
+// busy; the sums are stored so that no chain is dead code.
+__global__ void __launch_bounds__(256) fp64_fma_rate_kernel(double *out, int reps, double a, double c)
+{
+    double r[8];
+#pragma unroll
+    for (int k = 0; k < 8; ++k) r[k] = 1e-3 * (double)threadIdx.x + (double)k;
+    for (int i = 0; i < reps; ++i) {
+#pragma unroll
+        for (int k = 0; k < 8; ++k) r[k] = fma(r[k], a, c);
+    }
+    double s = 0.0;
+#pragma unroll
+    for (int k = 0; k < 8; ++k) s += r[k];
+    out[blockIdx.x * (size_t)blockDim.x + threadIdx.x] = s;
+}
+
 }  // namespace plcg
+
+extern "C" plcg_status plcg_measure_fp64_fma_rate(double *flops_per_s)
+{
+    using namespace plcg;
+    if (!flops_per_s) return PLCG_ERR_INVALID;
+    *flops_per_s = 0.0;
+    int dev = 0, sms = 0, per_sm = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess ||
+        cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess ||
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fp64_fma_rate_kernel, 256, 0) != cudaSuccess) {
+        set_last_error("plcg_measure_fp64_fma_rate: device query failed");
+        return PLCG_ERR_CUDA;
+    }
+    const int blocks = sms * per_sm, reps = 1 << 14;
+    double *out = nullptr;
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    cudaError_t e = cudaMalloc(&out, (size_t)blocks * 256 * sizeof(double));
+    if (e == cudaSuccess) e = cudaEventCreate(&e0);
+    if (e == cudaSuccess) e = cudaEventCreate(&e1);
+    float best = 0.f;
+    for (int t = 0; t < 4 && e == cudaSuccess; ++t) {   // the first launch warms up
+        e = cudaEventRecord(e0, 0);
+        if (e == cudaSuccess) {
+            fp64_fma_rate_kernel<<<blocks, 256>>>(out, reps, 0.9999999, 1e-7);
+            e = cudaGetLastError();
+        }
+        if (e == cudaSuccess) e = cudaEventRecord(e1, 0);
+        if (e == cudaSuccess) e = cudaEventSynchronize(e1);
+        float ms = 0.f;
+        if (e == cudaSuccess) e = cudaEventElapsedTime(&ms, e0, e1);
+        if (e == cudaSuccess && t > 0 && (best == 0.f || ms < best)) best = ms;
+    }
+    if (e0) cudaEventDestroy(e0);
+    if (e1) cudaEventDestroy(e1);
+    if (out) cudaFree(out);
+    if (e != cudaSuccess || !(best > 0.f)) {
+        set_last_error(std::string("plcg_measure_fp64_fma_rate: ") + cudaGetErrorString(e));
+        return PLCG_ERR_CUDA;
+    }
+    *flops_per_s = 2.0 * 8.0 * reps * (double)blocks * 256.0 / (best * 1e-3);
+    return PLCG_OK;
+}
+

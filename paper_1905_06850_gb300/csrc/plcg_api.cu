@@ -424,6 +424,10 @@ static plcg_status build_solve(const plcg_matrix *A, const double *b, double *x,
     const bool jac = prm->precond == PLCG_PRECOND_JACOBI && A->kind != kOpStencil;
     const int op = !jac ? A->kind : (A->kind == kOpCsr) ? (int)kOpCsrJacobi : (int)kOpVar27Jacobi;
     const bool f32 = sizeof(T) == 4;
+    // FP64 vectors over FP32 matrix values (the matrix was created with FP32 values)
+    const bool c32 = prm->prec == PLCG_FP32_MATRIX;
+    if (c32 && f32) return fail(PLCG_ERR_INVALID, "internal: FP32 matrix path with FP32 vectors");
+    const unsigned value_bytes = c32 ? 4u : (unsigned)sizeof(T);
     int vec = 1;
     if (op == kOpStencil) {
         const int want = 16 / (int)sizeof(T);
@@ -432,12 +436,12 @@ static plcg_status build_solve(const plcg_matrix *A, const double *b, double *x,
     // FP64 p(1)-CG on 2^19 rows or more: the scaled-basis kernel (two FP64
     // multiplies per row fewer; below that the longer scalar step costs more)
     const bool sc = !f32 && !cg && l == 1 && n >= (int64_t(1) << 19);
-    const void *func = kernel_ptr(f32, op, vec, cg ? 0 : l, cg, sc);
-    if (!func) return fail(PLCG_ERR_UNIMPL, "no kernel for prec=%d op=%d vec=%d l=%d", (int)f32, op, vec, l);
+    const void *func = kernel_ptr(f32, op, vec, cg ? 0 : l, cg, sc, c32);
+    if (!func) return fail(PLCG_ERR_UNIMPL, "no kernel for prec=%d op=%d vec=%d l=%d", prm->prec, op, vec, l);
     // CSR kernels stage each unit's entries in dynamic shared memory (FP64
     // classic CG excepted, see cg_body); the 27-point p(l)-CG kernels stage
     // coefficient and z tiles
-    const unsigned dsmem = (op_is_csr(op) && (!cg || f32)) ? csr_stage_bytes((unsigned)sizeof(T))
+    const unsigned dsmem = (op_is_csr(op) && (!cg || f32)) ? csr_stage_bytes(value_bytes)
                          : (op_is_var27(op) && !cg && f32)
                              ? v27_tile_bytes((unsigned)sizeof(T), l, op_is_jacobi(op)) : 0u;
     if (dsmem) {
@@ -511,7 +515,9 @@ static plcg_status build_solve(const plcg_matrix *A, const double *b, double *x,
         a.cf_hi = a.cf_lo + A->val_bytes;
     }
     if (jac) {
-        a.csr.dinv = A->jdinv;
+        // 1 / a_rr in the vector type (FP64 vectors: the FP64 inverse), a_rr
+        // in the stored value type
+        a.csr.dinv = f32 ? A->jdinv : static_cast<const void *>(A->jdinv64);
         a.csr.diag = A->jdiag;
         a.dinv64 = A->jdinv64;
     }
@@ -646,10 +652,17 @@ static plcg_status check_params(const plcg_matrix *A, const plcg_params *p)
     if (p->maxit < 0 || p->maxit > (int64_t(1) << 30))
         return fail(PLCG_ERR_INVALID, "maxit must be in [0, 2^30]");
     if (p->max_restarts < 0) return fail(PLCG_ERR_INVALID, "max_restarts must be >= 0");
-    if (p->prec != PLCG_FP64 && p->prec != PLCG_FP32_FP64DOT)
+    if (p->prec != PLCG_FP64 && p->prec != PLCG_FP32_FP64DOT && p->prec != PLCG_FP32_MATRIX)
         return fail(PLCG_ERR_INVALID, "unknown precision %d", p->prec);
-    if (A->kind != kOpStencil && p->prec != A->csr_prec)
+    if (p->prec == PLCG_FP32_MATRIX) {
+        if (A->kind == kOpStencil)
+            return fail(PLCG_ERR_UNIMPL, "PLCG_FP32_MATRIX: a stencil operator stores no matrix values");
+        if (A->csr_prec != PLCG_FP32_FP64DOT)
+            return fail(PLCG_ERR_INVALID, "PLCG_FP32_MATRIX needs a matrix created with FP32 values "
+                                          "(PLCG_FP32_FP64DOT)");
+    } else if (A->kind != kOpStencil && p->prec != A->csr_prec) {
         return fail(PLCG_ERR_INVALID, "matrix was created for precision %d", A->csr_prec);
+    }
     if (p->prec == PLCG_FP32_FP64DOT && !(p->inner_rtol_floor > 0.0 && p->inner_rtol_floor < 1.0))
         return fail(PLCG_ERR_INVALID, "inner_rtol_floor must be in (0, 1)");
     if (p->precond != PLCG_PRECOND_NONE && p->precond != PLCG_PRECOND_JACOBI)
@@ -683,7 +696,7 @@ extern "C" plcg_status plcg_solve(plcg_matrix *A, const double *b, double *x,
     if (prm->method == PLCG_METHOD_PLCG) resolve_shifts(A, prm, prm->lmin, prm->lmax, sigma);
     std::lock_guard<std::mutex> lock(A->mu);
     CUDA_TRY(cudaSetDevice(A->device));
-    if (prm->prec == PLCG_FP64) return run_solve<double>(A, b, x, prm, sigma, res);
+    if (prm->prec != PLCG_FP32_FP64DOT) return run_solve<double>(A, b, x, prm, sigma, res);
     return run_solve<float>(A, b, x, prm, sigma, res);
 }
 
@@ -744,7 +757,7 @@ plcg_status plcg::solve_stencil_fixed(const plcg_stencil_desc *d, const double *
     CUDA_TRY(cudaDeviceGetAttribute(&A.num_sms, cudaDevAttrMultiProcessorCount, A.device));
     double sigma[kMaxL] = {0};
     if (prm->method == PLCG_METHOD_PLCG) resolve_shifts(&A, prm, prm->lmin, prm->lmax, sigma);
-    if (prm->prec == PLCG_FP64) return run_solve_fixed<double>(&A, b, x, prm, sigma, base, cap, who, res);
+    if (prm->prec != PLCG_FP32_FP64DOT) return run_solve_fixed<double>(&A, b, x, prm, sigma, base, cap, who, res);
     return run_solve_fixed<float>(&A, b, x, prm, sigma, base, cap, who, res);
 }
 
@@ -826,7 +839,7 @@ extern "C" plcg_status plcg_estimate_interval(plcg_matrix *A, const plcg_params 
     }
     plcg_result res{};
     const double nosig[kMaxL] = {0};   // classic CG uses no shifts
-    st = (p.prec == PLCG_FP64) ? run_solve<double>(A, A->b_dev, A->x_dev, &p, nosig, &res, trace, steps)
+    st = (p.prec != PLCG_FP32_FP64DOT) ? run_solve<double>(A, A->b_dev, A->x_dev, &p, nosig, &res, trace, steps)
                                : run_solve<float>(A, A->b_dev, A->x_dev, &p, nosig, &res, trace, steps);
     std::vector<double> t(2 * (size_t)steps, 0.0);
     e = cudaMemcpy(t.data(), trace, t.size() * sizeof(double), cudaMemcpyDeviceToHost);
@@ -881,6 +894,24 @@ BatchCtx g_batch[64];
 static int g_batch_G = 8;
 static double g_batch_beta = 1.0;
 static double g_batch_gang_frac = 0.5;
+// Launch shape of FP32 batched solves (0, 0: each method's default).
+static int g_batch_ctas_per_sm = 0;
+static int g_batch_rows_per_thread = 0;
+
+extern "C" plcg_status plcg_set_batched_launch(int ctas_per_sm, int rows_per_thread)
+{
+    if (ctas_per_sm == 0 && rows_per_thread == 0) {
+        g_batch_ctas_per_sm = g_batch_rows_per_thread = 0;
+        return PLCG_OK;
+    }
+    if ((ctas_per_sm != 3 && ctas_per_sm != 4) ||
+        (rows_per_thread != 1 && rows_per_thread != 2 && rows_per_thread != 4))
+        return fail(PLCG_ERR_INVALID, "batched launch shape: need 3 or 4 CTAs per SM and 1, 2 or 4 "
+                                      "row groups per thread (or 0, 0)");
+    g_batch_ctas_per_sm = ctas_per_sm;
+    g_batch_rows_per_thread = rows_per_thread;
+    return PLCG_OK;
+}
 
 extern "C" plcg_status plcg_set_batched_schedule(int gang_size, double large_work_factor,
                                                  double max_gang_fraction)
@@ -921,7 +952,9 @@ static plcg_status run_batched(int count, plcg_matrix *const *A, const double *c
     const bool f32 = sizeof(T) == 4;
     const bool cg = prm->method == PLCG_METHOD_CG;
     const int l = cg ? 1 : prm->l;
-    const void *func = batched_kernel_ptr(f32, l, cg);
+    // the tuned launch shape applies to FP32 solves; FP64 uses the defaults
+    const void *func = f32 ? batched_kernel_ptr(f32, l, cg, g_batch_ctas_per_sm, g_batch_rows_per_thread)
+                           : batched_kernel_ptr(f32, l, cg);
     if (!func) return fail(PLCG_ERR_UNIMPL, "plcg_solve_batched: l must be 1..4");
     cudaStream_t stream = A[0]->stream;
     int dev = A[0]->device;
@@ -1070,13 +1103,16 @@ static plcg_status run_batched(int count, plcg_matrix *const *A, const double *c
     ba.gws_stride = gws_stride;
     ba.ws = ctx.mem + o_ws;
     ba.ws_stride = ws_stride;
+    ba.t0 = reinterpret_cast<unsigned long long *>(ctx.mem + o_ctr + 192);
     ba.proto = proto;
     void *args[] = {&ba};
     CUDA_TRY(cudaEventRecord(ctx.ev0, stream));
     CUDA_TRY(cudaLaunchCooperativeKernel(func, dim3(P), dim3(kBlock), args, 0, stream));
     CUDA_TRY(cudaEventRecord(ctx.ev1, stream));
     std::vector<DevResult> hres(count);
+    unsigned long long t0 = 0;
     CUDA_TRY(cudaMemcpyAsync(hres.data(), dres, sizeof(DevResult) * count, cudaMemcpyDeviceToHost, stream));
+    CUDA_TRY(cudaMemcpyAsync(&t0, ba.t0, sizeof(t0), cudaMemcpyDeviceToHost, stream));
     CUDA_TRY(cudaStreamSynchronize(stream));
     float ms = 0.f;
     CUDA_TRY(cudaEventElapsedTime(&ms, ctx.ev0, ctx.ev1));
@@ -1092,7 +1128,8 @@ static plcg_status run_batched(int count, plcg_matrix *const *A, const double *c
             results[i].recursive_relres = o.recursive_relres;
             results[i].true_relres = o.true_relres;
             results[i].seconds = ms * 1e-3;
-            results[i].latency = ms * 1e-3;
+            // from the launch's start to this system's result (device timer)
+            results[i].latency = o.t_end_ns >= t0 ? (double)(o.t_end_ns - t0) * 1e-9 : 0.0;
         }
         if (first == PLCG_OK && o.status != PLCG_OK) first = (plcg_status)o.status;
     }
@@ -1241,7 +1278,7 @@ static void server_loop(plcg_server *S)
             S->free_slots.pop_back();
             S->used += q->bytes;
             S->sm_used += q->sm_share;
-            const plcg_status st = (q->prm.prec == PLCG_FP64) ? server_launch<double>(S, *q)
+            const plcg_status st = (q->prm.prec != PLCG_FP32_FP64DOT) ? server_launch<double>(S, *q)
                                                               : server_launch<float>(S, *q);
             if (st != PLCG_OK) {
                 server_finish(S, q, st);
@@ -1336,7 +1373,7 @@ extern "C" plcg_status plcg_submit(plcg_server *S, plcg_matrix *A, const double 
     int64_t P = 0;
     int per_sm = 0;
     size_t bytes = 0, o_out = 0;
-    if (prm->prec == PLCG_FP64) {
+    if (prm->prec != PLCG_FP32_FP64DOT) {
         SolveArgs<double> a;
         st = build_solve<double>(A, b, x, &q->prm, q->sigma, 0, nullptr, &a, &func, &P, &per_sm, &bytes, &o_out);
     } else {
@@ -1348,7 +1385,7 @@ extern "C" plcg_status plcg_submit(plcg_server *S, plcg_matrix *A, const double 
     q->P = std::min<int64_t>(P, cap);
     q->sm_share = (double)q->P / per_sm;
     // recompute the byte count for the capped grid (partials scale with P)
-    if (prm->prec == PLCG_FP64) {
+    if (prm->prec != PLCG_FP32_FP64DOT) {
         SolveArgs<double> a;
         st = build_solve<double>(A, b, x, &q->prm, q->sigma, (int)q->P, nullptr, &a, &func, &P, &per_sm, &bytes, &o_out);
     } else {

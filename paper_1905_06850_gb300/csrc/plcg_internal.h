@@ -38,6 +38,7 @@ struct DevResult {
     long long refinements;
     double recursive_relres;
     double true_relres;
+    unsigned long long t_end_ns;   // device global timer when the result was written
 };
 
 // Division of a 32-bit unsigned x < 2^31 by an invariant d >= 1 with one
@@ -200,6 +201,7 @@ struct BatchArgs {
     size_t gws_stride;
     char *ws;                 // per-CTA workspaces (one-CTA path)
     size_t ws_stride;
+    unsigned long long *t0;   // device global timer at the launch's start (block 0)
     SolveArgs<T> proto;
 };
 

@@ -11,12 +11,17 @@
 namespace plcg {
 
 // Address of the persistent solver for (FP32 path?, operator, vector width,
-// pipeline length l, classic CG?); nullptr when not instantiated.
-const void *kernel_ptr(bool f32, int op, int vec, int l, bool cg, bool sc = false);
+// pipeline length l, classic CG?, scaled bases?, FP32 matrix values under
+// FP64 vectors?); nullptr when not instantiated.
+const void *kernel_ptr(bool f32, int op, int vec, int l, bool cg, bool sc = false, bool c32 = false);
 
-// Address of the batched kernel for p(l)-CG (l = 1..4) or classic CG.
-const void *batched_kernel_ptr(bool f32, int l, bool cg);
-const void *batched_kernel_ptr_f32(int l, bool cg);
+// Address of the batched kernel for p(l)-CG (l = 1..4) or classic CG in a
+// launch shape (CTAs per SM the registers are sized for, row groups per
+// thread; 0, 0 = the method's default; other shapes exist for FP32 only:
+// 3 or 4 CTAs per SM with 1, 2 or 4 row groups); nullptr when absent.
+const void *batched_kernel_ptr(bool f32, int l, bool cg, int ctas_per_sm = 0, int rows_per_thread = 0);
+const void *batched_kernel_ptr_f32(int l, bool cg, int ctas_per_sm, int rows_per_thread);
+const void *batched_kernel_ptr_f32_3(int l, bool cg, int rows_per_thread);
 const void *batched_kernel_ptr_f64(int l, bool cg);
 
 // Per-translation-unit getters used by kernel_ptr.
@@ -32,6 +37,10 @@ const void *kptr_f64_v27(int l, bool cg, bool sc);
 const void *kptr_f32_v27(int l, bool cg);
 const void *kptr_f64_v27j(int l, bool cg, bool sc);
 const void *kptr_f32_v27j(int l, bool cg);
+const void *kptr_m_csr(int l, bool cg, bool sc);
+const void *kptr_m_csrj(int l, bool cg, bool sc);
+const void *kptr_m_v27(int l, bool cg, bool sc);
+const void *kptr_m_v27j(int l, bool cg, bool sc);
 
 // Sets the thread-local message returned by plcg_last_error().
 void set_last_error(const std::string &msg);

@@ -47,6 +47,13 @@ __device__ __forceinline__ void red_release_add_u32(unsigned *p, unsigned v)
 
 __device__ __forceinline__ int ld_volatile(const int *p) { return *(volatile const int *)p; }
 
+__device__ __forceinline__ unsigned long long global_timer_ns()
+{
+    unsigned long long t;
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+    return t;
+}
+
 // Bounded grid-wide barrier.  Every CTA adds 1 to *bar; the barrier of epoch
 // e is passed when *bar reaches e * gridDim.x.  Returns false when the poll
 // bound ran out (the CTA then sets the abort flag) or another CTA aborted;
@@ -351,6 +358,30 @@ struct LdFirst {          // value = a[g] (CG first step, p_0 = r_0)
 };
 
 // ------------------------------------------------------------------------
+// Stored matrix values into the arithmetic type.  GB300 converts between
+// FP32 and FP64 on its narrow FP64 units, which the FP64 sweeps already keep
+// busy, so an FP32 value is widened to FP64 with integer operations: the
+// sign, the exponent rebiased by 1023 - 127 = 896 and the 23 mantissa bits
+// placed in the two 32-bit halves of the double.  Exact for zeros and every
+// normal FP32 value; FP32 subnormals (below 2^-126) read as signed zero.
+// ------------------------------------------------------------------------
+__device__ __forceinline__ double widen_f32(float f)
+{
+    const uint32_t u = __float_as_uint(f);
+    const bool normal = (u & 0x7f800000u) != 0u;
+    const uint32_t hi = (u & 0x80000000u) | (normal ? ((u & 0x7fffffffu) >> 3) + (896u << 20) : 0u);
+    const uint32_t lo = normal ? (u << 29) : 0u;
+    return __hiloint2double((int)hi, (int)lo);
+}
+
+template <typename V, typename C>
+__device__ __forceinline__ V coef_cast(C c)
+{
+    if constexpr (sizeof(V) == 8 && sizeof(C) == 4) return widen_f32(c);
+    else return (V)c;
+}
+
+// ------------------------------------------------------------------------
 // Operators.  apply() returns the centre values c and w = (A z) for the VEC
 // rows g0 .. g0+VEC-1 (stencil: nx % VEC == 0, so they share y and z).
 // ------------------------------------------------------------------------
@@ -427,7 +458,7 @@ __device__ __forceinline__ V var27_row(const StencilDesc &st, const C *coef, int
     const uint32_t zc = (__umulhi(line, st.dny.m) + line) >> st.dny.s;
     const uint32_t y = line - zc * ny;
     const bool xm = x > 0, xp = x + 1 < nx, ym = y > 0, yp = y + 1 < ny, zm = zc > 0, zp = zc + 1 < nz;
-    V s = (V)__ldg(coef + g) * ld.one(g);
+    V s = coef_cast<V>(__ldg(coef + g)) * ld.one(g);
 #pragma unroll
     for (int k = 0; k < 13; ++k) {
         const int dz = v27_dz(k), dy = v27_dy(k), dx = v27_dx(k);
@@ -437,8 +468,8 @@ __device__ __forceinline__ V var27_row(const StencilDesc &st, const C *coef, int
         const bool bwd = (dx > 0 ? xm : dx < 0 ? xp : true) && (dy > 0 ? ym : dy < 0 ? yp : true) &&
                          (dz > 0 ? zm : true);
         const C *ck = coef + (size_t)(1 + k) * n;
-        if (fwd) s = fma((V)__ldg(ck + g), ld.one(g + off), s);
-        if (bwd) s = fma((V)__ldg(ck + (g - off)), ld.one(g - off), s);
+        if (fwd) s = fma(coef_cast<V>(__ldg(ck + g)), ld.one(g + off), s);
+        if (bwd) s = fma(coef_cast<V>(__ldg(ck + (g - off))), ld.one(g - off), s);
     }
     return s;
 }
@@ -450,7 +481,7 @@ __device__ __forceinline__ V csr_row(const CsrDesc &A, const Ld &ld, uint32_t ro
     const C *val = static_cast<const C *>(A.val);
     const int64_t e0 = __ldg(A.rowptr + row), e1 = __ldg(A.rowptr + row + 1);
     V s = V(0);
-    for (int64_t e = e0; e < e1; ++e) s = fma((V)__ldg(val + e), ld.one(__ldg(A.col + e)), s);
+    for (int64_t e = e0; e < e1; ++e) s = fma(coef_cast<V>(__ldg(val + e)), ld.one(__ldg(A.col + e)), s);
     return s;
 }
 
@@ -463,7 +494,7 @@ __device__ __forceinline__ V csr_row_staged(const CsrDesc &A, const int32_t *sco
     const uint32_t k0 = (uint32_t)(__ldg(A.rowptr + row) - e0s);
     const uint32_t k1 = (uint32_t)(__ldg(A.rowptr + row + 1) - e0s);
     V s = V(0);
-    for (uint32_t k = k0; k < k1; ++k) s = fma((V)sval[k], ld.one((uint32_t)scol[k]), s);
+    for (uint32_t k = k0; k < k1; ++k) s = fma(coef_cast<V>(sval[k]), ld.one((uint32_t)scol[k]), s);
     return s;
 }
 
@@ -1307,7 +1338,7 @@ struct DotAcc {
 // preconditioner the natural norms r^T M^{-1} r and b^T M^{-1} b (Sec. 2.2,
 // "Residual norm in p(l)-CG").  Units of kBlock * V64 rows.
 // ------------------------------------------------------------------------
-template <typename T, int VEC, int OP, class Grp>
+template <typename T, int VEC, int OP, class Grp, typename C = T>
 __device__ void residual_sweep(const SolveArgs<T> &a, Smem<T> &s, const Grp &grp)
 {
     constexpr int V64 = (VEC >= 2) ? 2 : 1;
@@ -1325,10 +1356,10 @@ __device__ void residual_sweep(const SolveArgs<T> &a, Smem<T> &s, const Grp &grp
             stencil_apply<double, V64>(a.st, cC, cO, ld, g0, c, w);
         } else if constexpr (op_is_var27(OP)) {
             c[0] = a.x[g0];
-            w[0] = var27_row<double, T>(a.st, static_cast<const T *>(a.csr.val), a.csr.stride, ld, g0);
+            w[0] = var27_row<double, C>(a.st, static_cast<const C *>(a.csr.val), a.csr.stride, ld, g0);
         } else {
             c[0] = a.x[g0];
-            w[0] = csr_row<double, T>(a.csr, ld, g0);
+            w[0] = csr_row<double, C>(a.csr, ld, g0);
         }
         vldg<double, V64>(a.b + g0, bv);
         double rv[V64];
@@ -1363,6 +1394,7 @@ __device__ __forceinline__ void write_result(const SolveArgs<T> &a, int status, 
     o->refinements = refinements;
     o->recursive_relres = (normb > 0.0) ? recres / normb : 0.0;
     o->true_relres = (normb > 0.0) ? last_rn / normb : 0.0;
+    o->t_end_ns = global_timer_ns();
 }
 
 // K5 operand of dot q in the steady state (l+1 dots, i >= l+1): the same
@@ -1378,7 +1410,7 @@ __device__ __forceinline__ constexpr int steady_dot_src(int q)
 // ------------------------------------------------------------------------
 // p(l)-CG: a whole solve on one group (grid or CTA).
 // ------------------------------------------------------------------------
-template <typename T, int L, int VEC, int OP, class Grp, int RPT = 1, bool SC = false>
+template <typename T, int L, int VEC, int OP, class Grp, int RPT = 1, bool SC = false, typename CT = T>
 __device__ void plcg_body(const SolveArgs<T> &a, Smem<T> &s, Grp &grp)
 {
     constexpr int UNIT = kBlock * VEC;
@@ -1391,7 +1423,7 @@ __device__ void plcg_body(const SolveArgs<T> &a, Smem<T> &s, Grp &grp)
     // shared memory (one contiguous range per unit) before its rows are read
     constexpr bool kStage = op_is_csr(OP) && std::is_same<Grp, GridGroup<T>>::value && RPT == 1;
     extern __shared__ __align__(128) unsigned char plcg_dsm[];
-    CsrStage<T> stage(plcg_dsm);
+    CsrStage<CT> stage(plcg_dsm);
     if constexpr (kStage) {
         stage.init();
         __syncthreads();
@@ -1400,7 +1432,7 @@ __device__ void plcg_body(const SolveArgs<T> &a, Smem<T> &s, Grp &grp)
     // coefficients and z^(l) lines are staged as a shared-memory tile (the
     // FP64 sweep is bound by the FP64 units and measured faster without)
     constexpr bool kTile = op_is_var27(OP) && std::is_same<Grp, GridGroup<T>>::value && RPT == 1 &&
-                           sizeof(T) == 4;
+                           sizeof(T) == 4 && sizeof(CT) == 4;
     constexpr int kNV = kTile ? v27_vec_slots(L, op_is_jacobi(OP)) : 0;
     Var27Tile<T, kNV> tile(plcg_dsm);
     if constexpr (kTile) {
@@ -1446,7 +1478,7 @@ __device__ void plcg_body(const SolveArgs<T> &a, Smem<T> &s, Grp &grp)
 
     for (;;) {
         // ---- true residual r = b - A x and its norm (Algorithm 1 initialization / the final check)
-        residual_sweep<T, VEC, OP>(a, s, grp);
+        residual_sweep<T, VEC, OP, Grp, CT>(a, s, grp);
         grp.put_norms(a, s);
         spmvs++;
         PLCG_SYNC();
@@ -1631,7 +1663,7 @@ __device__ void plcg_body(const SolveArgs<T> &a, Smem<T> &s, Grp &grp)
                     if (j == 2 * L + 1) return pvec;
                     if (j == 2 * L + 2) return xi;
                     if (j == 2 * L + 3) return static_cast<const T *>(csr.dinv);
-                    return static_cast<const T *>(csr.diag);
+                    return reinterpret_cast<const T *>(static_cast<const CT *>(csr.diag));
                 };
                 // stage unit uu (if it exists) in buffer bb
                 auto tile_issue = [&](int bb, uint32_t uu) {
@@ -1686,14 +1718,14 @@ __device__ void plcg_body(const SolveArgs<T> &a, Smem<T> &s, Grp &grp)
                         if constexpr (kStage) {   // K1 operands
                             if (stg) {
                                 c[r][0] = C.zl_cur[g0[r]];
-                                nb[r][0] = csr_row_staged<T, T>(csr, stage.col, stage.val, e0s, Ld1<T>{C.zl_cur}, g0[r]);
+                                nb[r][0] = csr_row_staged<T, CT>(csr, stage.col, stage.val, e0s, Ld1<T>{C.zl_cur}, g0[r]);
                             } else {
-                                op_parts<T, T, VEC, OP>(st, csr, Ld1<T>{C.zl_cur}, g0[r], c[r], nb[r]);
+                                op_parts<T, CT, VEC, OP>(st, csr, Ld1<T>{C.zl_cur}, g0[r], c[r], nb[r]);
                             }
                         } else if constexpr (kTile) {
                             // K1 from the tile after the loads below
                         } else {
-                            op_parts<T, T, VEC, OP>(st, csr, Ld1<T>{C.zl_cur}, g0[r], c[r], nb[r]);
+                            op_parts<T, CT, VEC, OP>(st, csr, Ld1<T>{C.zl_cur}, g0[r], c[r], nb[r]);
                         }
                         if constexpr (kTile) {
                             if (SV && stg) {   // the steady sweep's vectors, from the tile
@@ -1714,12 +1746,12 @@ __device__ void plcg_body(const SolveArgs<T> &a, Smem<T> &s, Grp &grp)
                             }
                             if constexpr (op_is_jacobi(OP)) {
                                 c[r][0] = __ldg(static_cast<const T *>(csr.dinv) + g0[r]);   // 1 / a_gg for now
-                                dg[r] = __ldg(static_cast<const T *>(csr.diag) + g0[r]);
+                                dg[r] = coef_cast<T>(__ldg(static_cast<const CT *>(csr.diag) + g0[r]));
                             }
                         } else if constexpr (op_is_jacobi(OP)) {
                             // K1 with M = diag(A): z^(l)_{i+1} is built from M^{-1} A z^(l)_i
                             nb[r][0] *= __ldg(static_cast<const T *>(csr.dinv) + g0[r]);
-                            dg[r] = __ldg(static_cast<const T *>(csr.diag) + g0[r]);
+                            dg[r] = coef_cast<T>(__ldg(static_cast<const CT *>(csr.diag) + g0[r]));
                         }
                         if (rec) {
                             vld<T, VEC>(C.zl_prev + g0[r], zp[r]);
@@ -1750,7 +1782,7 @@ __device__ void plcg_body(const SolveArgs<T> &a, Smem<T> &s, Grp &grp)
                                 nb[r][0] = tile.template row<T>(tb, (int)(g0[r] - u * usw), &zc);
                                 c[r][0] = zc;
                             } else {
-                                op_parts<T, T, VEC, OP>(st, csr, Ld1<T>{C.zl_cur}, g0[r], c[r], nb[r]);
+                                op_parts<T, CT, VEC, OP>(st, csr, Ld1<T>{C.zl_cur}, g0[r], c[r], nb[r]);
                             }
                             if constexpr (op_is_jacobi(OP)) nb[r][0] *= di;
                         }
@@ -1892,7 +1924,7 @@ finish:
 // path and a.rc (FP32) on the FP32 path, whose inner iterate is the ring's
 // third vector.
 // ------------------------------------------------------------------------
-template <typename T, int VEC, int OP, class Grp, int RPT = 1>
+template <typename T, int VEC, int OP, class Grp, int RPT = 1, typename CT = T>
 __device__ void cg_body(const SolveArgs<T> &a, Smem<T> &s, Grp &grp)
 {
     constexpr int UNIT = kBlock * VEC;
@@ -1915,7 +1947,7 @@ __device__ void cg_body(const SolveArgs<T> &a, Smem<T> &s, Grp &grp)
     constexpr bool kStage = op_is_csr(OP) && std::is_same<Grp, GridGroup<T>>::value && RPT == 1 &&
                             sizeof(T) == 4;
     extern __shared__ __align__(128) unsigned char plcg_dsm[];
-    CsrStage<T> stage(plcg_dsm);
+    CsrStage<CT> stage(plcg_dsm);
     if constexpr (kStage) {
         stage.init();
         __syncthreads();
@@ -1935,7 +1967,7 @@ __device__ void cg_body(const SolveArgs<T> &a, Smem<T> &s, Grp &grp)
     } while (0)
 
     for (;;) {
-        residual_sweep<T, VEC, OP>(a, s, grp);
+        residual_sweep<T, VEC, OP, Grp, CT>(a, s, grp);
         grp.put_norms(a, s);
         spmvs++;
         CG_SYNC();
@@ -1980,7 +2012,7 @@ __device__ void cg_body(const SolveArgs<T> &a, Smem<T> &s, Grp &grp)
                 for (int v = 0; v < VEC; ++v) {
                     if constexpr (op_is_jacobi(OP)) {
                         z[v] = (T)(a.r[g0 + v] * __ldg(a.dinv64 + g0 + v));
-                        zm[v] = z[v] * __ldg(static_cast<const T *>(csr.diag) + g0 + v);
+                        zm[v] = z[v] * coef_cast<T>(__ldg(static_cast<const CT *>(csr.diag) + g0 + v));
                     } else {
                         z[v] = (T)a.r[g0 + v];
                         zm[v] = z[v];
@@ -2037,16 +2069,16 @@ __device__ void cg_body(const SolveArgs<T> &a, Smem<T> &s, Grp &grp)
                         if (k == 0) {
                             const LdFirst<T> ld{rc};
                             c[r][0] = ld.one(g0[r]);
-                            w[r][0] = csr_row_staged<T, T>(csr, stage.col, stage.val, e0s, ld, g0[r]);
+                            w[r][0] = csr_row_staged<T, CT>(csr, stage.col, stage.val, e0s, ld, g0[r]);
                         } else {
                             const LdAxpy<T> ld{rc, po, (T)beta};
                             c[r][0] = ld.one(g0[r]);
-                            w[r][0] = csr_row_staged<T, T>(csr, stage.col, stage.val, e0s, ld, g0[r]);
+                            w[r][0] = csr_row_staged<T, CT>(csr, stage.col, stage.val, e0s, ld, g0[r]);
                         }
                     } else if (k == 0) {
-                        op_apply<T, T, VEC, OP>(st, csr, cC, cO, LdFirst<T>{rc}, g0[r], c[r], w[r]);
+                        op_apply<T, CT, VEC, OP>(st, csr, cC, cO, LdFirst<T>{rc}, g0[r], c[r], w[r]);
                     } else {
-                        op_apply<T, T, VEC, OP>(st, csr, cC, cO, LdAxpy<T>{rc, po, (T)beta}, g0[r], c[r], w[r]);
+                        op_apply<T, CT, VEC, OP>(st, csr, cC, cO, LdAxpy<T>{rc, po, (T)beta}, g0[r], c[r], w[r]);
                     }
                     if constexpr (op_is_jacobi(OP))
                         mi[r] = __ldg(static_cast<const T *>(csr.dinv) + g0[r]);
@@ -2086,8 +2118,12 @@ __device__ void cg_body(const SolveArgs<T> &a, Smem<T> &s, Grp &grp)
                     vld<T, VEC>(q + g0[r], qv[r]);
                     vld<T, VEC>(xi + g0[r], xv[r]);
                     vld<T, VEC>(rc + g0[r], rv[r]);
-                    if constexpr (op_is_jacobi(OP))
-                        vldg<T, VEC>(static_cast<const T *>(csr.diag) + g0[r], dv[r]);
+                    if constexpr (op_is_jacobi(OP)) {
+                        CT dc[VEC];
+                        vldg<CT, VEC>(static_cast<const CT *>(csr.diag) + g0[r], dc);
+#pragma unroll
+                        for (int v = 0; v < VEC; ++v) dv[r][v] = coef_cast<T>(dc[v]);
+                    }
                 }
 #pragma unroll
                 for (int r = 0; r < RPT; ++r) {
@@ -2159,21 +2195,23 @@ template <typename T, int L, int OP>
 constexpr int kPlcgMinBlocks = (sizeof(T) == 4 && op_is_var27(OP)) ? (kV27Buf > 2 ? 1 : 2)
                              : (sizeof(T) == 4 && L <= 2) ? 3 : 2;
 
-template <typename T, int L, int VEC, int OP, bool SC = false>
+// CT: the stored type of the matrix values (T, or float under FP64 vectors:
+// the FP32-matrix path).
+template <typename T, int L, int VEC, int OP, bool SC = false, typename CT = T>
 __global__ void __launch_bounds__(kBlock, (kPlcgMinBlocks<T, L, OP>))
 plcg_kernel(SolveArgs<T> a)
 {
     __shared__ Smem<T> s;
     GridGroup<T> grp;
-    plcg_body<T, L, VEC, OP, GridGroup<T>, 1, SC>(a, s, grp);
+    plcg_body<T, L, VEC, OP, GridGroup<T>, 1, SC, CT>(a, s, grp);
 }
 
-template <typename T, int VEC, int OP>
+template <typename T, int VEC, int OP, typename CT = T>
 __global__ void __launch_bounds__(kBlock, 3) cg_kernel(SolveArgs<T> a)
 {
     __shared__ Smem<T> s;
     GridGroup<T> grp;
-    cg_body<T, VEC, OP>(a, s, grp);
+    cg_body<T, VEC, OP, GridGroup<T>, 1, CT>(a, s, grp);
 }
 
 // ------------------------------------------------------------------------
@@ -2193,6 +2231,9 @@ __global__ void __launch_bounds__(kBlock, 3) cg_kernel(SolveArgs<T> a)
 // method; 4 row groups for classic CG and p(1)-CG, 1 for p(l >= 2)-CG.
 template <int L, bool CG> constexpr int kBatchMinBlocks = 4;
 template <int L, bool CG> constexpr int kBatchRPT = (CG || L == 1) ? 4 : 1;
+// Other launch shapes (CTAs per SM the registers are sized for, row groups
+// per thread) are instantiated for the FP32 path; the batched autotuner
+// picks among them (plcg_set_batched_launch).
 
 template <typename T>
 __device__ __forceinline__ void batch_args(const BatchArgs<T> &ba, const BatchSys &sy, T *ws,
@@ -2225,12 +2266,13 @@ __device__ __forceinline__ void batch_args(const BatchArgs<T> &ba, const BatchSy
                                      ((((size_t)(nvec + 2) * nv * sizeof(T)) + 255) / 256) * 256);
 }
 
-template <typename T, int L, bool CG>
-__global__ void __launch_bounds__(kBlock, kBatchMinBlocks<L, CG>) batched_kernel(BatchArgs<T> ba)
+template <typename T, int L, bool CG, int MINB = kBatchMinBlocks<L, CG>, int RPT = kBatchRPT<L, CG>>
+__global__ void __launch_bounds__(kBlock, MINB) batched_kernel(BatchArgs<T> ba)
 {
     __shared__ Smem<T> s;
     __shared__ int s_next;
     const int b = blockIdx.x;
+    if (b == 0 && threadIdx.x == 0) *ba.t0 = global_timer_ns();
     if (b < ba.ngangs * ba.G) {
         const int gang = b / ba.G;
         GangGroup<T> grp;
@@ -2272,8 +2314,8 @@ __global__ void __launch_bounds__(kBlock, kBatchMinBlocks<L, CG>) batched_kernel
         SolveArgs<T> a;
         batch_args(ba, ba.sys[ba.order_small[k]], ws, a);
         BlockGroup<T> grp;
-        if constexpr (CG) cg_body<T, 1, kOpStencil, BlockGroup<T>, kBatchRPT<L, CG>>(a, s, grp);
-        else plcg_body<T, L, 1, kOpStencil, BlockGroup<T>, kBatchRPT<L, CG>>(a, s, grp);
+        if constexpr (CG) cg_body<T, 1, kOpStencil, BlockGroup<T>, RPT>(a, s, grp);
+        else plcg_body<T, L, 1, kOpStencil, BlockGroup<T>, RPT>(a, s, grp);
     }
 }
 

@@ -36,6 +36,7 @@ STATUS_NAMES = {0: "OK", 1: "PENDING", -1: "INVALID", -2: "NOMEM", -3: "CUDA", -
 
 PLCG_FP64 = 0
 PLCG_FP32_FP64DOT = 1
+PLCG_FP32_MATRIX = 2
 PLCG_METHOD_PLCG = 0
 PLCG_METHOD_CG = 1
 PLCG_PRECOND_NONE = 0
@@ -93,11 +94,13 @@ SIGNATURES = {
     "plcg_wait": (C.c_int, [_VP, C.c_uint64, C.POINTER(plcg_result)]),
     "plcg_server_destroy": (None, [_VP]),
     "plcg_set_batched_schedule": (C.c_int, [C.c_int, C.c_double, C.c_double]),
+    "plcg_set_batched_launch": (C.c_int, [C.c_int, C.c_int]),
     "plcg_last_error": (C.c_char_p, []),
     "plcg_version": (C.c_char_p, []),
     "plcg_debug_set_poll_limit": (None, [C.c_uint64]),
     "plcg_debug_force_barrier_timeout": (None, [C.c_int]),
     "plcg_debug_last_launch": (None, [C.POINTER(plcg_launch_info)]),
+    "plcg_measure_fp64_fma_rate": (C.c_int, [C.POINTER(C.c_double)]),
 }
 
 _lib = None
@@ -121,6 +124,13 @@ def load(path: str = LIB_PATH):
 
 def last_error() -> str:
     return load().plcg_last_error().decode()
+
+
+def measure_fp64_fma_rate() -> float:
+    """plcg_measure_fp64_fma_rate: the device's FP64 FMA throughput (FLOP/s)."""
+    v = C.c_double()
+    _check(load().plcg_measure_fp64_fma_rate(C.byref(v)))
+    return v.value
 
 
 def last_launch() -> dict:
@@ -171,6 +181,18 @@ def _result(r: plcg_result) -> Result:
                   r.true_relres, r.seconds, r.latency)
 
 
+def _prec_code(prec) -> int:
+    """Solve precision: "fp64", "fp32" (FP32 vectors and values, FP64 dots,
+    scalars and refinement) or "fp32_matrix" (FP32 values, FP64 vectors)."""
+    if prec in ("fp32", PLCG_FP32_FP64DOT):
+        return PLCG_FP32_FP64DOT
+    if prec in ("fp32_matrix", PLCG_FP32_MATRIX):
+        return PLCG_FP32_MATRIX
+    if prec in ("fp64", PLCG_FP64):
+        return PLCG_FP64
+    raise ValueError(f"unknown precision {prec!r}")
+
+
 def make_params(method="plcg", l=1, shifts=None, interval=(0.0, 8.0), rtol=1e-8, maxit=100000,
                 prec="fp64", dots_2l1=False, max_restarts=8, inner_rtol_floor=1e-4,
                 grid_ctas=0, precond=None):
@@ -185,7 +207,7 @@ def make_params(method="plcg", l=1, shifts=None, interval=(0.0, 8.0), rtol=1e-8,
     p.lmin, p.lmax = float(interval[0]), float(interval[1])
     p.rtol = float(rtol)
     p.maxit = int(maxit)
-    p.prec = PLCG_FP32_FP64DOT if prec in ("fp32", PLCG_FP32_FP64DOT) else PLCG_FP64
+    p.prec = _prec_code(prec)
     p.dots_2l1 = int(bool(dots_2l1))
     p.max_restarts = int(max_restarts)
     p.inner_rtol_floor = float(inner_rtol_floor)
@@ -200,6 +222,8 @@ class Matrix:
     """A device operator (stencil, CSR or structured 27-point) owned by the library."""
 
     def __init__(self, op: dict, prec="fp64", stream=None):
+        """prec: "fp64" keeps FP64 matrix values; "fp32" and "fp32_matrix"
+        store them rounded to FP32 (solvable with prec "fp32" or "fp32_matrix")."""
         lib = load()
         self.op = op
         if op["kind"] == "csr":
@@ -213,7 +237,7 @@ class Matrix:
             coef = np.ascontiguousarray(op["coef"], dtype=np.float64)
             if coef.shape != (14, self.n):
                 raise ValueError("var27 coef must have shape (14, n)")
-            pc = PLCG_FP32_FP64DOT if prec == "fp32" else PLCG_FP64
+            pc = PLCG_FP64 if _prec_code(prec) == PLCG_FP64 else PLCG_FP32_FP64DOT
             _check(lib.plcg_create_var27(int(op["nx"]), int(op["ny"]), int(op["nz"]), coef.ctypes.data,
                                          0, pc, _VP(_stream_ptr(stream)), C.byref(h)))
         elif op["kind"] == "stencil":
@@ -226,7 +250,7 @@ class Matrix:
             rowptr = np.ascontiguousarray(op["rowptr"], dtype=np.int64)
             col = np.ascontiguousarray(op["col"], dtype=np.int32)
             val = np.ascontiguousarray(op["val"], dtype=np.float64)
-            pc = PLCG_FP32_FP64DOT if prec == "fp32" else PLCG_FP64
+            pc = PLCG_FP64 if _prec_code(prec) == PLCG_FP64 else PLCG_FP32_FP64DOT
             _check(lib.plcg_create_csr(self.n, int(col.size), rowptr.ctypes.data, col.ctypes.data,
                                        val.ctypes.data, 0, pc, _VP(_stream_ptr(stream)), C.byref(h)))
         self.handle = h

@@ -363,13 +363,21 @@ def batched_systems(count: int = 4096, s_lo: int = 16, s_hi: int = 256, seed: in
     rng = np.random.default_rng(seed)
     sides = rng.integers(s_lo, s_hi + 1, size=count)
     cs = rng.uniform(0.0, 1.0, size=count)
-    out = []
-    for idx in range(count):
-        op = fp32_rounded(stencil2d(int(sides[idx]), int(sides[idx]), shift=float(cs[idx])))
-        b = np.random.default_rng([seed, idx]).standard_normal(op_size(op))
-        out.append({"op": op, "b": b, "interval": (float(cs[idx]), 8.0 + float(cs[idx])),
-                    "side": int(sides[idx]), "c": float(cs[idx])})
-    return out
+    return [_batched_one(seed, idx, int(sides[idx]), float(cs[idx])) for idx in range(count)]
+
+
+def batched_system(index: int, count: int = 4096, s_lo: int = 16, s_hi: int = 256, seed: int = 4) -> dict:
+    """System ``index`` of batched_systems(count, ...), built alone."""
+    rng = np.random.default_rng(seed)
+    sides = rng.integers(s_lo, s_hi + 1, size=count)
+    cs = rng.uniform(0.0, 1.0, size=count)
+    return _batched_one(seed, index, int(sides[index]), float(cs[index]))
+
+
+def _batched_one(seed: int, idx: int, side: int, c: float) -> dict:
+    op = fp32_rounded(stencil2d(side, side, shift=c))
+    b = np.random.default_rng([seed, idx]).standard_normal(op_size(op))
+    return {"op": op, "b": b, "interval": (c, 8.0 + c), "side": side, "c": c}
 
 
 def serving_stream(duration_s: float = 1.0, rate: float = 2000.0, n_lo: float = 1e3,

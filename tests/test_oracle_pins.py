@@ -649,3 +649,29 @@ def test_var27_solves_vs_dense_cholesky():
     for r in runs:
         assert r.status == O.ORC_OK and r.true_relres < rtol
         assert np.linalg.norm(r.x - x_chol) / np.linalg.norm(x_chol) <= bound
+
+
+# ------------------------------------------------------------ refinement loop
+def test_refined_loop_reduces_to_one_solve_and_matches_cholesky():
+    """O.refined (the FP32 path's outer loop in FP64): with a floor below
+    rtol it is one plain solve to rtol / 2, the inner target (same
+    iterations, same x); with the default
+    floor 1e-4 and rtol 1e-8 it takes at least two inner solves, and its x
+    satisfies the Cholesky bound like a plain solve."""
+    import scipy.linalg as sla
+    op = W.stencil2d(12, 11, shift=0.02)
+    b = np.random.default_rng(5).standard_normal(W.op_size(op))
+    for method, l in (("plcg", 1), ("plcg", 2), ("cg", 1)):
+        sig = O.chebyshev_shifts(l, *W.shift_interval(op)) if method == "plcg" else None
+        plain = (O.plcg(op, b, l=l, sigma=sig, rtol=0.5e-8, dots_2l1=False) if method == "plcg"
+                 else O.cg(op, b, rtol=0.5e-8))
+        one = O.refined(op, b, method=method, l=l, sigma=sig, rtol=1e-8, floor=1e-12)
+        assert one.segments == 1 and one.iters == plain.iters
+        assert np.array_equal(one.x, plain.x)
+        two = O.refined(op, b, method=method, l=l, sigma=sig, rtol=1e-8, floor=1e-4)
+        assert two.status == O.ORC_OK and two.segments >= 2
+        A = W.to_scipy(op).toarray()
+        xc = sla.cho_solve(sla.cho_factor(A), b)
+        lo, hi = W.stencil_spectrum_bounds(op)
+        assert np.linalg.norm(two.x - xc) / np.linalg.norm(xc) <= (hi / lo) * 1e-8
+        assert np.linalg.norm(b - A @ two.x) / np.linalg.norm(b) < 1e-8
