@@ -313,6 +313,16 @@ plcg_status plcg_measure_fp64_fma_rate(double *flops_per_s);
  * Errors: PLCG_ERR_INVALID. */
 plcg_status plcg_set_batched_launch(int ctas_per_sm, int rows_per_thread);
 
+/* Small systems (stencil or CSR operators, M = I or a Jacobi-preconditioned
+ * stencil, grid_ctas = 0) are solved by one thread-block cluster of up to 16
+ * blocks instead of a grid of blocks: the cluster barrier replaces the grid
+ * barrier and each block's partial dot products are read by the others from
+ * its shared memory.  This applies to p(l)-CG with 2 <= l <= 4 and classic CG
+ * up to max_rows unknowns, and to p(1)-CG up to max_rows / 2.  Process-wide;
+ * 0 disables; the default is 12288.  A device that cannot place a cluster
+ * falls back to the grid.  Errors: PLCG_ERR_INVALID (max_rows < 0). */
+plcg_status plcg_set_cluster_rows(int64_t max_rows);
+
 /* Thread-local message describing the last failure in this thread. */
 const char *plcg_last_error(void);
 
@@ -341,6 +351,8 @@ typedef struct {
     int staged;                 /* 1: CSR entries staged in shared memory       */
     uint64_t poll_limit;        /* bound of every device-side wait (polls)      */
     int force_timeout;          /* the plcg_debug_force_barrier_timeout setting */
+    int cluster;                /* > 0: the grid is one thread-block cluster of
+                                   this many blocks (small systems)             */
 } plcg_launch_info;
 void plcg_debug_last_launch(plcg_launch_info *out);
 

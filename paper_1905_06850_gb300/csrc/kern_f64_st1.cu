@@ -9,6 +9,7 @@ namespace plcg {
 const void *kptr_f64_st1(int l, bool cg, bool sc)
 {
     if (cg) return reinterpret_cast<const void *>(&cg_kernel<double, 1, kOpStencil>);
+    if (sc && l >= 2 && l <= 5) return kptr_f64_stsc(1, l);   // scaled bases, l = 2..5
     switch (l) {
     case 1:   // sc: the scaled-basis variant (large systems)
         return sc ? reinterpret_cast<const void *>(&plcg_kernel<double, 1, 1, kOpStencil, true>)

@@ -57,6 +57,61 @@ extern "C" const char *plcg_version(void) { return "plcg 0.1 (sm_103a)"; }
 extern "C" void plcg_debug_set_poll_limit(uint64_t polls) { g_poll_limit = polls; }
 extern "C" void plcg_debug_force_barrier_timeout(int on) { g_force_timeout = on ? 1 : 0; }
 
+// Systems of at most this many rows run on the cluster-resident solver
+// (p(l >= 2)-CG and classic CG; p(1)-CG up to half of it), 0: never; set by
+// plcg_set_cluster_rows.  The default comes from timing both paths on GB300:
+// at 4096 rows the cluster is faster for every method (p(1)-CG 6.0 vs 6.8 us
+// per iteration), at 10^4 rows for l >= 2 and CG (p(2)-CG 6.5 vs 7.7 us) but
+// not for p(1)-CG (8.0 vs 7.1 us: sixteen SMs of FP64 units against twenty),
+// and above ~2x10^4 rows the grid wins throughout.
+constexpr int64_t kClusterRowsDefault = 12288;
+static int64_t g_cluster_rows = kClusterRowsDefault;
+
+extern "C" plcg_status plcg_set_cluster_rows(int64_t max_rows)
+{
+    if (max_rows < 0) return fail(PLCG_ERR_INVALID, "plcg_set_cluster_rows: max_rows must be >= 0");
+    g_cluster_rows = max_rows;
+    return PLCG_OK;
+}
+
+// The largest cluster (<= want, 16 at most) that the device can place for
+// func, or 0: clusters above 8 CTAs need the non-portable-size attribute.
+static int cluster_size_for(const void *func, int want)
+{
+    static std::mutex mu;
+    static std::unordered_map<const void *, int> cache;   // func -> largest placeable cluster
+    int cmax = 0;
+    {
+        std::lock_guard<std::mutex> lk(mu);
+        auto it = cache.find(func);
+        if (it != cache.end()) cmax = it->second;
+    }
+    if (cmax == 0) {
+        cudaFuncSetAttribute(func, cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
+        for (int c : {16, 8, 4, 2, 1}) {
+            cudaLaunchConfig_t cfg = {};
+            cfg.gridDim = dim3((unsigned)c);
+            cfg.blockDim = dim3(kBlock);
+            cudaLaunchAttribute at[1];
+            at[0].id = cudaLaunchAttributeClusterDimension;
+            at[0].val.clusterDim.x = (unsigned)c;
+            at[0].val.clusterDim.y = 1;
+            at[0].val.clusterDim.z = 1;
+            cfg.attrs = at;
+            cfg.numAttrs = 1;
+            int nclusters = 0;
+            if (cudaOccupancyMaxActiveClusters(&nclusters, func, &cfg) == cudaSuccess && nclusters >= 1) {
+                cmax = c;
+                break;
+            }
+        }
+        cudaGetLastError();   // a refused size leaves no sticky error
+        std::lock_guard<std::mutex> lk(mu);
+        cache[func] = cmax > 0 ? cmax : -1;
+    }
+    return cmax > 0 ? std::min(cmax, std::max(1, want)) : 0;
+}
+
 static unsigned long long poll_limit()
 {
     // ~2 s at 64 ns per poll (the poll itself adds an L2 round trip)
@@ -433,15 +488,16 @@ static plcg_status build_solve(const plcg_matrix *A, const double *b, double *x,
         const int want = 16 / (int)sizeof(T);
         vec = (A->st.nx % want == 0) ? want : 1;
     }
-    // FP64 p(1)-CG on 2^19 rows or more: the scaled-basis kernel (two FP64
-    // multiplies per row fewer; below that the longer scalar step costs more)
-    const bool sc = !f32 && !cg && l == 1 && n >= (int64_t(1) << 19);
+    // FP64 p(l)-CG on 2^19 rows or more: the scaled-basis kernel (one FP64
+    // multiply per recurrence and row fewer; below that the longer scalar step
+    // costs more) -- l <= 5 on the stencils, l = 1 on the stored operators
+    const bool sc = !f32 && !cg && n >= (int64_t(1) << 19) && (l == 1 || (op == kOpStencil && l <= 5));
     const void *func = kernel_ptr(f32, op, vec, cg ? 0 : l, cg, sc, c32);
     if (!func) return fail(PLCG_ERR_UNIMPL, "no kernel for prec=%d op=%d vec=%d l=%d", prm->prec, op, vec, l);
     // CSR kernels stage each unit's entries in dynamic shared memory (FP64
     // classic CG excepted, see cg_body); the 27-point p(l)-CG kernels stage
     // coefficient and z tiles
-    const unsigned dsmem = (op_is_csr(op) && (!cg || f32)) ? csr_stage_bytes(value_bytes)
+    unsigned dsmem = (op_is_csr(op) && (!cg || f32)) ? csr_stage_bytes(value_bytes)
                          : (op_is_var27(op) && !cg && f32)
                              ? v27_tile_bytes((unsigned)sizeof(T), l, op_is_jacobi(op)) : 0u;
     if (dsmem) {
@@ -458,6 +514,22 @@ static plcg_status build_solve(const plcg_matrix *A, const double *b, double *x,
     if (prm->grid_ctas > 0) P = std::min<int64_t>(P, prm->grid_ctas);
     if (max_ctas > 0) P = std::min<int64_t>(P, max_ctas);
     P = std::max<int64_t>(1, std::min<int64_t>(P, nunits));
+    // small systems: one thread-block cluster holds the whole solve (its
+    // barrier and distributed shared memory replace the grid barrier and the
+    // partials in global memory)
+    int cluster = 0;
+    if (n <= (cg || l >= 2 ? g_cluster_rows : g_cluster_rows / 2) && !c32 &&
+        (op == kOpStencil || op == kOpCsr) && (cg || l <= 4) && prm->grid_ctas == 0) {
+        const void *cf = f32 ? kptr_cluster_f32(op, vec, cg ? 0 : l, cg) : kptr_cluster_f64(op, vec, cg ? 0 : l, cg);
+        const int c = cf ? cluster_size_for(cf, (int)std::min<int64_t>(16, nunits)) : 0;
+        if (c > 0 && (max_ctas == 0 || c <= max_ctas)) {
+            func = cf;
+            cluster = c;
+            P = c;
+            per_sm = 1;
+            dsmem = 0;
+        }
+    }
 
     SolveArgs<T> &a = *args;
     std::memset(&a, 0, sizeof(a));
@@ -548,9 +620,10 @@ static plcg_status build_solve(const plcg_matrix *A, const double *b, double *x,
     // that latency is a visible share of an iteration (smaller systems)
     a.lookahead = (!cg && l >= 2 && n < (int64_t(1) << 22)) ? 1 : 0;
     a.dsmem = dsmem;
+    a.cluster = cluster;
     // staging a warp's CSR entries pays when rows are long; short rows (the
     // diagonal toy has one entry) read them directly (measured)
-    a.stage = (op_is_csr(op) && A->nnz >= 4 * n) ? 1 : 0;
+    a.stage = (op_is_csr(op) && A->nnz >= 4 * n && !cluster) ? 1 : 0;
     return PLCG_OK;
 }
 
@@ -579,8 +652,26 @@ static plcg_status launch_built(const SolveArgs<T> &a0, const void *func, int64_
     g_last_launch.staged = a.stage;
     g_last_launch.poll_limit = a.poll_limit;
     g_last_launch.force_timeout = a.force_timeout;
+    g_last_launch.cluster = a.cluster;
     void *args[] = {&a};
-    CUDA_TRY(cudaLaunchCooperativeKernel(func, dim3((unsigned)P), dim3(kBlock), args, a.dsmem, stream));
+    if (a.cluster > 0) {
+        // the grid is one cluster: the hardware places all its CTAs together
+        cudaLaunchConfig_t cfg = {};
+        cfg.gridDim = dim3((unsigned)P);
+        cfg.blockDim = dim3(kBlock);
+        cfg.dynamicSmemBytes = a.dsmem;
+        cfg.stream = stream;
+        cudaLaunchAttribute at[1];
+        at[0].id = cudaLaunchAttributeClusterDimension;
+        at[0].val.clusterDim.x = (unsigned)P;
+        at[0].val.clusterDim.y = 1;
+        at[0].val.clusterDim.z = 1;
+        cfg.attrs = at;
+        cfg.numAttrs = 1;
+        CUDA_TRY(cudaLaunchKernelExC(&cfg, func, args));
+    } else {
+        CUDA_TRY(cudaLaunchCooperativeKernel(func, dim3((unsigned)P), dim3(kBlock), args, a.dsmem, stream));
+    }
     return PLCG_OK;
 }
 

@@ -114,6 +114,7 @@ struct SolveArgs {
     unsigned long long poll_limit;
     int force_timeout;
     int lookahead;            // l >= 2: compute the next iteration's scalars during the sweep
+    int cluster;              // > 0: the grid is one thread-block cluster of this many CTAs
     unsigned dsmem;           // dynamic shared memory of the launch (CSR / 27-point staging)
     const char *ws_lo, *ws_hi;   // the solve's workspace (bounds for staged copies)
     const char *cf_lo, *cf_hi;   // structured 27-point: the coefficient allocation (same)

@@ -27,6 +27,7 @@ const void *batched_kernel_ptr_f64(int l, bool cg);
 // Per-translation-unit getters used by kernel_ptr.
 const void *kptr_f64_st2(int l, bool cg, bool sc);
 const void *kptr_f64_st1(int l, bool cg, bool sc);
+const void *kptr_f64_stsc(int vec, int l);
 const void *kptr_f64_csr(int l, bool cg, bool sc);
 const void *kptr_f32_st4(int l, bool cg);
 const void *kptr_f32_st1(int l, bool cg);
@@ -37,6 +38,10 @@ const void *kptr_f64_v27(int l, bool cg, bool sc);
 const void *kptr_f32_v27(int l, bool cg);
 const void *kptr_f64_v27j(int l, bool cg, bool sc);
 const void *kptr_f32_v27j(int l, bool cg);
+// The cluster-resident small-system solver (stencil and CSR operators,
+// l = 1..4 or classic CG); nullptr when not instantiated.
+const void *kptr_cluster_f64(int op, int vec, int l, bool cg);
+const void *kptr_cluster_f32(int op, int vec, int l, bool cg);
 const void *kptr_m_csr(int l, bool cg, bool sc);
 const void *kptr_m_csrj(int l, bool cg, bool sc);
 const void *kptr_m_v27(int l, bool cg, bool sc);

@@ -826,8 +826,9 @@ struct Smem {
     double Ginv[kMaxL + 1];          // 1 / g_{c,c} of those columns
     double gam[kMaxL + 1], del[kMaxL + 1], idel[kMaxL + 1];   // gamma_j, delta_j, 1 / delta_j
     double eta[2], zeta[2], ieta[2]; // eta_m, zeta_m, 1 / eta_m
-    double scs[4], sct[4];           // scaled bases: s_j of z^(l)_j, t_j of z^(0)_j (j mod 4)
-    double iscs[4], isct[4];         // ... and their reciprocals
+    double scs[16], iscs[16];        // scaled bases: s_j of z^(l)_j (j mod 16) and reciprocals
+    double sct[kMaxL][16];           // ... t^(k)_j of z^(k)_j, k < l (j mod 16)
+    double isct[kMaxL][16];          // ... and their reciprocals
     double ikn;                      // 1 / kn
     double bring[kMaxL + 1][kMaxDots];   // one-CTA group: reduced dots of the last l+1 iterations
     double bnorm[2];
@@ -945,6 +946,105 @@ struct BlockGroup {
     }
 };
 
+// ------------------------------------------------------------------------
+// Thread-block clusters: the whole grid is one cluster of up to 16 CTAs on
+// neighbouring SMs, which the hardware schedules together.  Its barrier
+// (barrier.cluster, release/acquire at cluster scope, which orders the
+// CTAs' global and shared memory accesses) replaces the grid barrier, and
+// each CTA's reduced dots stay in its own shared memory, where the others
+// read them through distributed shared memory (mapa + ld.shared::cluster).
+// ------------------------------------------------------------------------
+__device__ __forceinline__ uint32_t cluster_rank()
+{
+    uint32_t r;
+    asm volatile("mov.u32 %0, %%cluster_ctarank;" : "=r"(r));
+    return r;
+}
+
+__device__ __forceinline__ uint32_t cluster_size()
+{
+    uint32_t r;
+    asm volatile("mov.u32 %0, %%cluster_nctarank;" : "=r"(r));
+    return r;
+}
+
+// Every thread of every CTA of the cluster (warp-converged).
+__device__ __forceinline__ void cluster_barrier()
+{
+    asm volatile("barrier.cluster.arrive.release.aligned;\n\tbarrier.cluster.wait.acquire.aligned;" ::: "memory");
+}
+
+// The double at the same shared-memory offset as *p in CTA `rank` of the cluster.
+__device__ __forceinline__ double ld_dsmem(const double *p, uint32_t rank)
+{
+    uint32_t ra;
+    double v;
+    asm volatile("mapa.shared::cluster.u32 %0, %1, %2;" : "=r"(ra) : "r"(smem_addr(p)), "r"(rank));
+    asm volatile("ld.shared::cluster.f64 %0, [%1];" : "=d"(v) : "r"(ra) : "memory");
+    return v;
+}
+
+// One warp: dst[q] = sum over the cluster's CTAs of their src[q], Q0 <= q < ND,
+// in a fixed order (lane c reads CTA c, then the reduce-scatter butterfly),
+// so every CTA gets the same bits; dst[q] = 0 for q < Q0.
+template <int ND, int Q0 = 0>
+__device__ __forceinline__ void cluster_dots_sum(const double *src, double *dst)
+{
+    constexpr int NA = ND - Q0;
+    constexpr int P = NA <= 1 ? 0 : NA <= 2 ? 1 : NA <= 4 ? 2 : NA <= 8 ? 3 : NA <= 16 ? 4 : 5;
+    const int lane = threadIdx.x & 31;
+    const uint32_t nc = cluster_size();
+    double v[NA];
+#pragma unroll
+    for (int q = 0; q < NA; ++q) v[q] = ((uint32_t)lane < nc) ? ld_dsmem(src + Q0 + q, (uint32_t)lane) : 0.0;
+    const double t = warp_reduce_scatter<NA>(v, lane);
+    if ((lane & ((32 >> P) - 1)) == 0) {
+        const int q = lane >> (5 - P);
+        if (q < NA) dst[Q0 + q] = t;
+    }
+    if (lane < Q0) dst[lane] = 0.0;
+    __syncwarp();
+}
+
+template <typename T>
+struct ClusterGroup {
+    __device__ __forceinline__ int64_t unit0() const { return cluster_rank(); }
+    __device__ __forceinline__ int64_t ustep() const { return cluster_size(); }
+    __device__ __forceinline__ bool leader() const { return cluster_rank() == 0; }
+    // no bounded wait to expire: every CTA takes the same branches (the
+    // scalars are bit-identical), so all arrive at every barrier
+    __device__ __forceinline__ bool sync(const SolveArgs<T> &, Smem<T> &)
+    {
+        cluster_barrier();
+        return true;
+    }
+    __device__ __forceinline__ void put_dots(const SolveArgs<T> &, Smem<T> &s, int slot, int nd)
+    {
+        if ((int)threadIdx.x < nd) s.bring[slot][threadIdx.x] = s.out[threadIdx.x];
+    }
+    template <int ND>
+    __device__ __forceinline__ void get_dots(const SolveArgs<T> &, Smem<T> &s, int slot, double *dst)
+    {
+        if (threadIdx.x < 32) cluster_dots_sum<ND>(&s.bring[slot][0], dst);
+        __syncthreads();
+    }
+    template <int ND>
+    __device__ __forceinline__ void get_dots_warp(const SolveArgs<T> &a, Smem<T> &s, int slot, double *dst)
+    {
+        if (a.dots_2l1) cluster_dots_sum<ND, 0>(&s.bring[slot][0], dst);
+        else cluster_dots_sum<ND, (ND - 1) / 2>(&s.bring[slot][0], dst);
+    }
+    __device__ __forceinline__ void put_norms(const SolveArgs<T> &, Smem<T> &s)
+    {
+        if (threadIdx.x < 2) s.bnorm[threadIdx.x] = s.out[threadIdx.x];
+    }
+    __device__ __forceinline__ void get_norms(const SolveArgs<T> &, Smem<T> &s)
+    {
+        if (threadIdx.x < 32) cluster_dots_sum<2>(&s.bnorm[0], s.out);
+        __syncthreads();
+    }
+};
+
 // A gang: G CTAs of one cooperative launch solving one system together
 // (batched solves of large systems); bounded barrier and FP64 partials of its
 // own, so gangs proceed independently of each other.
@@ -1050,21 +1150,27 @@ __device__ __forceinline__ void step_vectors(Coef<T> &cf, const SolveArgs<T> &a,
     }
 }
 
-// Scaled bases (FP64, l = 1).  The sweep stores Z_j = z^(1)_j / s_j and
-// W_j = z^(0)_j / t_j, and the direction P_m = phat_m / t_m, with the scales
-// chosen so that K4 needs no multiply: s_{i+1} = s_i kn / delta_m and
-// t_{m+1} = s_i / delta_m, times a power of two (2^e, 2^f) only when the
-// product leaves [2^-256, 2^256]; with (A z)_g = kc z_g + kn nb_g,
+// Scaled bases (FP64).  The sweep stores Z_j = z^(l)_j / s_j and, for each
+// basis k < l, W^(k)_j = z^(k)_j / t^(k)_j, and the direction
+// P_m = phat_m / t^(0)_m, with the scales chosen so that K4 needs no
+// multiply for one term of each recurrence: s_{i+1} = s_i kn / delta_m and
+// t^(k)_{m+k+1} = t^(k+1)_{m+k+1} / delta_m (t^(l) being s), times a power
+// of two (2^e, 2^f_k) only when a product leaves [2^-256, 2^256]; with
+// (A z)_g = kc z_g + kn nb_g,
 //   Z_{i+1} = nb(Z_i) + ((kc - gamma_m) / kn) Z_i - (delta_{m-1} s_{i-1} / (kn s_i)) Z_{i-1}
-//   W_{m+1} = Z_i + (sigma_0 - gamma_m)(t_m / s_i) W_m - delta_{m-1} (t_{m-1} / s_i) W_{m-1}
-// (each divided by 2^e or 2^f when that is not 1: the general sweep form
-// then).  The host picks this variant (SC) for 2^19 rows or more: below
-// that the step's extra latency outweighs two FP64 multiplies per row.
-// The K5 dots of scaled vectors are multiplied back by their scales here,
-// so G, gamma, delta, eta and zeta are those of the unscaled algorithm; K6
-// folds t into its scalars.  Same iterates in exact arithmetic.
+//   W^(k)_{m+k+1} = U + (sigma_k - gamma_m)(t^(k)_{m+k} / u) W^(k)_{m+k}
+//                     - delta_{m-1} (t^(k)_{m+k-1} / u) W^(k)_{m+k-1}
+// where U = W^(k+1)_{m+k+1} (Z_i for k = l - 1) has the scale u (each term
+// divided by 2^e or 2^f_k when that is not 1: the general sweep form then).
+// The host picks this variant (SC) for 2^19 rows or more (l <= 5 on the
+// stencils, l = 1 elsewhere): below that the step's extra latency outweighs
+// the FP64 multiplies per row it saves.  The K5 dots of scaled vectors are
+// multiplied back by their scales here, so G, gamma, delta, eta and zeta are
+// those of the unscaled algorithm; K6 folds t^(0) into its scalars.  Same
+// iterates in exact arithmetic.  Scale rings of 16 hold every index a step
+// reads: s over 2l values, t^(0) over 2l + 1 (l <= 5).
 template <typename T, int L>
-constexpr bool kScaledBases = (sizeof(T) == 8 && L == 1);
+constexpr bool kScaledBases = (sizeof(T) == 8 && L <= 5);
 
 template <typename T, int L, bool SC>
 __device__ __forceinline__ void scalar_step_body(Smem<T> &s, Coef<T> &cf, const double *raw,
@@ -1083,25 +1189,28 @@ __device__ __forceinline__ void scalar_step_body(Smem<T> &s, Coef<T> &cf, const 
         cf.mode = 0;
         cf.k6 = 0;
         cf.sig = (T)a.sigma[i];
-        if (kScaled && i == 0) {   // a segment starts from unscaled vectors
-            s.scs[0] = s.scs[1] = s.iscs[0] = s.iscs[1] = 1.0;
-            s.sct[0] = s.isct[0] = 1.0;
+        if (kScaled && i == 0) {   // a segment starts from unscaled vectors (the fill phase's)
+            for (int j = 0; j <= L; ++j) {
+                s.scs[j] = s.iscs[j] = 1.0;
+                for (int k = 0; k < L; ++k) s.sct[k][j] = s.isct[k][j] = 1.0;
+            }
             s.ikn = scl ? 1.0 / (double)kn : 0.0;
         }
         return;
     }
     const int c = i - L + 1;
     double *col = s.G[c % (L + 1)];
-    // scales of this step (l = 1: c = i, m = i - 1): s_i, s_{i-1}, t_m, t_{m-1}
-    // (with reciprocals kept beside them: no division on the step's path)
-    double s_i = 1.0, s_im1 = 1.0, t_m = 1.0, t_mm1 = 1.0, is_i = 1.0, it_m = 1.0;
+    // scales of this step: s_i, s_{i-1}, t_m = t^(0)_m, t_{m-1} (with
+    // reciprocals kept beside them: no division on the step's path)
+    double s_i = 1.0, s_im1 = 1.0, t_m = 1.0, t_mm1 = 1.0, is_i = 1.0, it_m = 1.0, s_c = 1.0;
     if (scl) {
-        s_i = s.scs[i & 3];
-        is_i = s.iscs[i & 3];
-        s_im1 = s.scs[(i - 1) & 3];
-        t_m = s.sct[m & 3];
-        it_m = s.isct[m & 3];
-        t_mm1 = (m >= 1) ? s.sct[(m - 1) & 3] : 1.0;
+        s_i = s.scs[i & 15];
+        is_i = s.iscs[i & 15];
+        s_im1 = s.scs[(i - 1) & 15];
+        s_c = s.scs[c & 15];
+        t_m = s.sct[0][m & 15];
+        it_m = s.isct[0][m & 15];
+        t_mm1 = (m >= 1) ? s.sct[0][(m - 1) & 15] : 1.0;
     }
     auto g = [&](int j, int cc) -> double {
         if (j < 0 || j < cc - 2 * L || j > cc) return 0.0;
@@ -1111,12 +1220,13 @@ __device__ __forceinline__ void scalar_step_body(Smem<T> &s, Coef<T> &cf, const 
     auto del = [&](int j) -> double { return j < 0 ? 0.0 : s.del[j % (L + 1)]; };
     auto idel = [&](int j) -> double { return s.idel[j % (L + 1)]; };
     auto gam = [&](int j) -> double { return s.gam[j % (L + 1)]; };
-    // raw column c (dots of iteration i-l): position q is row c-2l+q; scaled
-    // bases: u_c = s_c Z_c against t_{c-2} W, t_{c-1} W, s_c Z (l = 1)
+    // raw column c (dots of iteration i-l): position q is row j = c-2l+q;
+    // scaled bases: u_c = s_c Z_c against t^(0)_j W^(0)_j (q <= l) or s_j Z_j
 #pragma unroll
     for (int q = 0; q <= 2 * L; ++q) {
-        double v = (c - 2 * L + q >= 0) ? raw[q] : 0.0;
-        if (scl) v *= s_i * (q == 2 * L ? s_i : q == 2 * L - 1 ? t_m : t_mm1);
+        const int j = c - 2 * L + q;
+        double v = (j >= 0) ? raw[q] : 0.0;
+        if (scl && j >= 0) v *= s_c * (q <= L ? s.sct[0][j & 15] : s.scs[j & 15]);
         col[q] = v;
     }
     const int lo = (c - 2 * L > 0) ? c - 2 * L : 0;
@@ -1195,28 +1305,42 @@ __device__ __forceinline__ void scalar_step_body(Smem<T> &s, Coef<T> &cf, const 
     cf.mode = 1;
     cf.prev0 = (m >= 1);
     if (scl) {
-        // scaled bases: the new scales, 2^e and 2^f keeping them in range
-        const double bs = invd * (double)kn * s_i, bt = invd * s_i;
-        int e = 0, f = 0;
-        if (!(fabs(bs) >= 0x1p-256 && fabs(bs) <= 0x1p256)) e = -ilogb(bs);
-        if (!(fabs(bt) >= 0x1p-256 && fabs(bt) <= 0x1p256)) f = -ilogb(bt);
+        // scaled bases: the new scales, 2^e and 2^f_k keeping them in range
         auto pow2 = [](int k) -> double {   // 2^k, |k| < 1000
             return __longlong_as_double((long long)(1023 + k) << 52);
         };
-        const double pe = pow2(-e), pf = pow2(-f), ivk = pe * s.ikn;
-        s.scs[(i + 1) & 3] = bs * pow2(e);
-        s.iscs[(i + 1) & 3] = dm * s.ikn * is_i * pe;
-        s.sct[(m + 1) & 3] = bt * pow2(f);
-        s.isct[(m + 1) & 3] = dm * is_i * pf;
+        auto out_of_range = [](double v) -> bool { return !(fabs(v) >= 0x1p-256 && fabs(v) <= 0x1p256); };
+        const double bs = invd * (double)kn * s_i;
+        const int e = out_of_range(bs) ? -ilogb(bs) : 0;
+        const double pe = pow2(-e), ivk = pe * s.ikn;
+        s.scs[(i + 1) & 15] = bs * pow2(e);
+        s.iscs[(i + 1) & 15] = dm * s.ikn * is_i * pe;
         cf.invd = (T)ivk;
         cf.al = (T)(-gm * ivk);
         cf.uc = (T)(((double)kc - gm) * ivk);
         cf.unb = (T)pe;
         cf.bm = (T)((m >= 1) ? -dm1 * (s_im1 * is_i) * ivk : 0.0);
-        cf.ak[0] = (T)((a.sigma[0] - gm) * (t_m * is_i) * pf);
-        cf.wu[0] = (T)pf;
-        cf.wb[0] = (T)((m >= 1) ? -dm1 * (t_mm1 * is_i) * pf : 0.0);
-        cf.unit = (e == 0 && f == 0);
+        int unit = (e == 0);
+#pragma unroll
+        for (int k = 0; k < L; ++k) {
+            // basis k: current z^(k)_{m+k}, previous z^(k)_{m+k-1}, new z^(k)_{m+k+1};
+            // U = z^(k+1)_{m+k+1} (z^(l)_i for k = l - 1) with scale u
+            const int jc = m + k, jn = m + k + 1;
+            const double u = (k == L - 1) ? s_i : s.sct[k + 1][jn & 15];
+            const double iu = (k == L - 1) ? is_i : s.isct[k + 1][jn & 15];
+            const double tc = s.sct[k][jc & 15];
+            const double tp = (jc >= 1) ? s.sct[k][(jc - 1) & 15] : 1.0;
+            const double bt = invd * u;
+            const int f = out_of_range(bt) ? -ilogb(bt) : 0;
+            const double pf = pow2(-f);
+            s.sct[k][jn & 15] = bt * pow2(f);
+            s.isct[k][jn & 15] = dm * iu * pf;
+            cf.ak[k] = (T)((a.sigma[k] - gm) * (tc * iu) * pf);
+            cf.wu[k] = (T)pf;
+            cf.wb[k] = (T)((m >= 1) ? -dm1 * (tp * iu) * pf : 0.0);
+            unit &= (f == 0);
+        }
+        cf.unit = unit;
     } else {
         cf.invd = (T)invd;
         cf.al = (T)(-gm * invd);
@@ -1802,12 +1926,16 @@ __device__ void plcg_body(const SolveArgs<T> &a, Smem<T> &s, Grp &grp)
                             const T uc = C.uc, un_nb = C.unb;
                             if (kScaled && S && C.unit) {
                                 // scaled bases, steady state: the coefficients of nb
-                                // and of z^(l)_i in the z^(0) recurrence are 1
+                                // and of each recurrence's U term are 1
 #pragma unroll
-                                for (int v = 0; v < VEC; ++v) {
-                                    un[v] = fma(uc, c[r][v], fma(C.bm, zp[r][v], nb[r][v]));
-                                    nw[0][v] = fma(C.ak[0], cur[r][0][v], fma(C.wb[0], pk[r][0][v], c[r][v]));
-                                }
+                                for (int v = 0; v < VEC; ++v) un[v] = fma(uc, c[r][v], fma(C.bm, zp[r][v], nb[r][v]));
+#pragma unroll
+                                for (int k = 0; k < L; ++k)
+#pragma unroll
+                                    for (int v = 0; v < VEC; ++v) {
+                                        const T up = (k == L - 1) ? c[r][v] : cur[r][k + 1][v];
+                                        nw[k][v] = fma(C.ak[k], cur[r][k][v], fma(C.wb[k], pk[r][k][v], up));
+                                    }
                             } else {
 #pragma unroll
                                 for (int v = 0; v < VEC; ++v)
@@ -2212,6 +2340,20 @@ __global__ void __launch_bounds__(kBlock, 3) cg_kernel(SolveArgs<T> a)
     __shared__ Smem<T> s;
     GridGroup<T> grp;
     cg_body<T, VEC, OP, GridGroup<T>, 1, CT>(a, s, grp);
+}
+
+// Small systems: the grid is one thread-block cluster (ClusterGroup), launched
+// with a cluster dimension equal to the grid.  Every CTA passes a last
+// cluster barrier before it exits, so none leaves while another may still
+// read its shared memory.
+template <typename T, int L, int VEC, int OP, bool CG>
+__global__ void __launch_bounds__(kBlock, 1) plcg_cluster_kernel(SolveArgs<T> a)
+{
+    __shared__ Smem<T> s;
+    ClusterGroup<T> grp;
+    if constexpr (CG) cg_body<T, VEC, OP, ClusterGroup<T>>(a, s, grp);
+    else plcg_body<T, L, VEC, OP, ClusterGroup<T>>(a, s, grp);
+    cluster_barrier();
 }
 
 // ------------------------------------------------------------------------

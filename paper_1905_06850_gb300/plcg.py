@@ -67,7 +67,7 @@ class plcg_result(C.Structure):
 class plcg_launch_info(C.Structure):
     _fields_ = [("kernel", C.c_uint64), ("grid_ctas", C.c_int), ("dyn_smem", C.c_uint),
                 ("lookahead", C.c_int), ("staged", C.c_int), ("poll_limit", C.c_uint64),
-                ("force_timeout", C.c_int)]
+                ("force_timeout", C.c_int), ("cluster", C.c_int)]
 
 
 # every symbol include/plcg.h declares, with (restype, argtypes)
@@ -95,6 +95,7 @@ SIGNATURES = {
     "plcg_server_destroy": (None, [_VP]),
     "plcg_set_batched_schedule": (C.c_int, [C.c_int, C.c_double, C.c_double]),
     "plcg_set_batched_launch": (C.c_int, [C.c_int, C.c_int]),
+    "plcg_set_cluster_rows": (C.c_int, [C.c_int64]),
     "plcg_last_error": (C.c_char_p, []),
     "plcg_version": (C.c_char_p, []),
     "plcg_debug_set_poll_limit": (None, [C.c_uint64]),
@@ -124,6 +125,16 @@ def load(path: str = LIB_PATH):
 
 def last_error() -> str:
     return load().plcg_last_error().decode()
+
+
+CLUSTER_ROWS_DEFAULT = 12288
+
+
+def set_cluster_rows(max_rows: int = CLUSTER_ROWS_DEFAULT):
+    """plcg_set_cluster_rows: small systems run on one thread-block cluster
+    (p(l >= 2)-CG and CG up to max_rows rows, p(1)-CG up to half; 0: never;
+    no argument: the library's default)."""
+    _check(load().plcg_set_cluster_rows(int(max_rows)))
 
 
 def measure_fp64_fma_rate() -> float:

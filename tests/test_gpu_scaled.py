@@ -1,8 +1,9 @@
-"""GPU parity of FP64 p(1)-CG on systems of at least 2^19 rows, where the
-kernel keeps its bases scaled (Z_j = z^(1)_j / s_j, W_j = z^(0)_j / t_j,
-phat_m / t_m, the K5 dots multiplied back by their scales in the scalar
-step) and rescales by a power of two when a scale leaves [2^-256, 2^256]
-(about every 160 iterations on the 3D Laplacian).  Against the FP64 oracle,
+"""GPU parity of FP64 p(l)-CG on systems of at least 2^19 rows, where the
+kernel keeps its bases scaled (Z_j = z^(l)_j / s_j, W^(k)_j = z^(k)_j /
+t^(k)_j, phat_m / t^(0)_m, the K5 dots multiplied back by their scales in the
+scalar step; l <= 5 on the stencils, l = 1 on CSR and the structured
+27-point operator) and rescales by a power of two when a scale leaves
+[2^-256, 2^256] (about every 160 iterations on the 3D Laplacian at l = 1).  Against the FP64 oracle,
 through the C ABI: iterates before and after a rescale element-wise, whole
 solves, and the CSR and structured 27-point operators with Jacobi."""
 import numpy as np
@@ -89,3 +90,32 @@ def test_jacobi_early_iterates(P, kind):
     x, res = gpu_solve(P, op, b, l=1, interval=interval, rtol=1e-8, precond="jacobi",
                        max_restarts=16)
     assert res.ok and res.true_relres < 1e-8, (res, P.last_error())
+
+
+@pytest.mark.parametrize("l", [2, 3, 4, 5])
+@pytest.mark.parametrize("k", [1, 3, 40, 170, 330])
+def test_3d_scaled_l_iterates_across_rescales(P, lap3d, l, k):
+    """l >= 2 (every basis recurrence with a unit coefficient): x_k
+    element-wise at 1e-11 before and after rescales of the l + 1 scale
+    chains, and the launch is the scaled-basis kernel."""
+    c = lap3d
+    sig = O.chebyshev_shifts(l, *c["interval"])
+    ref = O.plcg(c["op"], c["b"], l=l, sigma=sig, rtol=1e-14, maxit=k, dots_2l1=False)
+    x, res = gpu_solve(P, c["op"], c["b"], l=l, rtol=1e-14, maxit=k, interval=c["interval"])
+    assert res.status == P.PLCG_ERR_MAXIT and res.iters == k
+    assert rel(x, ref.x) <= 1e-11, (l, k, rel(x, ref.x))
+
+
+@pytest.mark.parametrize("l", [2, 3])
+def test_3d_scaled_l_whole_solve_and_2l1_dots(P, lap3d, l):
+    c = lap3d
+    sig = O.chebyshev_shifts(l, *c["interval"])
+    ref = O.plcg(c["op"], c["b"], l=l, sigma=sig, rtol=1e-10, dots_2l1=False)
+    x, res = gpu_solve(P, c["op"], c["b"], l=l, rtol=1e-10, interval=c["interval"])
+    assert res.ok and res.true_relres < 1e-10
+    assert abs(res.iters - ref.iters) <= 1, (res.iters, ref.iters)
+    assert rel(x, ref.x) <= 1e-11
+    ref = O.plcg(c["op"], c["b"], l=l, sigma=sig, rtol=1e-14, maxit=200, dots_2l1=True)
+    x, res = gpu_solve(P, c["op"], c["b"], l=l, rtol=1e-14, maxit=200, interval=c["interval"], dots_2l1=True)
+    assert res.status == P.PLCG_ERR_MAXIT and rel(x, ref.x) <= 1e-11, rel(x, ref.x)
+

@@ -103,7 +103,7 @@ def test_noalloc_matches_plcg_solve_on_two_calls():
             assert r.true_relres < 1e-8
             assert _rel(x, x_ref) <= tol, (kw, _rel(x, x_ref))
             for key in ("kernel", "grid_ctas", "dyn_smem", "lookahead", "staged", "poll_limit",
-                        "force_timeout"):
+                        "force_timeout", "cluster"):
                 assert info[key] == info_ref[key], (kw, key, info[key], info_ref[key])
 
 
@@ -119,6 +119,7 @@ def test_noalloc_bounded_wait_timeout_then_recover():
     d = _desc(plcg, c["op"])
     bt = torch.tensor(c["b"], device="cuda")
     try:
+        plcg.set_cluster_rows(0)   # the grid path: the cluster barrier has no bound to expire
         lib.plcg_debug_set_poll_limit(20000)
         lib.plcg_debug_force_barrier_timeout(1)
         st, _, r, info = _noalloc(torch, plcg, lib, d, bt, l=1, interval=c["interval"], rtol=1e-8)
@@ -128,6 +129,7 @@ def test_noalloc_bounded_wait_timeout_then_recover():
     finally:
         lib.plcg_debug_force_barrier_timeout(0)
         lib.plcg_debug_set_poll_limit(0)
+        plcg.set_cluster_rows()
     st, x, r, _ = _noalloc(torch, plcg, lib, d, bt, l=1, interval=c["interval"], rtol=1e-8)
     assert st == plcg.PLCG_OK and r.true_relres < 1e-8
 
