@@ -647,19 +647,28 @@ def serving(plcg, W, dev):
             for tk in list(pending):
                 r = S.poll(tk)
                 if r is not None:
-                    results.append(r)
+                    results.append((pending[tk], r))
                     del pending[tk]
                     t_last = time.perf_counter()
             if i < len(items) and not pending:
                 time.sleep(max(0.0, items[i][0] - (time.perf_counter() - t0)))
         S.close()
         span = t_last - t0
-        lat = np.array([r.latency for r in results]) * 1e3
-        ok = sum(r.status == 0 for r in results)
+        lat = np.array([r.latency for _, r in results]) * 1e3
+        ok = sum(r.status == 0 for _, r in results)
+        # latency by size class (each request's grid is capped at half the
+        # GPU's resident CTAs, so that a request's bits do not depend on the mix)
+        classes = {}
+        for lo_, hi_, name in ((0, 3e4, "n<3e4"), (3e4, 3e5, "3e4<=n<3e5"), (3e5, 1e12, "n>=3e5")):
+            sel = np.array([r.latency for i_, r in results if lo_ <= items[i_][1].n < hi_]) * 1e3
+            if sel.size:
+                classes[name] = {"requests": int(sel.size), "p50_ms": round(float(np.percentile(sel, 50)), 2),
+                                 "p99_ms": round(float(np.percentile(sel, 99)), 2)}
         return {"requests": len(items), "converged": ok, "window_s": round(items[-1][0], 3),
                 "makespan_s": round(span, 3), "solves_per_s": round(len(items) / span, 1),
                 "p50_latency_ms": round(float(np.percentile(lat, 50)), 2),
                 "p99_latency_ms": round(float(np.percentile(lat, 99)), 2),
+                "latency_by_size": classes,
                 "backlog_drain_s": round(span - items[-1][0], 3)}
 
     reqs = W.serving_stream(duration_s=0.25, rate=2000.0, seed=5)
