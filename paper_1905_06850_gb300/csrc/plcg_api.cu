@@ -497,9 +497,12 @@ static plcg_status build_solve(const plcg_matrix *A, const double *b, double *x,
     // CSR kernels stage each unit's entries in dynamic shared memory (FP64
     // classic CG excepted, see cg_body); the 27-point p(l)-CG kernels stage
     // coefficient and z tiles
+    // CSR kernels stage each unit's entries (FP64 classic CG excepted); the
+    // FP32 27-point kernels stage tiles (classic CG's SpMV without vector slots)
     unsigned dsmem = (op_is_csr(op) && (!cg || f32)) ? csr_stage_bytes(value_bytes)
-                         : (op_is_var27(op) && !cg && f32)
-                             ? v27_tile_bytes((unsigned)sizeof(T), l, op_is_jacobi(op)) : 0u;
+                   : (op_is_var27(op) && f32 && !c32)
+                       ? (cg ? v27_tile_bytes_nv((unsigned)sizeof(T), 0)
+                             : v27_tile_bytes((unsigned)sizeof(T), l, op_is_jacobi(op))) : 0u;
     if (dsmem) {
         CUDA_TRY(cudaFuncSetAttribute(func, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)dsmem));
         CUDA_TRY(cudaFuncSetAttribute(func, cudaFuncAttributePreferredSharedMemoryCarveout,

@@ -153,10 +153,13 @@ constexpr int v27_vec_slots(int l, bool jacobi)
 {
     return l <= 3 ? 2 * l + 3 + (jacobi ? 2 : 0) : 0;
 }
+constexpr unsigned v27_tile_bytes_nv(unsigned value_bytes, int nv)
+{
+    return 16u * ((kV27Buf + 1) / 2) + (unsigned)kV27Buf * (36u + (unsigned)nv) * (unsigned)kV27Slot * value_bytes;
+}
 constexpr unsigned v27_tile_bytes(unsigned value_bytes, int l, bool jacobi)
 {
-    return 16u * ((kV27Buf + 1) / 2) +
-           (unsigned)kV27Buf * (36u + (unsigned)v27_vec_slots(l, jacobi)) * (unsigned)kV27Slot * value_bytes;
+    return v27_tile_bytes_nv(value_bytes, v27_vec_slots(l, jacobi));
 }
 
 // CSR entries (column index + value) each warp of a CSR kernel stages in

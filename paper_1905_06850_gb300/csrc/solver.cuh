@@ -2080,6 +2080,33 @@ __device__ void cg_body(const SolveArgs<T> &a, Smem<T> &s, Grp &grp)
         stage.init();
         __syncthreads();
     }
+    // structured 27-point operator on the whole grid, FP32: p_k = z_k +
+    // beta p_{k-1} gets a sweep of its own (in place, in ring vector 0, which
+    // carries the zero halos), and the SpMV reads p through the shared-memory
+    // tiles of the p(l)-CG sweep -- one barrier more per iteration instead of
+    // forming p at all 27 stencil points (Table 1 charges CG and p(l)-CG the
+    // same SpMV)
+    constexpr bool kTileCG = op_is_var27(OP) && std::is_same<Grp, GridGroup<T>>::value && RPT == 1 &&
+                             sizeof(T) == 4 && sizeof(CT) == 4;
+    Var27Tile<T, 0> tile(plcg_dsm);
+    if constexpr (kTileCG) {
+        pr[0] = pr[1] = a.zring;
+        xi = a.zring + 2 * a.vstride;
+        tile.init(a.st);
+        __syncthreads();
+        // zero the halo before ring vector 0 and the span after every ring
+        // vector: the tiles' z copies reach into them (the grid barrier after
+        // the first residual sweep orders these stores before any copy)
+        const int64_t span = a.vstride - a.n, nzr = a.halo + (int64_t)a.nring * span;
+        for (int64_t e = (int64_t)blockIdx.x * kBlock + threadIdx.x; e < nzr; e += (int64_t)gridDim.x * kBlock) {
+            if (e < a.halo) {
+                a.zring[e - a.halo] = T(0);
+            } else {
+                const int64_t i = (e - a.halo) / span;
+                a.zring[i * a.vstride + a.n + (e - a.halo - i * span)] = T(0);
+            }
+        }
+    }
 
     long long iters = 0, spmvs = 0, restarts = 0, refinements = 0, segments = 0;
     int last_end = kSegConverged;
@@ -2179,47 +2206,94 @@ __device__ void cg_body(const SolveArgs<T> &a, Smem<T> &s, Grp &grp)
             DotAcc<T, VEC> d1;
             int since_flush = 0;
             const int64_t nunits_s = (n + USWEEP - 1) / USWEEP;
-            for (uint32_t u = (uint32_t)grp.unit0(); u < (uint32_t)nunits_s; u += (uint32_t)grp.ustep()) {
-                T c[RPT][VEC], w[RPT][VEC], mi[RPT];
-                uint32_t g0[RPT];
-                bool stg = false;
-                int64_t e0s = 0;
-                if constexpr (kStage) {   // this warp's 32 rows of the unit
-                    const uint32_t w0 = u * USWEEP + (uint32_t)(tid & ~31);
-                    if (a.stage)
-                        stg = stage.stage(csr, w0, min(w0 + 32u, nn), &e0s, a.poll_limit, &a.out->abort);
+            if constexpr (kTileCG) {
+                // p_k in place, then the tiled SpMV on it
+                for (int64_t u = grp.unit0(); u < nunits; u += grp.ustep()) {
+                    const int64_t g = u * UNIT + tid;
+                    if (g < n) pn[g] = (k == 0) ? rc[g] : fma((T)beta, pn[g], rc[g]);
                 }
-#pragma unroll
-                for (int r = 0; r < RPT; ++r) {
-                    g0[r] = u * USWEEP + ((uint32_t)r * kBlock + tid) * VEC;
-                    if (g0[r] >= nn) continue;
-                    if (stg) {
-                        if (k == 0) {
-                            const LdFirst<T> ld{rc};
-                            c[r][0] = ld.one(g0[r]);
-                            w[r][0] = csr_row_staged<T, CT>(csr, stage.col, stage.val, e0s, ld, g0[r]);
+                CG_SYNC();
+                const uint32_t usw = (uint32_t)kBlock;
+                int tb = 0;
+                uint32_t stg_q = 0;
+                auto novec = [](int) -> const T * { return nullptr; };
+                auto tile_issue = [&](int bb, uint32_t uu) {
+                    const bool more = uu < (uint32_t)nunits;
+                    const bool on = tile.issue(bb, more, false, novec, st, static_cast<const T *>(csr.val),
+                                               csr.stride, a.cf_lo, a.cf_hi, pn, a.ws_lo, a.ws_hi,
+                                               more ? uu * usw : 0u, more ? min(uu * usw + usw, nn) : 0u, kBlock);
+                    stg_q = (stg_q & ~(1u << bb)) | ((on ? 1u : 0u) << bb);
+                };
+                // p was written by generic stores before the barrier above; one
+                // proxy fence per issuing thread orders them before the copies
+                if (tid < Var27Tile<T, 0>::kSlots) fence_proxy_async_all();
+                if ((uint32_t)grp.unit0() < (uint32_t)nunits)
+                    for (int bb = 0; bb < kV27Buf - 1; ++bb)
+                        tile_issue(bb, (uint32_t)grp.unit0() + (uint32_t)bb * (uint32_t)grp.ustep());
+                for (uint32_t u = (uint32_t)grp.unit0(); u < (uint32_t)nunits; u += (uint32_t)grp.ustep()) {
+                    const bool stg = (stg_q >> tb) & 1u;
+                    tile_issue((tb + kV27Buf - 1) % kV27Buf, u + (uint32_t)(kV27Buf - 1) * (uint32_t)grp.ustep());
+                    if (stg) tile.wait(tb, a.poll_limit, &a.out->abort);
+                    const uint32_t g = u * usw + (uint32_t)tid;
+                    if (g < nn) {
+                        T c[VEC], w[VEC];
+                        if (stg) {
+                            T zc;
+                            w[0] = tile.template row<T>(tb, tid, &zc);
+                            c[0] = zc;
                         } else {
-                            const LdAxpy<T> ld{rc, po, (T)beta};
-                            c[r][0] = ld.one(g0[r]);
-                            w[r][0] = csr_row_staged<T, CT>(csr, stage.col, stage.val, e0s, ld, g0[r]);
+                            op_parts<T, CT, VEC, OP>(st, csr, Ld1<T>{pn}, g, c, w);
                         }
-                    } else if (k == 0) {
-                        op_apply<T, CT, VEC, OP>(st, csr, cC, cO, LdFirst<T>{rc}, g0[r], c[r], w[r]);
-                    } else {
-                        op_apply<T, CT, VEC, OP>(st, csr, cC, cO, LdAxpy<T>{rc, po, (T)beta}, g0[r], c[r], w[r]);
+                        d1.add(c, w);
+                        if constexpr (op_is_jacobi(OP)) w[0] *= __ldg(static_cast<const T *>(csr.dinv) + g);   // q = M^{-1} A p
+                        vst<T, VEC>(q + g, w);
                     }
-                    if constexpr (op_is_jacobi(OP))
-                        mi[r] = __ldg(static_cast<const T *>(csr.dinv) + g0[r]);
+                    if (++since_flush == kFlushUnits) { d1.flush(); since_flush = 0; }
+                    tb = (tb + 1) % kV27Buf;
                 }
+            } else {
+                for (uint32_t u = (uint32_t)grp.unit0(); u < (uint32_t)nunits_s; u += (uint32_t)grp.ustep()) {
+                    T c[RPT][VEC], w[RPT][VEC], mi[RPT];
+                    uint32_t g0[RPT];
+                    bool stg = false;
+                    int64_t e0s = 0;
+                    if constexpr (kStage) {   // this warp's 32 rows of the unit
+                        const uint32_t w0 = u * USWEEP + (uint32_t)(tid & ~31);
+                        if (a.stage)
+                            stg = stage.stage(csr, w0, min(w0 + 32u, nn), &e0s, a.poll_limit, &a.out->abort);
+                    }
 #pragma unroll
-                for (int r = 0; r < RPT; ++r) {
-                    if (g0[r] >= nn) continue;
-                    vst<T, VEC>(pn + g0[r], c[r]);
-                    d1.add(c[r], w[r]);
-                    if constexpr (op_is_jacobi(OP)) w[r][0] *= mi[r];   // q = M^{-1} A p
-                    vst<T, VEC>(q + g0[r], w[r]);
+                    for (int r = 0; r < RPT; ++r) {
+                        g0[r] = u * USWEEP + ((uint32_t)r * kBlock + tid) * VEC;
+                        if (g0[r] >= nn) continue;
+                        if (stg) {
+                            if (k == 0) {
+                                const LdFirst<T> ld{rc};
+                                c[r][0] = ld.one(g0[r]);
+                                w[r][0] = csr_row_staged<T, CT>(csr, stage.col, stage.val, e0s, ld, g0[r]);
+                            } else {
+                                const LdAxpy<T> ld{rc, po, (T)beta};
+                                c[r][0] = ld.one(g0[r]);
+                                w[r][0] = csr_row_staged<T, CT>(csr, stage.col, stage.val, e0s, ld, g0[r]);
+                            }
+                        } else if (k == 0) {
+                            op_apply<T, CT, VEC, OP>(st, csr, cC, cO, LdFirst<T>{rc}, g0[r], c[r], w[r]);
+                        } else {
+                            op_apply<T, CT, VEC, OP>(st, csr, cC, cO, LdAxpy<T>{rc, po, (T)beta}, g0[r], c[r], w[r]);
+                        }
+                        if constexpr (op_is_jacobi(OP))
+                            mi[r] = __ldg(static_cast<const T *>(csr.dinv) + g0[r]);
+                    }
+#pragma unroll
+                    for (int r = 0; r < RPT; ++r) {
+                        if (g0[r] >= nn) continue;
+                        vst<T, VEC>(pn + g0[r], c[r]);
+                        d1.add(c[r], w[r]);
+                        if constexpr (op_is_jacobi(OP)) w[r][0] *= mi[r];   // q = M^{-1} A p
+                        vst<T, VEC>(q + g0[r], w[r]);
+                    }
+                    if (++since_flush == kFlushUnits) { d1.flush(); since_flush = 0; }
                 }
-                if (++since_flush == kFlushUnits) { d1.flush(); since_flush = 0; }
             }
             d1.flush();
             spmvs++;

@@ -157,8 +157,9 @@ def test_var27_ragged_grids(P, dims):
 
 @pytest.mark.parametrize("dims", [(1, 1, 1), (3, 1, 4), (33, 3, 2), (5, 2, 3), (17, 9, 13), (40, 30, 20)])
 def test_var27_fp32_tiles_ragged_grids(P, dims):
-    """The FP32 p(l)-CG sweep stages shared-memory tiles (coefficients, z
-    lines and, in the steady state, the vector operands) and applies rows
+    """The FP32 p(l)-CG sweep (and classic CG's SpMV) stages shared-memory
+    tiles (coefficients, z lines and, in the p(l)-CG steady state, the vector
+    operands) and applies rows
     without boundary tests (out-of-grid entries stored as zero, zero halos
     around the arrays): ragged and degenerate grids, units that straddle the
     grid's ends, l = 1..5 with and without Jacobi (l > 3 stages the operator
@@ -170,7 +171,8 @@ def test_var27_fp32_tiles_ragged_grids(P, dims):
     A = W.to_scipy(W.fp32_rounded(op)).tocsc()
     xs = spl.spsolve(A, b)
     for kw in ({"l": 1}, {"l": 2}, {"l": 3}, {"l": 1, "precond": "jacobi"}, {"l": 3, "precond": "jacobi"},
-               {"l": 4}, {"l": 5, "precond": "jacobi"}):   # l > 3: tiles without vector slots
+               {"l": 4}, {"l": 5, "precond": "jacobi"},   # l > 3: tiles without vector slots
+               {"method": "cg"}, {"method": "cg", "precond": "jacobi"}):   # classic CG's tiled SpMV
         oop = W.fp32_rounded(op)
         interval = W.jacobi_shift_interval(oop) if "precond" in kw else W.shift_interval(oop)
         x, res = gpu_solve(P, op, b, prec="fp32", interval=interval, rtol=1e-10, max_restarts=64, **kw)
