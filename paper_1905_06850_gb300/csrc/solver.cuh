@@ -2088,10 +2088,17 @@ __device__ void cg_body(const SolveArgs<T> &a, Smem<T> &s, Grp &grp)
     // same SpMV)
     constexpr bool kTileCG = op_is_var27(OP) && std::is_same<Grp, GridGroup<T>>::value && RPT == 1 &&
                              sizeof(T) == 4 && sizeof(CT) == 4;
+    // FP64 on the whole grid: the same separate p sweep, since GB300's FP64
+    // units, not HBM, bound the FP64 sweeps and forming p on the fly costs an
+    // FP64 FMA at every stencil point or matrix entry (one pass more, 7 of 18
+    // FP64 instructions per row fewer on the 7-point stencil)
+    constexpr bool kSepP = kTileCG || (sizeof(T) == 8 && std::is_same<Grp, GridGroup<T>>::value && RPT == 1);
     Var27Tile<T, 0> tile(plcg_dsm);
+    if constexpr (kSepP) {
+        pr[0] = pr[1] = a.zring;   // p updated in place
+        if constexpr (kF32) xi = a.zring + 2 * a.vstride;
+    }
     if constexpr (kTileCG) {
-        pr[0] = pr[1] = a.zring;
-        xi = a.zring + 2 * a.vstride;
         tile.init(a.st);
         __syncthreads();
         // zero the halo before ring vector 0 and the span after every ring
@@ -2206,13 +2213,37 @@ __device__ void cg_body(const SolveArgs<T> &a, Smem<T> &s, Grp &grp)
             DotAcc<T, VEC> d1;
             int since_flush = 0;
             const int64_t nunits_s = (n + USWEEP - 1) / USWEEP;
-            if constexpr (kTileCG) {
-                // p_k in place, then the tiled SpMV on it
+            if constexpr (kSepP) {
+                // p_k in place
                 for (int64_t u = grp.unit0(); u < nunits; u += grp.ustep()) {
-                    const int64_t g = u * UNIT + tid;
-                    if (g < n) pn[g] = (k == 0) ? rc[g] : fma((T)beta, pn[g], rc[g]);
+                    const int64_t g0 = u * UNIT + (int64_t)tid * VEC;
+                    if (g0 >= n) continue;
+                    T pv[VEC], zv[VEC];
+                    vld<T, VEC>(rc + g0, zv);
+                    if (k == 0) {
+                        vst<T, VEC>(pn + g0, zv);
+                    } else {
+                        vld<T, VEC>(pn + g0, pv);
+#pragma unroll
+                        for (int v = 0; v < VEC; ++v) pv[v] = fma((T)beta, pv[v], zv[v]);
+                        vst<T, VEC>(pn + g0, pv);
+                    }
                 }
                 CG_SYNC();
+            }
+            if constexpr (kSepP && !kTileCG) {
+                // q = A p_k and (p_k, A p_k) from the stored p
+                for (uint32_t u = (uint32_t)grp.unit0(); u < (uint32_t)nunits; u += (uint32_t)grp.ustep()) {
+                    const uint32_t g0 = u * (uint32_t)UNIT + (uint32_t)tid * VEC;
+                    if (g0 >= nn) continue;
+                    T c[VEC], w[VEC];
+                    op_apply<T, CT, VEC, OP>(st, csr, cC, cO, Ld1<T>{pn}, g0, c, w);
+                    d1.add(c, w);
+                    if constexpr (op_is_jacobi(OP)) w[0] *= __ldg(static_cast<const T *>(csr.dinv) + g0);
+                    vst<T, VEC>(q + g0, w);
+                    if (++since_flush == kFlushUnits) { d1.flush(); since_flush = 0; }
+                }
+            } else if constexpr (kTileCG) {
                 const uint32_t usw = (uint32_t)kBlock;
                 int tb = 0;
                 uint32_t stg_q = 0;
