@@ -1,4 +1,4 @@
-"""Host model of FP64 p(1)-CG with scaled bases (no GPU).
+"""Host models of FP64 p(l)-CG with scaled bases (no GPU).
 
 The GPU kernel for FP64 p(1)-CG on large systems stores its bases scaled,
 Z_j = z^(1)_j / s_j and W_j = z^(0)_j / t_j (and the direction phat_m / t_m),
@@ -10,6 +10,8 @@ numpy twice -- with unscaled bases, and with scaled bases whose range bound
 is made tiny (2^-1 .. 2^1) so that almost every iteration rescales -- and
 checks both against the FP64 oracle's iterates: the transformation is exact
 up to rounding, and the power-of-two rescaling path is exercised densely.
+A second model does the same for any l (the stencil kernels take scaled
+bases up to l = 5): one scale chain for z^(l) and one per lower basis.
 """
 import numpy as np
 import pytest
