@@ -258,10 +258,13 @@ typedef struct plcg_server plcg_server;
  * submitted requests in FIFO order as soon as (a) their device workspace fits
  * the remaining mem_budget_bytes (0: 80% of the free memory at creation),
  * (b) one of max_inflight stream slots is free (0: 32), and (c) their thread
- * blocks fit on the GPU next to the solves already running.  Each admitted
- * request runs as its own persistent launch (Algorithm 1 or CG, as in
- * plcg_solve) on its own stream, so requests of different sizes overlap on
- * the device and new requests start while others are running.  A request's
+ * blocks fit on the GPU next to the solves already running; a request that
+ * does not fit yet lets later requests that fit start before it for up to
+ * 100 ms of its waiting time (backfilling), then admission waits for it.
+ * Each admitted request runs as its own persistent launch (Algorithm 1 or
+ * CG, as in plcg_solve) on its own stream, so requests of different sizes
+ * overlap on the device and new requests start while others are running.
+ * A request's
  * grid size depends only on the request, so its result is bit-identical
  * whether it runs alone or in a mix.  Errors: PLCG_ERR_INVALID, PLCG_ERR_CUDA. */
 plcg_status plcg_server_create(size_t mem_budget_bytes, int max_inflight, plcg_server **out);
@@ -355,6 +358,16 @@ typedef struct {
                                    this many blocks (small systems)             */
 } plcg_launch_info;
 void plcg_debug_last_launch(plcg_launch_info *out);
+
+/* Test hook (no GPU work): the server's admission pass over a queue of n
+ * requests in FIFO order -- request i needs bytes[i] of workspace, occupies
+ * share[i] SMs and has waited waited_s[i] seconds -- given mem_free bytes of
+ * budget left, sm_used SMs occupied by running solves, num_sms SMs and
+ * free_slots stream slots.  Writes the admitted indices, in order, to
+ * admitted[] (room for n) and returns their count. */
+int plcg_debug_server_admission(int n, const uint64_t *bytes, const double *share,
+                                const double *waited_s, uint64_t mem_free, double sm_used,
+                                int num_sms, int free_slots, int *admitted);
 
 #ifdef __cplusplus
 }

@@ -495,13 +495,11 @@ static plcg_status build_solve(const plcg_matrix *A, const double *b, double *x,
     const void *func = kernel_ptr(f32, op, vec, cg ? 0 : l, cg, sc, c32);
     if (!func) return fail(PLCG_ERR_UNIMPL, "no kernel for prec=%d op=%d vec=%d l=%d", prm->prec, op, vec, l);
     // CSR kernels stage each unit's entries in dynamic shared memory (FP64
-    // classic CG excepted, see cg_body); the 27-point p(l)-CG kernels stage
-    // coefficient and z tiles
-    // CSR kernels stage each unit's entries (FP64 classic CG excepted); the
-    // FP32 27-point kernels stage tiles (classic CG's SpMV without vector slots)
+    // classic CG excepted, see cg_body); the FP32 27-point kernels stage
+    // coefficient and z tiles (classic CG's SpMV without vector slots)
     unsigned dsmem = (op_is_csr(op) && (!cg || f32)) ? csr_stage_bytes(value_bytes)
                    : (op_is_var27(op) && f32 && !c32)
-                       ? (cg ? v27_tile_bytes_nv((unsigned)sizeof(T), 0)
+                       ? (cg ? v27_tile_bytes_cg((unsigned)sizeof(T))
                              : v27_tile_bytes((unsigned)sizeof(T), l, op_is_jacobi(op))) : 0u;
     if (dsmem) {
         CUDA_TRY(cudaFuncSetAttribute(func, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)dsmem));
@@ -1261,7 +1259,8 @@ extern "C" plcg_status plcg_solve_batched(int count, plcg_matrix *const *A, cons
 // in FIFO order whenever their workspace fits the device-memory budget, a
 // stream slot is free and their CTAs fit next to the in-flight solves (so
 // every cooperative grid can be resident at once and its grid barriers always
-// complete).  Each admitted request runs as its own persistent launch on its
+// complete); a request that does not fit yet lets later ones that do fit
+// pass it for a bounded time (backfilling).  Each admitted request runs as its own persistent launch on its
 // own stream; its grid size depends only on the request (its n, kernel and
 // the per-request cap), so a request gives the same bits alone or in a mix.
 namespace {
@@ -1284,6 +1283,46 @@ struct ServerReq {
 };
 
 }  // namespace
+
+// Admission, request by request in FIFO order (while a stream slot is
+// free): a request starts when its workspace fits the remaining budget and
+// its CTAs fit next to the running solves (sm_used: SMs their CTAs occupy;
+// the first request always fits, its grid being capped at the GPU's
+// resident CTAs).  One that does not fit yet is passed by later requests
+// that do (backfilling) until it has waited kServerBackfillWindow; then
+// admission stops at it, so that a stream of small requests cannot keep it
+// out.
+constexpr double kServerBackfillWindow = 0.1;   // seconds
+enum { kAdmitStart = 0, kAdmitSkip = 1, kAdmitStop = 2 };
+static int admit_decision(size_t bytes, double share, double waited_s, size_t mem_free, double sm_used,
+                          int num_sms)
+{
+    const bool fits = bytes <= mem_free && !(sm_used > 0.0 && sm_used + share > num_sms + 1e-9);
+    if (fits) return kAdmitStart;
+    return waited_s >= kServerBackfillWindow ? kAdmitStop : kAdmitSkip;
+}
+
+// Test hook: the admission pass over a queue of n requests (workspace
+// bytes[i], SM share[i], waited_s[i] seconds in the queue) given the free
+// budget, the SMs in use, the SM count and the free stream slots.  Writes the
+// indices of the admitted requests, in admission order, to admitted[] and
+// returns their count.
+extern "C" int plcg_debug_server_admission(int n, const uint64_t *bytes, const double *share,
+                                           const double *waited_s, uint64_t mem_free, double sm_used,
+                                           int num_sms, int free_slots, int *admitted)
+{
+    int k = 0;
+    for (int i = 0; i < n && free_slots > 0; ++i) {
+        const int d = admit_decision((size_t)bytes[i], share[i], waited_s[i], (size_t)mem_free, sm_used, num_sms);
+        if (d == kAdmitStop) break;
+        if (d == kAdmitSkip) continue;
+        admitted[k++] = i;
+        mem_free -= bytes[i];
+        sm_used += share[i];
+        --free_slots;
+    }
+    return k;
+}
 
 struct plcg_server {
     int device = 0;
@@ -1362,12 +1401,18 @@ static void server_loop(plcg_server *S)
     std::unique_lock<std::mutex> lk(S->mu);
     for (;;) {
         bool progress = false;
-        // admission: FIFO, by memory budget, stream slots and resident CTAs
-        while (!S->queue.empty() && !S->free_slots.empty()) {
-            auto q = S->queue.front();
-            if (q->bytes > S->budget - S->used) break;
-            if (S->sm_used > 0.0 && S->sm_used + q->sm_share > S->num_sms + 1e-9) break;
-            S->queue.pop_front();
+        const auto now = std::chrono::steady_clock::now();
+        for (auto it = S->queue.begin(); it != S->queue.end() && !S->free_slots.empty();) {
+            auto q = *it;
+            const int d = admit_decision(q->bytes, q->sm_share,
+                                         std::chrono::duration<double>(now - q->t_submit).count(),
+                                         S->budget - S->used, S->sm_used, S->num_sms);
+            if (d == kAdmitStop) break;
+            if (d == kAdmitSkip) {
+                ++it;
+                continue;
+            }
+            it = S->queue.erase(it);
             q->slot = S->free_slots.back();
             S->free_slots.pop_back();
             S->used += q->bytes;

@@ -126,16 +126,28 @@ struct SolveArgs {
     int trace_cap;            // pairs trace can hold
 };
 
-// Structured 27-point tiles: per sweep unit, 36 shared-memory slots of
-// kV27Slot elements -- the diagonal and 13 forward coefficient segments, the
-// 13 backward segments, the 9 line segments of z around the unit -- and, for
-// l <= 3, v27_vec_slots(l, jacobi) slots of the vector operands the
-// steady-state p(l)-CG sweep streams (z^(l)_{i-1}, the l current and l
-// previous z^(k), p, the iterate and, with Jacobi, 1/a_gg and a_gg).
-// kV27Buf buffers, each with its mbarrier: the unit being computed and the
-// next kV27Buf - 1 in flight.
+// Structured 27-point tiles: per sweep unit, shared-memory slots of
+// kV27Slot elements -- the diagonal and 13 forward coefficient segments, with
+// SB (staged backward) the 13 backward segments (forward array k at rows
+// g - d_k), and the 9 line segments of z around the unit -- and, for l <= 3,
+// v27_vec_slots(l, jacobi) slots of the vector operands the steady-state
+// p(l)-CG sweep streams (z^(l)_{i-1}, the l current and l previous z^(k), p,
+// the iterate and, with Jacobi, 1/a_gg; a_gg is the diagonal slot).  Without SB the backward coefficients come through L2
+// (another unit's forward copies bring them there shortly before or after)
+// and the smaller tiles leave room for a third buffer.  v27_bufs(SB)
+// buffers, each with its mbarrier: the unit being computed and the next
+// ones in flight.  The dynamic shared memory starts with the mbarriers, then
+// (without SB) the 13 base pointers of the backward loads, then the buffers.
 constexpr int kV27Slot = 256 + 16;
-constexpr int kV27Buf = 2;
+PLCG_HD constexpr int v27_bufs(bool sb) { return sb ? 2 : 3; }
+PLCG_HD constexpr int v27_op_slots(bool sb) { return 14 + (sb ? 13 : 0) + 9; }
+PLCG_HD constexpr unsigned v27_hdr(bool sb) { return 16u * ((unsigned)(v27_bufs(sb) + 1) / 2u) + (sb ? 0u : 112u); }
+// the choice per kernel family (measured on GB300, 128^3 heterogeneous
+// operator): the p(l)-CG sweep, whose vector slots make its tiles large,
+// keeps two buffers of fully staged tiles; classic CG's SpMV-only tiles take
+// the third buffer
+constexpr bool kV27StageBwdPlcg = true;
+constexpr bool kV27StageBwdCg = false;
 
 // The 13 forward offsets (dz, dy, dx) of the structured 27-point operator,
 // lexicographic (the order of its coefficient arrays 1..13).
@@ -151,15 +163,20 @@ PLCG_HD constexpr int v27_dx(int k) { return k == 0 ? 1 : k < 4 ? k - 2 : (k - 4
 PLCG_HD constexpr int64_t v27_halo(int64_t nx, int64_t ny) { return (nx * ny + nx + 8 + 63) / 64 * 64; }
 constexpr int v27_vec_slots(int l, bool jacobi)
 {
-    return l <= 3 ? 2 * l + 3 + (jacobi ? 2 : 0) : 0;
+    return l <= 3 ? 2 * l + 3 + (jacobi ? 1 : 0) : 0;
 }
-constexpr unsigned v27_tile_bytes_nv(unsigned value_bytes, int nv)
+constexpr unsigned v27_tile_bytes_nv(unsigned value_bytes, int nv, bool sb)
 {
-    return 16u * ((kV27Buf + 1) / 2) + (unsigned)kV27Buf * (36u + (unsigned)nv) * (unsigned)kV27Slot * value_bytes;
+    return v27_hdr(sb) + (unsigned)v27_bufs(sb) * (unsigned)(v27_op_slots(sb) + nv) * (unsigned)kV27Slot * value_bytes;
 }
+// dynamic shared memory of the p(l)-CG kernels and of classic CG's
 constexpr unsigned v27_tile_bytes(unsigned value_bytes, int l, bool jacobi)
 {
-    return v27_tile_bytes_nv(value_bytes, v27_vec_slots(l, jacobi));
+    return v27_tile_bytes_nv(value_bytes, v27_vec_slots(l, jacobi), kV27StageBwdPlcg);
+}
+constexpr unsigned v27_tile_bytes_cg(unsigned value_bytes)
+{
+    return v27_tile_bytes_nv(value_bytes, 0, kV27StageBwdCg);
 }
 
 // CSR entries (column index + value) each warp of a CSR kernel stages in

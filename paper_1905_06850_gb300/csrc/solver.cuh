@@ -499,46 +499,59 @@ __device__ __forceinline__ V csr_row_staged(const CsrDesc &A, const int32_t *sco
 }
 
 // Per-CTA tiles of the structured 27-point operator, one per sweep unit of
-// rows [r0, r1) (dynamic shared memory: kV27Buf mbarriers in 16-byte pairs,
-// then kV27Buf buffers of 36 + NV slots of kV27Slot elements): slots 0..13 the diagonal and forward
-// coefficients of the unit's rows, 14..26 the backward coefficients (forward
-// array k at rows g - d_k), 27..35 the nine line segments of z around the
-// unit ((dz, dy) in {-1,0,1}^2, x - 1 .. x + 1), 36.. the unit's rows of NV
-// vector operands (the steady-state sweep's; other sweeps load those from
-// global memory).  One bulk copy per slot, each rounded out to 16 bytes; the
-// rounding puts element g of an operator slot at a shift that is fixed for
-// the whole solve (the arrays and ring vectors start on 256-byte boundaries
-// and units on multiples of 4 rows), so the shifts are computed once; vector
-// slots start at their first row.  The sweep keeps the next kV27Buf - 1
-// units' copies in flight while it computes from the current buffer.  A unit whose
-// operator copies would leave the arrays' allocations falls back to global
-// loads (vectors and the inverse diagonal are padded to 256 bytes, so their
-// rounded copies always stay inside).
-template <typename T, int NV>
+// rows [r0, r1) (dynamic shared memory: v27_hdr(SB) bytes of header -- the
+// NB mbarriers in 16-byte pairs and, without SB, the 13 base pointers of the
+// backward loads -- then NB buffers of kSlots slots of kV27Slot elements):
+// slots 0..13 the diagonal and forward coefficients of the unit's rows; with
+// SB slots 14..26 the backward coefficients (forward array k at rows g - d_k,
+// by symmetry); then the nine line segments of z around the unit ((dz, dy)
+// in {-1,0,1}^2, x - 1 .. x + 1); then the unit's rows of NV vector operands
+// (the steady-state sweep's; other sweeps load those from global memory).
+// One bulk copy per slot, each rounded out to 16 bytes; the rounding puts
+// element g of a backward or z slot at a shift that is fixed for the whole
+// solve (the arrays and ring vectors start on 256-byte boundaries and units
+// on multiples of 4 rows), so the shifts are computed once; forward and
+// vector slots start at their first row.  The sweep keeps the next NB - 1
+// units' copies in flight while it computes from the current buffer.
+// Without SB the backward coefficients come through L2, loaded before the
+// wait for the unit's copies.  A unit whose copies would leave the arrays'
+// allocations falls back to global loads (vectors are padded to 256 bytes,
+// so their rounded copies always stay inside).
+template <typename T, int NV, bool SB>
 struct Var27Tile {
     static constexpr int A = 16 / (int)sizeof(T);   // elements per 16 bytes
-    static constexpr int kSlots = 36 + NV;
+    static constexpr int NB = v27_bufs(SB);          // buffers
+    static constexpr int kZ = SB ? 27 : 14;          // first z slot
+    static constexpr int kV = v27_op_slots(SB);      // first vector slot
+    static constexpr int kSlots = kV + NV;
     static constexpr int kBuf = kSlots * kV27Slot;   // elements per buffer
-    static constexpr int kHdr = 16 * ((kV27Buf + 1) / 2);
-    uint64_t *bar;                                   // bar[0 .. kV27Buf-1]
+    uint64_t *bar;                                   // bar[0 .. NB-1]
+    const T **bwd;                                   // without SB: bwd[k] + g, backward coefficient k of row g
     T *slot0;
     uint32_t parity = 0;          // bit b: the phase buffer b waits for next
     uint32_t shb = 0, shz = 0;    // 2-bit shifts of the backward and z slots
     __device__ __forceinline__ explicit Var27Tile(unsigned char *dsm)
-        : bar(reinterpret_cast<uint64_t *>(dsm)), slot0(reinterpret_cast<T *>(dsm + kHdr))
+        : bar(reinterpret_cast<uint64_t *>(dsm)),
+          bwd(reinterpret_cast<const T **>(dsm + 16 * ((NB + 1) / 2))),
+          slot0(reinterpret_cast<T *>(dsm + v27_hdr(SB)))
     {
     }
-    __device__ __forceinline__ void init(const StencilDesc &st)
+    // Needs a __syncthreads() before the first issue().
+    __device__ __forceinline__ void init(const StencilDesc &st, const T *coef, int64_t cstride)
     {
+        const int64_t nx = st.nx, nxy = (int64_t)st.nx * st.ny;
         if (threadIdx.x == 0)
-            for (int b = 0; b < kV27Buf; ++b) mbar_init(bar + b, kSlots);
-        const int nx = st.nx, nxy = st.nx * st.ny;
+            for (int b = 0; b < NB; ++b) mbar_init(bar + b, kSlots);
+        if (!SB && threadIdx.x < 13) {
+            const int k = threadIdx.x;
+            bwd[k] = coef + (1 + k) * cstride - (v27_dz(k) * nxy + v27_dy(k) * nx + v27_dx(k));
+        }
         for (int k = 0; k < 13; ++k) {
-            const int off = v27_dz(k) * nxy + v27_dy(k) * nx + v27_dx(k);
+            const int off = v27_dz(k) * (int)nxy + v27_dy(k) * (int)nx + v27_dx(k);
             shb |= (uint32_t)(((-off) % A + A) % A) << (2 * k);
         }
         for (int q = 0; q < 9; ++q) {
-            const int d = (q / 3 - 1) * nxy + (q % 3 - 1) * nx;
+            const int d = (q / 3 - 1) * (int)nxy + (q % 3 - 1) * (int)nx;
             shz |= (uint32_t)(((d - 1) % A + A) % A) << (2 * q);
         }
     }
@@ -547,21 +560,31 @@ struct Var27Tile {
     // Vector slot j of buffer buf (element t = row r0 + t).
     __device__ __forceinline__ const T *vec(int buf, int j) const
     {
-        return slot0 + buf * kBuf + (36 + j) * kV27Slot;
+        return slot0 + buf * kBuf + (kV + j) * kV27Slot;
+    }
+    // a_gg of row r0 + t (the diagonal slot).
+    __device__ __forceinline__ T diag(int buf, int t) const { return slot0[buf * kBuf + t]; }
+    // Without SB: the backward coefficients of row g (issued before wait():
+    // their L2 latency overlaps the copies').
+    __device__ __forceinline__ void backward(uint32_t g, T (&bw)[13]) const
+    {
+        if constexpr (!SB) {
+#pragma unroll
+            for (int k = 0; k < 13; ++k) bw[k] = __ldg(bwd[k] + g);
+        }
     }
     // Start staging rows [r0, r1) in buffer buf (`want` false: nothing to
     // stage, the barrier alone; `vecs`: also the vector slots, vsrc(j) giving
-    // vector j).  Threads 0..35 each own one operator slot: they check that
+    // vector j).  Threads 0..kV-1 each own one operator slot: they check that
     // their 16-byte-rounded range stays inside its allocation ([clo, chi) for
     // coefficients, [zlo, zhi) for z), the first `nthreads` threads agree on
     // the result with a barrier reduction (which also orders every read of
     // the buffer's previous unit before the new copies: those reads have
     // completed into registers, and the async-proxy writes follow the
-    // barrier), and threads
-    // 0..kSlots-1 issue their copies, each arriving on the buffer's mbarrier
-    // (init count kSlots) with its bytes.  Returns false when the unit is to
-    // be read from global memory; otherwise every thread calls wait() before
-    // reading the tile.
+    // barrier), and threads 0..kSlots-1 issue their copies, each arriving on
+    // the buffer's mbarrier (init count kSlots) with its bytes.  Returns false
+    // when the unit is to be read from global memory; otherwise every thread
+    // calls wait() before reading the tile.
     template <class VSrc>
     __device__ __forceinline__ bool issue(int buf, bool want, bool vecs, const VSrc &vsrc, const StencilDesc &st,
                                           const T *coef, int64_t cstride, const char *clo, const char *chi,
@@ -571,8 +594,8 @@ struct Var27Tile {
         const int sl = threadIdx.x;
         uintptr_t b0 = 0, b1 = 0;
         int ok = 1;
-        if (sl < 36 && !want) ok = 0;
-        if (sl < 36 && want) {
+        if (sl < kV && !want) ok = 0;
+        if (sl < kV && want) {
             const int64_t nx = st.nx, nxy = (int64_t)st.nx * st.ny;
             const T *base;
             int64_t lo, hi;
@@ -580,28 +603,28 @@ struct Var27Tile {
                 base = coef + sl * cstride;
                 lo = r0;
                 hi = r1;
-            } else if (sl < 27) {
+            } else if (sl < kZ) {
                 const int k = sl - 14;
                 const int64_t off = v27_dz(k) * nxy + v27_dy(k) * nx + v27_dx(k);
                 base = coef + (1 + k) * cstride;
                 lo = (int64_t)r0 - off;   // may start in the zero halo before the arrays
                 hi = (int64_t)r1 - off;
             } else {
-                const int q = sl - 27;
+                const int q = sl - kZ;
                 const int64_t d = (q / 3 - 1) * nxy + (q % 3 - 1) * nx;
                 base = z;
                 lo = (int64_t)r0 + d - 1;
                 hi = (int64_t)r1 + d + 1;
             }
             if (hi > lo) {
-                const char *mlo = sl < 27 ? clo : zlo, *mhi = sl < 27 ? chi : zhi;
+                const char *mlo = sl < kZ ? clo : zlo, *mhi = sl < kZ ? chi : zhi;
                 b0 = reinterpret_cast<uintptr_t>(base + lo) & ~uintptr_t(15);
                 b1 = (reinterpret_cast<uintptr_t>(base + hi) + 15) & ~uintptr_t(15);
                 ok = b0 >= reinterpret_cast<uintptr_t>(mlo) && b1 <= reinterpret_cast<uintptr_t>(mhi) &&
                      b1 - b0 <= (uintptr_t)(kV27Slot * sizeof(T));
             }
-        } else if (NV > 0 && sl >= 36 && sl < kSlots && want && vecs) {
-            const T *base = vsrc(sl - 36);
+        } else if (NV > 0 && sl >= kV && sl < kSlots && want && vecs) {
+            const T *base = vsrc(sl - kV);
             b0 = reinterpret_cast<uintptr_t>(base + r0);
             b1 = (reinterpret_cast<uintptr_t>(base + r1) + 15) & ~uintptr_t(15);
         }
@@ -633,14 +656,15 @@ struct Var27Tile {
         parity ^= 1u << buf;
     }
     // (A z)_g for row g = r0 + t of the unit staged in buffer buf (z's centre
-    // value in *zc).  No boundary tests: entries towards cells outside the
-    // grid are stored as zero and every z value a copy brings in is finite
-    // (z itself, or the zero halos around the ring vectors).
+    // value in *zc; without SB, bw holds backward()'s coefficients of the
+    // row).  No boundary tests: entries towards cells outside the grid are
+    // stored as zero and every z value a copy brings in is finite (z itself,
+    // or the zero halos around the ring vectors).
     template <typename V>
-    __device__ __forceinline__ V row(int buf, int t, V *zc) const
+    __device__ __forceinline__ V row(int buf, int t, const T (&bw)[13], V *zc) const
     {
         const T *slot = slot0 + buf * kBuf;
-        const T *zs = slot + 27 * kV27Slot;
+        const T *zs = slot + kZ * kV27Slot;
         auto zat = [&](int dz, int dy, int dx) -> V {
             const int q = (dz + 1) * 3 + (dy + 1);
             return (V)zs[q * kV27Slot + t + 1 + dx + sz(q)];
@@ -652,7 +676,8 @@ struct Var27Tile {
         for (int k = 0; k < 13; ++k) {
             const int dz = v27_dz(k), dy = v27_dy(k), dx = v27_dx(k);
             s = fma((V)slot[(1 + k) * kV27Slot + t], zat(dz, dy, dx), s);
-            s = fma((V)slot[(14 + k) * kV27Slot + t + sb(k)], zat(-dz, -dy, -dx), s);
+            const V b = SB ? (V)slot[(14 + k) * kV27Slot + t + sb(k)] : (V)bw[k];
+            s = fma(b, zat(-dz, -dy, -dx), s);
         }
         return s;
     }
@@ -1558,9 +1583,10 @@ __device__ void plcg_body(const SolveArgs<T> &a, Smem<T> &s, Grp &grp)
     constexpr bool kTile = op_is_var27(OP) && std::is_same<Grp, GridGroup<T>>::value && RPT == 1 &&
                            sizeof(T) == 4 && sizeof(CT) == 4;
     constexpr int kNV = kTile ? v27_vec_slots(L, op_is_jacobi(OP)) : 0;
-    Var27Tile<T, kNV> tile(plcg_dsm);
+    using Tile = Var27Tile<T, kNV, kV27StageBwdPlcg>;
+    Tile tile(plcg_dsm);
     if constexpr (kTile) {
-        tile.init(a.st);
+        tile.init(a.st, static_cast<const T *>(a.csr.val), a.csr.stride);
         __syncthreads();
         // zero the halo before ring vector 0 and the span after every ring
         // vector (rows n .. vstride-1): the tiles' z-line copies reach into
@@ -1785,9 +1811,8 @@ __device__ void plcg_body(const SolveArgs<T> &a, Smem<T> &s, Grp &grp)
                     if (j <= L) return C.cur[j - 1];
                     if (j <= 2 * L) return C.prv[j - 1 - L];
                     if (j == 2 * L + 1) return pvec;
-                    if (j == 2 * L + 2) return xi;
-                    if (j == 2 * L + 3) return static_cast<const T *>(csr.dinv);
-                    return reinterpret_cast<const T *>(static_cast<const CT *>(csr.diag));
+                    if (j == 2 * L + 2) return static_cast<const T *>(xi);
+                    return static_cast<const T *>(csr.dinv);
                 };
                 // stage unit uu (if it exists) in buffer bb
                 auto tile_issue = [&](int bb, uint32_t uu) {
@@ -1797,15 +1822,15 @@ __device__ void plcg_body(const SolveArgs<T> &a, Smem<T> &s, Grp &grp)
                                                more ? min(uu * usw + usw, nn) : 0u, nsw);
                     stg_q = (stg_q & ~(1u << bb)) | ((on ? 1u : 0u) << bb);
                 };
-                if constexpr (kTile) {   // the first kV27Buf - 1 units
+                if constexpr (kTile) {   // the first NB - 1 units
                     // z^(l)_i and the vectors were written by generic stores
                     // before the grid barrier that began this sweep; nothing
                     // the copies read is written during it.  One proxy fence
                     // per issuing thread orders those stores before all of
                     // the sweep's copies.
-                    if (tid < Var27Tile<T, kNV>::kSlots) fence_proxy_async_all();
+                    if (tid < Tile::kSlots) fence_proxy_async_all();
                     if ((uint32_t)grp.unit0() < nunits_s)
-                        for (int bb = 0; bb < kV27Buf - 1; ++bb)
+                        for (int bb = 0; bb < Tile::NB - 1; ++bb)
                             tile_issue(bb, (uint32_t)grp.unit0() + (uint32_t)bb * (uint32_t)grp.ustep());
                 }
                 for (uint32_t u = (uint32_t)grp.unit0(); u < nunits_s; u += (uint32_t)grp.ustep()) {
@@ -1823,10 +1848,12 @@ __device__ void plcg_body(const SolveArgs<T> &a, Smem<T> &s, Grp &grp)
                         if (a.stage)
                             stg = stage.stage(csr, w0, min(w0 + 32u, nn), &e0s, a.poll_limit, &a.out->abort);
                     }
-                    if constexpr (kTile) {    // the copies kV27Buf - 1 units ahead; this unit's tile
+                    T bw[13];   // the tiled unit's backward coefficients (row g0[0])
+                    if constexpr (kTile) {    // the copies NB - 1 units ahead; this unit's tile
                         stg = (stg_q >> tb) & 1u;
-                        tile_issue((tb + kV27Buf - 1) % kV27Buf,
-                                   u + (uint32_t)(kV27Buf - 1) * (uint32_t)grp.ustep());
+                        tile_issue((tb + Tile::NB - 1) % Tile::NB,
+                                   u + (uint32_t)(Tile::NB - 1) * (uint32_t)grp.ustep());
+                        if (stg && ok[0]) tile.backward(g0[0], bw);
                         if (stg) tile.wait(tb, a.poll_limit, &a.out->abort);
                     }
                     // -- loads
@@ -1864,13 +1891,18 @@ __device__ void plcg_body(const SolveArgs<T> &a, Smem<T> &s, Grp &grp)
                                 xv[r][0] = tile.vec(tb, 2 * L + 2)[t];
                                 if constexpr (op_is_jacobi(OP)) {
                                     c[r][0] = tile.vec(tb, 2 * L + 3)[t];   // 1 / a_gg for now
-                                    dg[r] = tile.vec(tb, 2 * L + 4)[t];
+                                    dg[r] = tile.diag(tb, t);                // a_gg: the diagonal slot
                                 }
                                 continue;
                             }
-                            if constexpr (op_is_jacobi(OP)) {
-                                c[r][0] = __ldg(static_cast<const T *>(csr.dinv) + g0[r]);   // 1 / a_gg for now
-                                dg[r] = coef_cast<T>(__ldg(static_cast<const CT *>(csr.diag) + g0[r]));
+                            if constexpr (op_is_jacobi(OP)) {   // 1 / a_gg for now
+                                if (stg) {
+                                    c[r][0] = __ldg(static_cast<const T *>(csr.dinv) + g0[r]);
+                                    dg[r] = tile.diag(tb, (int)(g0[r] - u * usw));
+                                } else {
+                                    c[r][0] = __ldg(static_cast<const T *>(csr.dinv) + g0[r]);
+                                    dg[r] = coef_cast<T>(__ldg(static_cast<const CT *>(csr.diag) + g0[r]));
+                                }
                             }
                         } else if constexpr (op_is_jacobi(OP)) {
                             // K1 with M = diag(A): z^(l)_{i+1} is built from M^{-1} A z^(l)_i
@@ -1903,7 +1935,7 @@ __device__ void plcg_body(const SolveArgs<T> &a, Smem<T> &s, Grp &grp)
                             const T di = c[r][0];
                             if (stg) {
                                 T zc;
-                                nb[r][0] = tile.template row<T>(tb, (int)(g0[r] - u * usw), &zc);
+                                nb[r][0] = tile.template row<T>(tb, (int)(g0[r] - u * usw), bw, &zc);
                                 c[r][0] = zc;
                             } else {
                                 op_parts<T, CT, VEC, OP>(st, csr, Ld1<T>{C.zl_cur}, g0[r], c[r], nb[r]);
@@ -1997,7 +2029,7 @@ __device__ void plcg_body(const SolveArgs<T> &a, Smem<T> &s, Grp &grp)
                             if (!S || steady_dot_src<L>(q) != 0) dac[q].flush();   // dots in use
                         since_flush = 0;
                     }
-                    tb = (tb + 1) % kV27Buf;
+                    tb = (tb + 1) % Tile::NB;
                 }
             };
             if (steady) sweep(std::true_type{});
@@ -2093,13 +2125,14 @@ __device__ void cg_body(const SolveArgs<T> &a, Smem<T> &s, Grp &grp)
     // FP64 FMA at every stencil point or matrix entry (one pass more, 7 of 18
     // FP64 instructions per row fewer on the 7-point stencil)
     constexpr bool kSepP = kTileCG || (sizeof(T) == 8 && std::is_same<Grp, GridGroup<T>>::value && RPT == 1);
-    Var27Tile<T, 0> tile(plcg_dsm);
+    using Tile = Var27Tile<T, 0, kV27StageBwdCg>;
+    Tile tile(plcg_dsm);
     if constexpr (kSepP) {
         pr[0] = pr[1] = a.zring;   // p updated in place
         if constexpr (kF32) xi = a.zring + 2 * a.vstride;
     }
     if constexpr (kTileCG) {
-        tile.init(a.st);
+        tile.init(a.st, static_cast<const T *>(csr.val), csr.stride);
         __syncthreads();
         // zero the halo before ring vector 0 and the span after every ring
         // vector: the tiles' z copies reach into them (the grid barrier after
@@ -2257,30 +2290,37 @@ __device__ void cg_body(const SolveArgs<T> &a, Smem<T> &s, Grp &grp)
                 };
                 // p was written by generic stores before the barrier above; one
                 // proxy fence per issuing thread orders them before the copies
-                if (tid < Var27Tile<T, 0>::kSlots) fence_proxy_async_all();
+                if (tid < Tile::kSlots) fence_proxy_async_all();
                 if ((uint32_t)grp.unit0() < (uint32_t)nunits)
-                    for (int bb = 0; bb < kV27Buf - 1; ++bb)
+                    for (int bb = 0; bb < Tile::NB - 1; ++bb)
                         tile_issue(bb, (uint32_t)grp.unit0() + (uint32_t)bb * (uint32_t)grp.ustep());
                 for (uint32_t u = (uint32_t)grp.unit0(); u < (uint32_t)nunits; u += (uint32_t)grp.ustep()) {
                     const bool stg = (stg_q >> tb) & 1u;
-                    tile_issue((tb + kV27Buf - 1) % kV27Buf, u + (uint32_t)(kV27Buf - 1) * (uint32_t)grp.ustep());
-                    if (stg) tile.wait(tb, a.poll_limit, &a.out->abort);
+                    tile_issue((tb + Tile::NB - 1) % Tile::NB, u + (uint32_t)(Tile::NB - 1) * (uint32_t)grp.ustep());
                     const uint32_t g = u * usw + (uint32_t)tid;
+                    T bw[13];
+                    if (stg && g < nn) tile.backward(g, bw);
+                    if (stg) tile.wait(tb, a.poll_limit, &a.out->abort);
                     if (g < nn) {
                         T c[VEC], w[VEC];
+                        T mi = T(1);   // Jacobi: 1 / a_gg
                         if (stg) {
                             T zc;
-                            w[0] = tile.template row<T>(tb, tid, &zc);
+                            w[0] = tile.template row<T>(tb, tid, bw, &zc);
                             c[0] = zc;
+                            // the correctly rounded reciprocal of the diagonal
+                            // slot: the stored inverse diagonal's value
+                            if constexpr (op_is_jacobi(OP)) mi = __frcp_rn(tile.diag(tb, tid));
                         } else {
                             op_parts<T, CT, VEC, OP>(st, csr, Ld1<T>{pn}, g, c, w);
+                            if constexpr (op_is_jacobi(OP)) mi = __ldg(static_cast<const T *>(csr.dinv) + g);
                         }
                         d1.add(c, w);
-                        if constexpr (op_is_jacobi(OP)) w[0] *= __ldg(static_cast<const T *>(csr.dinv) + g);   // q = M^{-1} A p
+                        if constexpr (op_is_jacobi(OP)) w[0] *= mi;   // q = M^{-1} A p
                         vst<T, VEC>(q + g, w);
                     }
                     if (++since_flush == kFlushUnits) { d1.flush(); since_flush = 0; }
-                    tb = (tb + 1) % kV27Buf;
+                    tb = (tb + 1) % Tile::NB;
                 }
             } else {
                 for (uint32_t u = (uint32_t)grp.unit0(); u < (uint32_t)nunits_s; u += (uint32_t)grp.ustep()) {
@@ -2425,8 +2465,7 @@ finish:
 // two otherwise; the 27-point tiles' buffers (about 47 KB each) leave room
 // for one CTA per SM with four of them (two with two).
 template <typename T, int L, int OP>
-constexpr int kPlcgMinBlocks = (sizeof(T) == 4 && op_is_var27(OP)) ? (kV27Buf > 2 ? 1 : 2)
-                             : (sizeof(T) == 4 && L <= 2) ? 3 : 2;
+constexpr int kPlcgMinBlocks = (sizeof(T) == 4 && op_is_var27(OP)) ? 2 : (sizeof(T) == 4 && L <= 2) ? 3 : 2;
 
 // CT: the stored type of the matrix values (T, or float under FP64 vectors:
 // the FP32-matrix path).

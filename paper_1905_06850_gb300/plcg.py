@@ -101,6 +101,8 @@ SIGNATURES = {
     "plcg_debug_set_poll_limit": (None, [C.c_uint64]),
     "plcg_debug_force_barrier_timeout": (None, [C.c_int]),
     "plcg_debug_last_launch": (None, [C.POINTER(plcg_launch_info)]),
+    "plcg_debug_server_admission": (C.c_int, [C.c_int, _VP, _VP, _VP, C.c_uint64, C.c_double, C.c_int,
+                                              C.c_int, _VP]),
     "plcg_measure_fp64_fma_rate": (C.c_int, [C.POINTER(C.c_double)]),
 }
 
@@ -149,6 +151,19 @@ def last_launch() -> dict:
     info = plcg_launch_info()
     load().plcg_debug_last_launch(C.byref(info))
     return {name: getattr(info, name) for name, _ in info._fields_}
+
+
+def server_admission(bytes_, share, waited_s, mem_free, sm_used, num_sms, free_slots):
+    """plcg_debug_server_admission: the indices the server's admission pass
+    would start, in order, for a queue described by the three lists."""
+    n = len(bytes_)
+    b = (C.c_uint64 * max(n, 1))(*bytes_)
+    sh = (C.c_double * max(n, 1))(*share)
+    w = (C.c_double * max(n, 1))(*waited_s)
+    out = (C.c_int * max(n, 1))()
+    k = load().plcg_debug_server_admission(n, b, sh, w, int(mem_free), float(sm_used), int(num_sms),
+                                           int(free_slots), out)
+    return list(out[:k])
 
 
 class PlcgError(RuntimeError):
