@@ -264,9 +264,10 @@ typedef struct plcg_server plcg_server;
  * Each admitted request runs as its own persistent launch (Algorithm 1 or
  * CG, as in plcg_solve) on its own stream, so requests of different sizes
  * overlap on the device and new requests start while others are running.
- * A request's
- * grid size depends only on the request, so its result is bit-identical
- * whether it runs alone or in a mix.  Errors: PLCG_ERR_INVALID, PLCG_ERR_CUDA. */
+ * A request's grid size depends only on the request (at most half of the
+ * GPU's resident thread blocks), so its result is bit-identical whether it
+ * runs alone or in a mix.
+ * Errors: PLCG_ERR_INVALID, PLCG_ERR_CUDA. */
 plcg_status plcg_server_create(size_t mem_budget_bytes, int max_inflight, plcg_server **out);
 
 /* Queue a solve of A x = b (device pointers, 16-byte aligned, kept alive by

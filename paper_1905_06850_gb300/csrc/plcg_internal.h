@@ -129,25 +129,32 @@ struct SolveArgs {
 // Structured 27-point tiles: per sweep unit, shared-memory slots of
 // kV27Slot elements -- the diagonal and 13 forward coefficient segments, with
 // SB (staged backward) the 13 backward segments (forward array k at rows
-// g - d_k), and the 9 line segments of z around the unit -- and, for l <= 3,
-// v27_vec_slots(l, jacobi) slots of the vector operands the steady-state
-// p(l)-CG sweep streams (z^(l)_{i-1}, the l current and l previous z^(k), p,
-// the iterate and, with Jacobi, 1/a_gg; a_gg is the diagonal slot).  Without SB the backward coefficients come through L2
-// (another unit's forward copies bring them there shortly before or after)
-// and the smaller tiles leave room for a third buffer.  v27_bufs(SB)
-// buffers, each with its mbarrier: the unit being computed and the next
-// ones in flight.  The dynamic shared memory starts with the mbarriers, then
-// (without SB) the 13 base pointers of the backward loads, then the buffers.
+// g - d_k), and nine slots' room for z around the unit (the 9 line segments,
+// or 3 plane segments) -- and, for l <= 3, v27_vec_slots(l, jacobi) slots of
+// the vector operands the steady-state p(l)-CG sweep streams (z^(l)_{i-1},
+// the l current and l previous z^(k), p, the iterate and, with Jacobi,
+// 1/a_gg; a_gg is the diagonal slot).  Without SB the backward coefficients
+// come through L2 (another unit's forward copies bring them there shortly
+// before or after) and the smaller tiles leave room for a third buffer.
+// v27_bufs(SB) buffers, each with its mbarrier: the unit being computed and
+// the next ones in flight.  The dynamic shared memory starts with the
+// mbarriers, then (without SB) the 13 base pointers of the backward loads,
+// then the buffers.
 constexpr int kV27Slot = 256 + 16;
 PLCG_HD constexpr int v27_bufs(bool sb) { return sb ? 2 : 3; }
 PLCG_HD constexpr int v27_op_slots(bool sb) { return 14 + (sb ? 13 : 0) + 9; }
 PLCG_HD constexpr unsigned v27_hdr(bool sb) { return 16u * ((unsigned)(v27_bufs(sb) + 1) / 2u) + (sb ? 0u : 112u); }
 // the choice per kernel family (measured on GB300, 128^3 heterogeneous
-// operator): the p(l)-CG sweep, whose vector slots make its tiles large,
-// keeps two buffers of fully staged tiles; classic CG's SpMV-only tiles take
-// the third buffer
+// operator, Jacobi): fully staged tiles in two buffers for both, p(l)-CG
+// (p(1) 13.0 vs 13.6 ms through L2 with three buffers; p(3)'s three buffers
+// do not fit two CTAs per SM) and classic CG (19.4 vs 20.6 ms)
 constexpr bool kV27StageBwdPlcg = true;
-constexpr bool kV27StageBwdCg = false;
+constexpr bool kV27StageBwdCg = true;
+// z staged by plane (three copies per unit) where a plane's three lines fit,
+// else by line (nine); measured: p(l)-CG 128^3 Jacobi p(1) 13.07 -> 12.55 ms
+// by plane, classic CG's SpMV 19.43 (by line) vs 21.56 ms (by plane)
+constexpr bool kV27MergeZPlcg = true;
+constexpr bool kV27MergeZCg = false;
 
 // The 13 forward offsets (dz, dy, dx) of the structured 27-point operator,
 // lexicographic (the order of its coefficient arrays 1..13).

@@ -504,10 +504,12 @@ __device__ __forceinline__ V csr_row_staged(const CsrDesc &A, const int32_t *sco
 // backward loads -- then NB buffers of kSlots slots of kV27Slot elements):
 // slots 0..13 the diagonal and forward coefficients of the unit's rows; with
 // SB slots 14..26 the backward coefficients (forward array k at rows g - d_k,
-// by symmetry); then the nine line segments of z around the unit ((dz, dy)
-// in {-1,0,1}^2, x - 1 .. x + 1); then the unit's rows of NV vector operands
-// (the steady-state sweep's; other sweeps load those from global memory).
-// One bulk copy per slot, each rounded out to 16 bytes; the rounding puts
+// by symmetry); then nine slots' room for z around the unit: its nine line
+// segments ((dz, dy) in {-1,0,1}^2, x - 1 .. x + 1), or its three plane
+// segments (each the lines dy = -1..1 of plane dz with their x halo); then
+// the unit's rows of NV vector operands (the steady-state sweep's; other
+// sweeps load those from global memory).  One bulk copy per slot (a plane
+// segment fills three), each rounded out to 16 bytes; the rounding puts
 // element g of a backward or z slot at a shift that is fixed for the whole
 // solve (the arrays and ring vectors start on 256-byte boundaries and units
 // on multiples of 4 rows), so the shifts are computed once; forward and
@@ -530,6 +532,13 @@ struct Var27Tile {
     T *slot0;
     uint32_t parity = 0;          // bit b: the phase buffer b waits for next
     uint32_t shb = 0, shz = 0;    // 2-bit shifts of the backward and z slots
+    // z staging: the nine line segments in slots of their own, or (zm, when
+    // a plane's three lines with their x halo fit three slots: nx <= 275)
+    // one copy per plane dz holding the lines dy = -1, 0, 1 nx apart, so a
+    // unit takes 3 z copies instead of 9; ys = the distance between the
+    // line segments of one plane in the tile
+    bool zm = false;
+    int ys = kV27Slot;
     __device__ __forceinline__ explicit Var27Tile(unsigned char *dsm)
         : bar(reinterpret_cast<uint64_t *>(dsm)),
           bwd(reinterpret_cast<const T **>(dsm + 16 * ((NB + 1) / 2))),
@@ -537,7 +546,7 @@ struct Var27Tile {
     {
     }
     // Needs a __syncthreads() before the first issue().
-    __device__ __forceinline__ void init(const StencilDesc &st, const T *coef, int64_t cstride)
+    __device__ __forceinline__ void init(const StencilDesc &st, const T *coef, int64_t cstride, bool merge_z)
     {
         const int64_t nx = st.nx, nxy = (int64_t)st.nx * st.ny;
         if (threadIdx.x == 0)
@@ -550,11 +559,27 @@ struct Var27Tile {
             const int off = v27_dz(k) * (int)nxy + v27_dy(k) * (int)nx + v27_dx(k);
             shb |= (uint32_t)(((-off) % A + A) % A) << (2 * k);
         }
+        zm = merge_z && 2 * nx + kBlock + 2 * A + 2 <= 3 * kV27Slot;
+        ys = zm ? (int)nx : kV27Slot;
         for (int q = 0; q < 9; ++q) {
-            const int d = (q / 3 - 1) * (int)nxy + (q % 3 - 1) * (int)nx;
-            shz |= (uint32_t)(((d - 1) % A + A) % A) << (2 * q);
+            // the row at the start of the z copy that holds line q, relative to r0
+            const int d = zm ? (q / 3 - 1) * (int)nxy - (int)nx - 1
+                             : (q / 3 - 1) * (int)nxy + (q % 3 - 1) * (int)nx - 1;
+            shz |= (uint32_t)((d % A + A) % A) << (2 * q);
         }
     }
+    // The slot this thread stages when the first nthreads threads (whole
+    // warps) sweep; kSlots or more: none.  The slots are dealt round-robin
+    // over those warps (slot = lane * warps + warp): the bulk copies that one
+    // warp instruction issues for several lanes go out one after another, so
+    // each warp issues only a few of the unit's copies (128^3 Jacobi
+    // p(1)-CG 15.1 -> 13.0 ms against threads 0 .. kSlots-1 owning them).
+    __device__ __forceinline__ static int my_slot(int nthreads)
+    {
+        const int w = (int)(threadIdx.x >> 5), nw = nthreads >> 5;
+        return w < nw ? (int)(threadIdx.x & 31) * nw + w : kSlots;
+    }
+    __device__ __forceinline__ static bool issues(int nthreads) { return my_slot(nthreads) < kSlots; }
     __device__ __forceinline__ int sb(int k) const { return (int)((shb >> (2 * k)) & 3u); }
     __device__ __forceinline__ int sz(int q) const { return (int)((shz >> (2 * q)) & 3u); }
     // Vector slot j of buffer buf (element t = row r0 + t).
@@ -575,14 +600,15 @@ struct Var27Tile {
     }
     // Start staging rows [r0, r1) in buffer buf (`want` false: nothing to
     // stage, the barrier alone; `vecs`: also the vector slots, vsrc(j) giving
-    // vector j).  Threads 0..kV-1 each own one operator slot: they check that
-    // their 16-byte-rounded range stays inside its allocation ([clo, chi) for
+    // vector j).  Each slot has one owner thread among the first `nthreads`
+    // (my_slot): the owners of operator slots check that their
+    // 16-byte-rounded range stays inside its allocation ([clo, chi) for
     // coefficients, [zlo, zhi) for z), the first `nthreads` threads agree on
     // the result with a barrier reduction (which also orders every read of
     // the buffer's previous unit before the new copies: those reads have
     // completed into registers, and the async-proxy writes follow the
-    // barrier), and threads 0..kSlots-1 issue their copies, each arriving on
-    // the buffer's mbarrier (init count kSlots) with its bytes.  Returns false
+    // barrier), and every owner issues its copy, arriving on the buffer's
+    // mbarrier (init count kSlots) with its bytes.  Returns false
     // when the unit is to be read from global memory; otherwise every thread
     // calls wait() before reading the tile.
     template <class VSrc>
@@ -591,8 +617,10 @@ struct Var27Tile {
                                           const T *z, const char *zlo, const char *zhi, uint32_t r0,
                                           uint32_t r1, int nthreads)
     {
-        const int sl = threadIdx.x;
+        const int sl = my_slot(nthreads);
         uintptr_t b0 = 0, b1 = 0;
+        int dst = sl * kV27Slot;   // the copy's place in the buffer (elements)
+        int cap = kV27Slot;        // and its capacity
         int ok = 1;
         if (sl < kV && !want) ok = 0;
         if (sl < kV && want) {
@@ -611,17 +639,25 @@ struct Var27Tile {
                 hi = (int64_t)r1 - off;
             } else {
                 const int q = sl - kZ;
-                const int64_t d = (q / 3 - 1) * nxy + (q % 3 - 1) * nx;
                 base = z;
-                lo = (int64_t)r0 + d - 1;
-                hi = (int64_t)r1 + d + 1;
+                if (zm) {   // planes dz = q - 1 in slots kZ, kZ + 3, kZ + 6; no copy for q >= 3
+                    const int64_t d = (q - 1) * nxy;
+                    lo = q < 3 ? (int64_t)r0 + d - nx - 1 : 0;
+                    hi = q < 3 ? (int64_t)r1 + d + nx + 1 : 0;
+                    dst = kZ * kV27Slot + q * 3 * kV27Slot;
+                    cap = 3 * kV27Slot;
+                } else {
+                    const int64_t d = (q / 3 - 1) * nxy + (q % 3 - 1) * nx;
+                    lo = (int64_t)r0 + d - 1;
+                    hi = (int64_t)r1 + d + 1;
+                }
             }
             if (hi > lo) {
                 const char *mlo = sl < kZ ? clo : zlo, *mhi = sl < kZ ? chi : zhi;
                 b0 = reinterpret_cast<uintptr_t>(base + lo) & ~uintptr_t(15);
                 b1 = (reinterpret_cast<uintptr_t>(base + hi) + 15) & ~uintptr_t(15);
                 ok = b0 >= reinterpret_cast<uintptr_t>(mlo) && b1 <= reinterpret_cast<uintptr_t>(mhi) &&
-                     b1 - b0 <= (uintptr_t)(kV27Slot * sizeof(T));
+                     b1 - b0 <= (uintptr_t)(cap * sizeof(T));
             }
         } else if (NV > 0 && sl >= kV && sl < kSlots && want && vecs) {
             const T *base = vsrc(sl - kV);
@@ -639,8 +675,7 @@ struct Var27Tile {
             const uint32_t bytes = (uint32_t)(b1 - b0);
             mbar_arrive_expect_tx(bar + buf, bytes);
             if (bytes)
-                bulk_copy_g2s(slot0 + buf * kBuf + sl * kV27Slot, reinterpret_cast<const void *>(b0), bytes,
-                              bar + buf);
+                bulk_copy_g2s(slot0 + buf * kBuf + dst, reinterpret_cast<const void *>(b0), bytes, bar + buf);
         }
         return true;
     }
@@ -667,7 +702,7 @@ struct Var27Tile {
         const T *zs = slot + kZ * kV27Slot;
         auto zat = [&](int dz, int dy, int dx) -> V {
             const int q = (dz + 1) * 3 + (dy + 1);
-            return (V)zs[q * kV27Slot + t + 1 + dx + sz(q)];
+            return (V)zs[(dz + 1) * 3 * kV27Slot + (dy + 1) * ys + t + 1 + dx + sz(q)];
         };
         const V c = zat(0, 0, 0);
         *zc = c;
@@ -1586,7 +1621,7 @@ __device__ void plcg_body(const SolveArgs<T> &a, Smem<T> &s, Grp &grp)
     using Tile = Var27Tile<T, kNV, kV27StageBwdPlcg>;
     Tile tile(plcg_dsm);
     if constexpr (kTile) {
-        tile.init(a.st, static_cast<const T *>(a.csr.val), a.csr.stride);
+        tile.init(a.st, static_cast<const T *>(a.csr.val), a.csr.stride, kV27MergeZPlcg);
         __syncthreads();
         // zero the halo before ring vector 0 and the span after every ring
         // vector (rows n .. vstride-1): the tiles' z-line copies reach into
@@ -1828,7 +1863,7 @@ __device__ void plcg_body(const SolveArgs<T> &a, Smem<T> &s, Grp &grp)
                     // the copies read is written during it.  One proxy fence
                     // per issuing thread orders those stores before all of
                     // the sweep's copies.
-                    if (tid < Tile::kSlots) fence_proxy_async_all();
+                    if (Tile::issues(nsw)) fence_proxy_async_all();
                     if ((uint32_t)grp.unit0() < nunits_s)
                         for (int bb = 0; bb < Tile::NB - 1; ++bb)
                             tile_issue(bb, (uint32_t)grp.unit0() + (uint32_t)bb * (uint32_t)grp.ustep());
@@ -2132,7 +2167,7 @@ __device__ void cg_body(const SolveArgs<T> &a, Smem<T> &s, Grp &grp)
         if constexpr (kF32) xi = a.zring + 2 * a.vstride;
     }
     if constexpr (kTileCG) {
-        tile.init(a.st, static_cast<const T *>(csr.val), csr.stride);
+        tile.init(a.st, static_cast<const T *>(csr.val), csr.stride, kV27MergeZCg);
         __syncthreads();
         // zero the halo before ring vector 0 and the span after every ring
         // vector: the tiles' z copies reach into them (the grid barrier after
@@ -2290,7 +2325,7 @@ __device__ void cg_body(const SolveArgs<T> &a, Smem<T> &s, Grp &grp)
                 };
                 // p was written by generic stores before the barrier above; one
                 // proxy fence per issuing thread orders them before the copies
-                if (tid < Tile::kSlots) fence_proxy_async_all();
+                if (Tile::issues(kBlock)) fence_proxy_async_all();
                 if ((uint32_t)grp.unit0() < (uint32_t)nunits)
                     for (int bb = 0; bb < Tile::NB - 1; ++bb)
                         tile_issue(bb, (uint32_t)grp.unit0() + (uint32_t)bb * (uint32_t)grp.ustep());

@@ -155,10 +155,12 @@ def test_var27_ragged_grids(P, dims):
         assert rel(x, xs) <= 1e-9, (dims, kw)
 
 
-@pytest.mark.parametrize("dims", [(1, 1, 1), (3, 1, 4), (33, 3, 2), (5, 2, 3), (17, 9, 13), (40, 30, 20)])
+@pytest.mark.parametrize("dims", [(1, 1, 1), (3, 1, 4), (33, 3, 2), (5, 2, 3), (17, 9, 13), (40, 30, 20),
+                                  (275, 2, 3), (300, 3, 2)])
 def test_var27_fp32_tiles_ragged_grids(P, dims):
     """The FP32 p(l)-CG sweep (and classic CG's SpMV) stages shared-memory
-    tiles (coefficients, z lines and, in the p(l)-CG steady state, the vector
+    tiles (coefficients, z by plane -- or by line when a plane's three lines
+    do not fit, nx > 275 -- and, in the p(l)-CG steady state, the vector
     operands) and applies rows
     without boundary tests (out-of-grid entries stored as zero, zero halos
     around the arrays): ragged and degenerate grids, units that straddle the
