@@ -2592,6 +2592,10 @@ __global__ void __launch_bounds__(kBlock, MINB) batched_kernel(BatchArgs<T> ba)
 {
     __shared__ Smem<T> s;
     __shared__ int s_next;
+    // the current system's arguments, in shared memory: every thread reads
+    // the same fields, and a per-thread copy (~600 bytes) in local memory
+    // would not stay in L1 with 1024 threads per SM
+    __shared__ SolveArgs<T> sa;
     const int b = blockIdx.x;
     if (b == 0 && threadIdx.x == 0) *ba.t0 = global_timer_ns();
     if (b < ba.ngangs * ba.G) {
@@ -2606,20 +2610,20 @@ __global__ void __launch_bounds__(kBlock, MINB) batched_kernel(BatchArgs<T> ba)
         grp.abort_flag = ba.gabort + gang;
         grp.limit = ba.proto.poll_limit;
         T *ws = reinterpret_cast<T *>(ba.gws + (size_t)gang * ba.gws_stride);
-        SolveArgs<T> a;
         for (;;) {
             if (grp.rank == 0 && threadIdx.x == 0) {
                 const int k = atomicAdd(ba.ctr_large, 1);
                 ba.gslot[gang] = (k < ba.nlarge) ? ba.order_large[k] : -1;
             }
-            if (!grp.sync(a, s)) return;   // a broken gang barrier ends this gang
+            if (!grp.sync(ba.proto, s)) return;   // a broken gang barrier ends this gang
             if (threadIdx.x == 0) s_next = ld_volatile(ba.gslot + gang);
             __syncthreads();
             const int sysi = s_next;
             if (sysi < 0) break;
-            batch_args(ba, ba.sys[sysi], ws, a);
-            if constexpr (CG) cg_body<T, 1, kOpStencil>(a, s, grp);
-            else plcg_body<T, L, 1, kOpStencil>(a, s, grp);
+            if (threadIdx.x == 0) batch_args(ba, ba.sys[sysi], ws, sa);
+            __syncthreads();
+            if constexpr (CG) cg_body<T, 1, kOpStencil>(sa, s, grp);
+            else plcg_body<T, L, 1, kOpStencil>(sa, s, grp);
             if (ld_volatile(grp.abort_flag)) return;
             // every member has read gslot before the leader overwrites it: they
             // all passed the solve's own barriers since reading it
@@ -2632,11 +2636,11 @@ __global__ void __launch_bounds__(kBlock, MINB) batched_kernel(BatchArgs<T> ba)
         const int k = s_next;
         __syncthreads();
         if (k >= ba.nsmall) return;
-        SolveArgs<T> a;
-        batch_args(ba, ba.sys[ba.order_small[k]], ws, a);
+        if (threadIdx.x == 0) batch_args(ba, ba.sys[ba.order_small[k]], ws, sa);
+        __syncthreads();
         BlockGroup<T> grp;
-        if constexpr (CG) cg_body<T, 1, kOpStencil, BlockGroup<T>, RPT>(a, s, grp);
-        else plcg_body<T, L, 1, kOpStencil, BlockGroup<T>, RPT>(a, s, grp);
+        if constexpr (CG) cg_body<T, 1, kOpStencil, BlockGroup<T>, RPT>(sa, s, grp);
+        else plcg_body<T, L, 1, kOpStencil, BlockGroup<T>, RPT>(sa, s, grp);
     }
 }
 
