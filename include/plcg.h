@@ -215,8 +215,10 @@ plcg_status plcg_solve_host(plcg_matrix *A, const double *b, double *x,
  * system's own [lmin_i, lmax_i] given in lmin[], lmax[] (may be NULL: then
  * prm->lmin/lmax for all).  Systems of large estimated work are solved by
  * gangs of thread blocks (see plcg_set_batched_schedule), the rest by one
- * thread block each; each results[i].seconds is the whole batch's time.  results[count] may be NULL.  Only stencil
- * matrices are supported (PLCG_ERR_UNIMPL otherwise).
+ * thread block each; each results[i].seconds is the whole batch's time.
+ * results[count] may be NULL.  Only stencil matrices, l <= 4 and the l + 1
+ * dot products (prm->dots_2l1 = 0) are supported (PLCG_ERR_UNIMPL
+ * otherwise).
  * Returns PLCG_OK when every system returned PLCG_OK, else the first
  * non-OK status in index order. */
 plcg_status plcg_solve_batched(int count, plcg_matrix *const *A,

@@ -1249,6 +1249,8 @@ extern "C" plcg_status plcg_solve_batched(int count, plcg_matrix *const *A, cons
     if (st != PLCG_OK) return st;
     if (prm->method == PLCG_METHOD_PLCG && prm->l > 4)
         return fail(PLCG_ERR_UNIMPL, "plcg_solve_batched: l must be 1..4");
+    if (prm->method == PLCG_METHOD_PLCG && prm->dots_2l1)
+        return fail(PLCG_ERR_UNIMPL, "plcg_solve_batched computes the l+1 dot products only (dots_2l1 = 0)");
     CUDA_TRY(cudaSetDevice(A[0]->device));
     if (prm->prec == PLCG_FP64) return run_batched<double>(count, A, b, x, lmin, lmax, prm, results);
     return run_batched<float>(count, A, b, x, lmin, lmax, prm, results);

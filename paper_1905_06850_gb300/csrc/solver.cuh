@@ -1594,9 +1594,13 @@ __device__ __forceinline__ constexpr int steady_dot_src(int q)
 // ------------------------------------------------------------------------
 // p(l)-CG: a whole solve on one group (grid or CTA).
 // ------------------------------------------------------------------------
-template <typename T, int L, int VEC, int OP, class Grp, int RPT = 1, bool SC = false, typename CT = T>
+// D1: the l + 1 dots of Sec. 2.2 only (the 2l + 1 option compiled out: the
+// sweep then carries no accumulators for positions 0 .. l-1).
+template <typename T, int L, int VEC, int OP, class Grp, int RPT = 1, bool SC = false, typename CT = T,
+          bool D1 = false>
 __device__ void plcg_body(const SolveArgs<T> &a, Smem<T> &s, Grp &grp)
 {
+    const bool d2 = !D1 && a.dots_2l1;   // the 2l + 1 dots
     constexpr int UNIT = kBlock * VEC;
     constexpr bool kF32 = (sizeof(T) == 4);
     constexpr bool kOolScalar = kF32 && std::is_same<Grp, GridGroup<T>>::value;
@@ -1827,7 +1831,7 @@ __device__ void plcg_body(const SolveArgs<T> &a, Smem<T> &s, Grp &grp)
             // the recurrences run, K6 updates p and x, z^(0)_{m-1} exists and the
             // K5 operands follow a fixed pattern.  That case gets its own loop
             // with those tests and the operand selection resolved at compile time.
-            const bool steady = C.mode == 1 && C.k6 == 2 && C.prev0 && !a.dots_2l1;
+            const bool steady = C.mode == 1 && C.k6 == 2 && C.prev0 && !d2;
             auto sweep = [&](auto steady_tag) {
                 constexpr bool S = decltype(steady_tag)::value;
                 const bool rec = S || C.mode == 1;
@@ -2044,6 +2048,7 @@ __device__ void plcg_body(const SolveArgs<T> &a, Smem<T> &s, Grp &grp)
                         for (int v = 0; v < VEC; ++v) uM[v] = op_is_jacobi(OP) ? un[v] * dg[r] : un[v];
 #pragma unroll
                         for (int q = 0; q <= 2 * L; ++q) {
+                            if (D1 && q < L) continue;
                             const int src = S ? steady_dot_src<L>(q) : C.dsrc[q];
                             if (src == 0) continue;
                             T o[VEC];
@@ -2061,7 +2066,7 @@ __device__ void plcg_body(const SolveArgs<T> &a, Smem<T> &s, Grp &grp)
                     if (++since_flush == kFlushUnits) {
 #pragma unroll
                         for (int q = 0; q <= 2 * L; ++q)
-                            if (!S || steady_dot_src<L>(q) != 0) dac[q].flush();   // dots in use
+                            if ((!D1 || q >= L) && (!S || steady_dot_src<L>(q) != 0)) dac[q].flush();   // dots in use
                         since_flush = 0;
                     }
                     tb = (tb + 1) % Tile::NB;
@@ -2072,12 +2077,12 @@ __device__ void plcg_body(const SolveArgs<T> &a, Smem<T> &s, Grp &grp)
             double acc[2 * L + 1];
 #pragma unroll
             for (int q = 0; q <= 2 * L; ++q) {
-                if (q >= L || a.dots_2l1) dac[q].flush();   // positions < l: only with 2l+1 dots
+                if (q >= L || d2) dac[q].flush();   // positions < l: only with 2l+1 dots
                 acc[q] = dac[q].acc;
             }
             spmvs++;
             // MPI_Iallreduce(..., req(i)): publish this CTA's partials in slot i mod (l+1)
-            if (a.dots_2l1) {
+            if (d2) {
                 block_sum<2 * L + 1>(acc, s.red, s.out);
             } else {
                 // the l+1 dots of Sec. 2.2 (positions l .. 2l); the others are
@@ -2623,7 +2628,7 @@ __global__ void __launch_bounds__(kBlock, MINB) batched_kernel(BatchArgs<T> ba)
             if (threadIdx.x == 0) batch_args(ba, ba.sys[sysi], ws, sa);
             __syncthreads();
             if constexpr (CG) cg_body<T, 1, kOpStencil>(sa, s, grp);
-            else plcg_body<T, L, 1, kOpStencil>(sa, s, grp);
+            else plcg_body<T, L, 1, kOpStencil, GangGroup<T>, 1, false, T, true>(sa, s, grp);
             if (ld_volatile(grp.abort_flag)) return;
             // every member has read gslot before the leader overwrites it: they
             // all passed the solve's own barriers since reading it
@@ -2640,7 +2645,7 @@ __global__ void __launch_bounds__(kBlock, MINB) batched_kernel(BatchArgs<T> ba)
         __syncthreads();
         BlockGroup<T> grp;
         if constexpr (CG) cg_body<T, 1, kOpStencil, BlockGroup<T>, RPT>(sa, s, grp);
-        else plcg_body<T, L, 1, kOpStencil, BlockGroup<T>, RPT>(sa, s, grp);
+        else plcg_body<T, L, 1, kOpStencil, BlockGroup<T>, RPT, false, T, true>(sa, s, grp);
     }
 }
 

@@ -116,6 +116,9 @@ def test_batched_edge_cases(P):
     assert st == P.PLCG_OK and res[2].iters == 0 and not xs[2].any()
     st, res, xs = run(P, systems, "fp64", l=5, rtol=1e-8)
     assert st == P.PLCG_ERR_UNIMPL
+    # the batched kernel computes the l + 1 dot products only
+    st, res, xs = run(P, systems, "fp32", l=2, rtol=1e-8, dots_2l1=True)
+    assert st == P.PLCG_ERR_UNIMPL and "dots_2l1" in P.last_error()
     # a CSR matrix in the batch is rejected
     csr = P.Matrix(W.random_spd_csr(100, seed=1))
     b = torch.ones(100, dtype=torch.float64, device="cuda")
