@@ -734,7 +734,8 @@ def cpu_baseline_configs():
     bounded sample: the whole 2D 100^2 solve (p(1)-CG and CG, rtol 1e-6), 10
     iterations of p(2)-CG on the 27-point heterogeneous CSR 128^3, and 16
     systems of the 4096-system batch (p(1)-CG, rtol 1e-8) scaled to solves/s
-    of the batch's size mix."""
+    of the batch's size mix; then the same oracle on all host cores at once
+    (cpu_all_cores)."""
     from oracle import oracle as O
     from paper_1905_06850_gb300 import workloads as W
     out = {"host_cores": os.cpu_count(), "cores_used": 1, "kind": "oracle"}
@@ -772,6 +773,45 @@ def cpu_baseline_configs():
     out["batched_4096_2d"] = {"sample": f"{len(pick)} systems (every 256th), p(1)-CG, rtol 1e-8",
                               "seconds": round(dt, 2),
                               "solves_per_s_scaled": round(len(systems) / (dt * total / unknowns), 2)}
+    out["all_cores"] = cpu_all_cores(systems)
+    return out
+
+
+def cpu_all_cores(systems):
+    """The same serial oracle on every host core at once: one spawn worker
+    process per core (started and loaded before the clock starts), each
+    solving whole systems -- 256 systems of the batch (every 16th, p(1)-CG,
+    rtol 1e-8, scaled to solves/s of the batch's size mix) and 2D 100^2
+    p(1)-CG solves (rtol 1e-6, eight per core).  A throughput figure for
+    independent solves, not a faster single solve."""
+    from oracle import jobs
+    from paper_1905_06850_gb300 import workloads as W
+    cores = os.cpu_count() or 1
+    out = {"cores": cores, "kind": "oracle, one process per core"}
+    with jobs.pool(max_workers=cores) as ex:
+        list(ex.map(jobs.warm, range(cores)))
+        pick = list(range(0, len(systems), 16))
+        t0 = time.perf_counter()
+        futs = [ex.submit(jobs.run, {"key": i, "workload": {"kind": "batched", "index": i, "count": len(systems)},
+                                     "method": "plcg", "l": 1, "interval": systems[i]["interval"], "rtol": 1e-8})
+                for i in pick]
+        for f in futs:
+            f.result()
+        dt = time.perf_counter() - t0
+        unknowns = sum(W.op_size(systems[i]["op"]) for i in pick)
+        total = sum(W.op_size(s_["op"]) for s_ in systems)
+        out["batched_4096_2d"] = {"sample": f"{len(pick)} systems (every 16th), p(1)-CG, rtol 1e-8",
+                                  "seconds": round(dt, 2),
+                                  "solves_per_s_scaled": round(len(systems) / (dt * total / unknowns), 2)}
+        c = W.config_2d()
+        t0 = time.perf_counter()
+        futs = [ex.submit(jobs.run, {"key": k, "workload": {"kind": "2d", "nx": 100}, "method": "plcg", "l": 1,
+                                     "interval": c["interval"], "rtol": c["rtol"]}) for k in range(8 * cores)]
+        for f in futs:
+            f.result()
+        dt = time.perf_counter() - t0
+        out["2d_100_fp64_rtol1e-6"] = {"solves": 8 * cores, "seconds": round(dt, 3),
+                                       "solves_per_s": round(8 * cores / dt, 1)}
     return out
 
 

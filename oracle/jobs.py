@@ -19,7 +19,8 @@ import time
 def workload(w: dict):
     """(operator, b) of a workload description: "3d" (7-point Laplacian, nx),
     "h27" (the FP32-rounded 27-point heterogeneous CSR, nx), "batched" (one
-    system of the shifted 2D batch: index, count)."""
+    system of the shifted 2D batch: index, count), "2d" (5-point Laplacian,
+    nx)."""
     from paper_1905_06850_gb300 import workloads as W
     if w["kind"] == "3d":
         c = W.config_3d(nx=w["nx"], seed=2)
@@ -30,7 +31,18 @@ def workload(w: dict):
     if w["kind"] == "batched":
         s = W.batched_system(w["index"], count=w["count"])
         return s["op"], s["b"]   # FP32-rounded coefficients
+    if w["kind"] == "2d":
+        c = W.config_2d(nx=w["nx"])
+        return c["op"], c["b"]
     raise ValueError(f"unknown workload {w['kind']!r}")
+
+
+def warm(_=None):
+    """Loads the oracle in a worker (so that a timed batch of run() calls
+    does not include the workers' start-up); returns the worker's pid."""
+    from oracle import oracle as O   # noqa: F401  (builds nothing: imports and loads the library)
+    from paper_1905_06850_gb300 import workloads as W   # noqa: F401
+    return os.getpid()
 
 
 def run(job: dict):
