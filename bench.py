@@ -816,7 +816,7 @@ def cpu_all_cores(systems):
 
 
 def run_reference(args):
-    """The reference arm: the FP64 CPU oracle on the machine's host cores, same
+    """The reference arm: the FP64 CPU oracle on the host's cores, same
     metric and workload, each step a bounded sample (a few iterations)."""
     rank, world, _ = dist_env()
     if rank != 0:
