@@ -158,9 +158,11 @@ def test_fp32_with_fp64_refinement(P, l, case):
 # FP64 too (Sec. 2.2: the oracle restarts 3-6 times here, 50-100 times at
 # 128^3 for l = 2, 3); with FP32 storage of the bases the breakdowns come
 # about twice as often (a float32 emulation of this very path shows the same:
-# 2-11 restarts here, +15-30% iterations), so the FP32-vector path gets a
-# 50% iteration window on this operator, while the FP32-matrix path (FP64
-# vectors) is held to the FP64 bars below.
+# 2-11 restarts here, +15-30% iterations; measured on GB300: 106/121/114
+# iterations with 4/11/11 restarts against the refined oracle's 92/101/107
+# with 2/3/5 for l = 1/2/3), so the FP32-vector path gets a 30% iteration
+# window on this operator, while the FP32-matrix path (FP64 vectors) is held
+# to the FP64 bars below.
 @pytest.mark.parametrize("l", [1, 2, 3])
 def test_csr_hetero27_fp64(P, l):
     op = W.hetero27_csr(14, 12, 10, seed=3)
@@ -181,7 +183,7 @@ def test_csr_hetero27_fp64(P, l):
 def test_csr_hetero27_fp32(P, l):
     op = W.hetero27_csr(14, 12, 10, seed=3)
     b = W.rhs(op, np.random.default_rng(4).standard_normal(op["n"]))
-    check_plcg(P, op, b, l, 1e-8, W.shift_interval(op), prec="fp32", iter_slack=0.5,
+    check_plcg(P, op, b, l, 1e-8, W.shift_interval(op), prec="fp32", iter_slack=0.3,
                max_restarts=64)
 
 
@@ -196,7 +198,9 @@ def test_csr_random_spd(P, prec):
             check_plcg(P, op, b, l, 1e-8, W.shift_interval(op), tol=max(1e-10, 4 * sens_x),
                        iter_slack=max(0.1, 2 * sens_k))
         else:
-            check_plcg(P, op, b, l, 1e-8, W.shift_interval(op), prec="fp32", iter_slack=0.5,
+            # the FP32 path's iterations within 10% of the refined oracle's
+            # (measured on GB300: 42 vs 42 for l = 1, 45 vs 44 for l = 2)
+            check_plcg(P, op, b, l, 1e-8, W.shift_interval(op), prec="fp32", iter_slack=0.1,
                        max_restarts=64)
     oop = W.fp32_rounded(op) if prec == "fp32" else op
     ref = O.cg(oop, b, rtol=1e-8)
