@@ -174,7 +174,9 @@ constexpr int v27_vec_slots(int l, bool jacobi)
 }
 constexpr unsigned v27_tile_bytes_nv(unsigned value_bytes, int nv, bool sb)
 {
-    return v27_hdr(sb) + (unsigned)v27_bufs(sb) * (unsigned)(v27_op_slots(sb) + nv) * (unsigned)kV27Slot * value_bytes;
+    // header, buffers, then one 40-byte copy plan per slot
+    return v27_hdr(sb) + (unsigned)v27_bufs(sb) * (unsigned)(v27_op_slots(sb) + nv) * (unsigned)kV27Slot * value_bytes +
+           40u * (unsigned)(v27_op_slots(sb) + nv);
 }
 // dynamic shared memory of the p(l)-CG kernels and of classic CG's
 constexpr unsigned v27_tile_bytes(unsigned value_bytes, int l, bool jacobi)

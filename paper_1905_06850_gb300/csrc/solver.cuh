@@ -598,71 +598,90 @@ struct Var27Tile {
             for (int k = 0; k < 13; ++k) bw[k] = __ldg(bwd[k] + g);
         }
     }
-    // Start staging rows [r0, r1) in buffer buf (`want` false: nothing to
-    // stage, the barrier alone; `vecs`: also the vector slots, vsrc(j) giving
-    // vector j).  Each slot has one owner thread among the first `nthreads`
-    // (my_slot): the owners of operator slots check that their
-    // 16-byte-rounded range stays inside its allocation ([clo, chi) for
-    // coefficients, [zlo, zhi) for z), the first `nthreads` threads agree on
-    // the result with a barrier reduction (which also orders every read of
-    // the buffer's previous unit before the new copies: those reads have
-    // completed into registers, and the async-proxy writes follow the
-    // barrier), and every owner issues its copy, arriving on the buffer's
-    // mbarrier (init count kSlots) with its bytes.  Returns false
-    // when the unit is to be read from global memory; otherwise every thread
-    // calls wait() before reading the tile.
+    // The copy plan of one slot for the current sweep: the copy of unit
+    // [r0, r1) reads [base + (r0 + loff) elements, base + (r1 + hoff)
+    // elements), rounded out to 16 bytes, which must lie inside [lo, hi) and
+    // fit cap bytes, into element dst of the buffer; base == null: no copy.
+    // Written by prepare() and read by issue() in the slot's owner thread
+    // only (no barrier between them), kept in shared memory after the
+    // buffers rather than in registers.
+    struct Plan {
+        const char *base, *lo, *hi;
+        int loff, hoff, dst, cap;
+    };
+    __device__ __forceinline__ Plan *plans() const { return reinterpret_cast<Plan *>(slot0 + NB * kBuf); }
+    // The plans of this sweep (every thread calls it; owners write): the
+    // operator slots from coef (allocation [clo, chi)) and z (the ring's
+    // allocation [zlo, zhi)), the vector slots from vsrc(j) when `vecs`.
     template <class VSrc>
-    __device__ __forceinline__ bool issue(int buf, bool want, bool vecs, const VSrc &vsrc, const StencilDesc &st,
-                                          const T *coef, int64_t cstride, const char *clo, const char *chi,
-                                          const T *z, const char *zlo, const char *zhi, uint32_t r0,
-                                          uint32_t r1, int nthreads)
+    __device__ __forceinline__ void prepare(bool vecs, const VSrc &vsrc, const StencilDesc &st, const T *coef,
+                                            int64_t cstride, const char *clo, const char *chi, const T *z,
+                                            const char *zlo, const char *zhi, int nthreads)
+    {
+        const int sl = my_slot(nthreads);
+        if (sl >= kSlots) return;
+        const int nx = st.nx, nxy = st.nx * st.ny;
+        Plan p{nullptr, clo, chi, 0, 0, sl * kV27Slot, kV27Slot * (int)sizeof(T)};
+        if (sl < 14) {
+            p.base = reinterpret_cast<const char *>(coef + sl * cstride);
+        } else if (sl < kZ) {
+            const int k = sl - 14;
+            const int off = v27_dz(k) * nxy + v27_dy(k) * nx + v27_dx(k);
+            p.base = reinterpret_cast<const char *>(coef + (1 + k) * cstride);
+            p.loff = p.hoff = -off;   // may start in the zero halo before the arrays
+        } else if (sl < kV) {
+            const int q = sl - kZ;
+            p.lo = zlo;
+            p.hi = zhi;
+            if (zm) {   // planes dz = q - 1 in slots kZ, kZ + 3, kZ + 6; no copy for q >= 3
+                if (q < 3) {
+                    p.base = reinterpret_cast<const char *>(z);
+                    p.loff = (q - 1) * nxy - nx - 1;
+                    p.hoff = (q - 1) * nxy + nx + 1;
+                    p.dst = kZ * kV27Slot + q * 3 * kV27Slot;
+                    p.cap = 3 * kV27Slot * (int)sizeof(T);
+                }
+            } else {
+                const int d = (q / 3 - 1) * nxy + (q % 3 - 1) * nx;
+                p.base = reinterpret_cast<const char *>(z);
+                p.loff = d - 1;
+                p.hoff = d + 1;
+            }
+        } else if (vecs) {   // whole rows from their start; padded to 256 bytes: always inside
+            p.base = reinterpret_cast<const char *>(vsrc(sl - kV));
+            p.lo = nullptr;
+            p.hi = reinterpret_cast<const char *>(~uintptr_t(0));
+        }
+        plans()[sl] = p;
+    }
+    // Start staging rows [r0, r1) in buffer buf by this sweep's plans
+    // (`want` false: nothing to stage, the barrier alone).  Each slot has one
+    // owner thread among the first `nthreads` (my_slot): the owners check
+    // that their 16-byte-rounded ranges stay inside their allocations, the
+    // first `nthreads` threads agree on the result with a barrier reduction
+    // (which also orders every read of the buffer's previous unit before the
+    // new copies: those reads have completed into registers, and the
+    // async-proxy writes follow the barrier), and every owner issues its copy,
+    // arriving on the buffer's mbarrier (init count kSlots) with its bytes.
+    // Returns false when the unit is to be read from global memory;
+    // otherwise every thread calls wait() before reading the tile.
+    __device__ __forceinline__ bool issue(int buf, bool want, uint32_t r0, uint32_t r1, int nthreads)
     {
         const int sl = my_slot(nthreads);
         uintptr_t b0 = 0, b1 = 0;
-        int dst = sl * kV27Slot;   // the copy's place in the buffer (elements)
-        int cap = kV27Slot;        // and its capacity
+        int dst = 0;
         int ok = 1;
         if (sl < kV && !want) ok = 0;
-        if (sl < kV && want) {
-            const int64_t nx = st.nx, nxy = (int64_t)st.nx * st.ny;
-            const T *base;
-            int64_t lo, hi;
-            if (sl < 14) {
-                base = coef + sl * cstride;
-                lo = r0;
-                hi = r1;
-            } else if (sl < kZ) {
-                const int k = sl - 14;
-                const int64_t off = v27_dz(k) * nxy + v27_dy(k) * nx + v27_dx(k);
-                base = coef + (1 + k) * cstride;
-                lo = (int64_t)r0 - off;   // may start in the zero halo before the arrays
-                hi = (int64_t)r1 - off;
-            } else {
-                const int q = sl - kZ;
-                base = z;
-                if (zm) {   // planes dz = q - 1 in slots kZ, kZ + 3, kZ + 6; no copy for q >= 3
-                    const int64_t d = (q - 1) * nxy;
-                    lo = q < 3 ? (int64_t)r0 + d - nx - 1 : 0;
-                    hi = q < 3 ? (int64_t)r1 + d + nx + 1 : 0;
-                    dst = kZ * kV27Slot + q * 3 * kV27Slot;
-                    cap = 3 * kV27Slot;
-                } else {
-                    const int64_t d = (q / 3 - 1) * nxy + (q % 3 - 1) * nx;
-                    lo = (int64_t)r0 + d - 1;
-                    hi = (int64_t)r1 + d + 1;
-                }
+        if (sl < kSlots && want) {
+            const Plan p = plans()[sl];
+            dst = p.dst;
+            const int64_t lo = (int64_t)r0 + p.loff, hi = (int64_t)r1 + p.hoff;
+            if (p.base && hi > lo) {
+                b0 = reinterpret_cast<uintptr_t>(p.base + lo * (int64_t)sizeof(T)) & ~uintptr_t(15);
+                b1 = (reinterpret_cast<uintptr_t>(p.base + hi * (int64_t)sizeof(T)) + 15) & ~uintptr_t(15);
+                ok = b0 >= reinterpret_cast<uintptr_t>(p.lo) && b1 <= reinterpret_cast<uintptr_t>(p.hi) &&
+                     b1 - b0 <= (uintptr_t)p.cap;
             }
-            if (hi > lo) {
-                const char *mlo = sl < kZ ? clo : zlo, *mhi = sl < kZ ? chi : zhi;
-                b0 = reinterpret_cast<uintptr_t>(base + lo) & ~uintptr_t(15);
-                b1 = (reinterpret_cast<uintptr_t>(base + hi) + 15) & ~uintptr_t(15);
-                ok = b0 >= reinterpret_cast<uintptr_t>(mlo) && b1 <= reinterpret_cast<uintptr_t>(mhi) &&
-                     b1 - b0 <= (uintptr_t)(cap * sizeof(T));
-            }
-        } else if (NV > 0 && sl >= kV && sl < kSlots && want && vecs) {
-            const T *base = vsrc(sl - kV);
-            b0 = reinterpret_cast<uintptr_t>(base + r0);
-            b1 = (reinterpret_cast<uintptr_t>(base + r1) + 15) & ~uintptr_t(15);
         }
         int all;
         asm volatile("{\n\t.reg .pred p, q;\n\t"
@@ -1856,9 +1875,8 @@ __device__ void plcg_body(const SolveArgs<T> &a, Smem<T> &s, Grp &grp)
                 // stage unit uu (if it exists) in buffer bb
                 auto tile_issue = [&](int bb, uint32_t uu) {
                     const bool more = uu < nunits_s;
-                    const bool on = tile.issue(bb, more, SV, vsrc, st, static_cast<const T *>(csr.val), csr.stride,
-                                               tclo, tchi, C.zl_cur, a.ws_lo, a.ws_hi, more ? uu * usw : 0u,
-                                               more ? min(uu * usw + usw, nn) : 0u, nsw);
+                    const bool on = tile.issue(bb, more, more ? uu * usw : 0u, more ? min(uu * usw + usw, nn) : 0u,
+                                               nsw);
                     stg_q = (stg_q & ~(1u << bb)) | ((on ? 1u : 0u) << bb);
                 };
                 if constexpr (kTile) {   // the first NB - 1 units
@@ -1868,6 +1886,8 @@ __device__ void plcg_body(const SolveArgs<T> &a, Smem<T> &s, Grp &grp)
                     // per issuing thread orders those stores before all of
                     // the sweep's copies.
                     if (Tile::issues(nsw)) fence_proxy_async_all();
+                    tile.prepare(SV, vsrc, st, static_cast<const T *>(csr.val), csr.stride, tclo, tchi, C.zl_cur,
+                                 a.ws_lo, a.ws_hi, nsw);
                     if ((uint32_t)grp.unit0() < nunits_s)
                         for (int bb = 0; bb < Tile::NB - 1; ++bb)
                             tile_issue(bb, (uint32_t)grp.unit0() + (uint32_t)bb * (uint32_t)grp.ustep());
@@ -2323,14 +2343,15 @@ __device__ void cg_body(const SolveArgs<T> &a, Smem<T> &s, Grp &grp)
                 auto novec = [](int) -> const T * { return nullptr; };
                 auto tile_issue = [&](int bb, uint32_t uu) {
                     const bool more = uu < (uint32_t)nunits;
-                    const bool on = tile.issue(bb, more, false, novec, st, static_cast<const T *>(csr.val),
-                                               csr.stride, a.cf_lo, a.cf_hi, pn, a.ws_lo, a.ws_hi,
-                                               more ? uu * usw : 0u, more ? min(uu * usw + usw, nn) : 0u, kBlock);
+                    const bool on = tile.issue(bb, more, more ? uu * usw : 0u,
+                                               more ? min(uu * usw + usw, nn) : 0u, kBlock);
                     stg_q = (stg_q & ~(1u << bb)) | ((on ? 1u : 0u) << bb);
                 };
                 // p was written by generic stores before the barrier above; one
                 // proxy fence per issuing thread orders them before the copies
                 if (Tile::issues(kBlock)) fence_proxy_async_all();
+                tile.prepare(false, novec, st, static_cast<const T *>(csr.val), csr.stride, a.cf_lo, a.cf_hi, pn,
+                             a.ws_lo, a.ws_hi, kBlock);
                 if ((uint32_t)grp.unit0() < (uint32_t)nunits)
                     for (int bb = 0; bb < Tile::NB - 1; ++bb)
                         tile_issue(bb, (uint32_t)grp.unit0() + (uint32_t)bb * (uint32_t)grp.ustep());

@@ -89,7 +89,7 @@ def test_two_ctas_of_tiles_fit_one_sm(values):
         sb, l, jac, nv, tb = int(r[1]), int(r[2]), int(r[3]), int(r[4]), int(r[5])
         nbuf, ops, hdr = lay[sb]
         assert nv == (2 * l + 3 + jac if 1 <= l <= 3 else 0)
-        assert tb == hdr + nbuf * (ops + nv) * slot * 4
+        assert tb == hdr + nbuf * (ops + nv) * slot * 4 + 40 * (ops + nv)   # + one copy plan per slot
         if sb == (choice[1] if l == 0 else choice[0]):   # the layouts the kernels use
             assert 2 * (tb + STATIC_SMEM_BOUND + SMEM_RESERVED_PER_CTA) <= SMEM_PER_SM, (sb, l, jac, tb)
     used = [int(v) for v in next(r for r in values if r[0] == "used")[1:]]
