@@ -485,14 +485,11 @@ __device__ __forceinline__ V csr_row(const CsrDesc &A, const Ld &ld, uint32_t ro
     return s;
 }
 
-// CSR row whose entries were staged in shared memory: scol / sval hold the
-// entries from global position e0s on.
+// A CSR row whose entries were staged in shared memory (scol / sval), from
+// the row's staged entry range [k0, k1).
 template <typename V, typename C, class Ld>
-__device__ __forceinline__ V csr_row_staged(const CsrDesc &A, const int32_t *scol, const C *sval,
-                                            int64_t e0s, const Ld &ld, uint32_t row)
+__device__ __forceinline__ V csr_row_k(const int32_t *scol, const C *sval, uint32_t k0, uint32_t k1, const Ld &ld)
 {
-    const uint32_t k0 = (uint32_t)(__ldg(A.rowptr + row) - e0s);
-    const uint32_t k1 = (uint32_t)(__ldg(A.rowptr + row + 1) - e0s);
     V s = V(0);
     for (uint32_t k = k0; k < k1; ++k) s = fma(coef_cast<V>(sval[k]), ld.one((uint32_t)scol[k]), s);
     return s;
@@ -762,17 +759,37 @@ struct CsrStage {
     {
         if ((threadIdx.x & 31) == 0) mbar_init(bar, 1);
     }
-    // Stage the entries of rows [r0, r1) (the warp's rows): the range
-    // [rowptr[r0], rowptr[r1]) rounded out to 16 bytes (the arrays carry the
-    // padding), issued by lane 0 once every lane is done with the previous
-    // rows' entries; every lane waits.  Returns false (read global memory)
-    // when the range exceeds the warp's buffer; *e0s is the global position of
-    // the first staged entry.
-    __device__ __forceinline__ bool stage(const CsrDesc &csr, uint32_t r0, uint32_t r1, int64_t *e0s,
-                                          unsigned long long limit, int *abort_flag)
+    // The row pointers of the warp's rows [r0, r1) (r1 - r0 <= 32), loaded
+    // one unit ahead so that their latency overlaps the current unit: one
+    // broadcast load of rowptr[r0] and one coalesced load of this lane's row
+    // end rowptr[min(r0 + lane + 1, r1)].
+    struct Rows {
+        int64_t start, end;
+    };
+    __device__ __forceinline__ static Rows rows_load(const CsrDesc &csr, uint32_t r0, uint32_t r1)
     {
-        if (r0 >= r1) return false;
-        const int64_t e0 = __ldg(csr.rowptr + r0), e1 = __ldg(csr.rowptr + r1);
+        const uint32_t lane = threadIdx.x & 31;
+        return {__ldg(csr.rowptr + r0), __ldg(csr.rowptr + min(r0 + lane + 1, r1))};
+    }
+    // The warp's entry range [e0, e1) and this lane's row [rs, re) from the
+    // loads (every lane of the warp calls it: shuffles).
+    __device__ __forceinline__ static void rows_bounds(const Rows &p, int64_t *e0, int64_t *e1, int64_t *rs,
+                                                       int64_t *re)
+    {
+        const int64_t up = __shfl_up_sync(0xffffffffu, p.end, 1);
+        *e0 = p.start;
+        *e1 = __shfl_sync(0xffffffffu, p.end, 31);
+        *rs = (threadIdx.x & 31) ? up : p.start;
+        *re = p.end;
+    }
+    // Stage the entries [e0, e1) of the warp's rows (rows_bounds), rounded
+    // out to 16 bytes (the arrays carry the padding), issued by lane 0 once
+    // every lane is done with the previous rows' entries; every lane waits.
+    // Returns false (read global memory) when the range exceeds the warp's
+    // buffer; *e0s is the global position of the first staged entry.
+    __device__ __forceinline__ bool stage_range(const CsrDesc &csr, int64_t e0, int64_t e1, int64_t *e0s,
+                                                unsigned long long limit, int *abort_flag)
+    {
         *e0s = e0 & ~int64_t(3);
         const int64_t cnt = ((e1 + 3) & ~int64_t(3)) - *e0s;
         const bool on = cnt > 0 && cnt <= kCsrStageWarpCap;
@@ -1892,6 +1909,11 @@ __device__ void plcg_body(const SolveArgs<T> &a, Smem<T> &s, Grp &grp)
                         for (int bb = 0; bb < Tile::NB - 1; ++bb)
                             tile_issue(bb, (uint32_t)grp.unit0() + (uint32_t)bb * (uint32_t)grp.ustep());
                 }
+                typename CsrStage<CT>::Rows rp_next{0, 0};   // the warp's next unit's row pointers
+                if constexpr (kStage) {
+                    const uint32_t w0 = (uint32_t)grp.unit0() * usw + (uint32_t)(tid & ~31);
+                    if (a.stage && w0 < nn) rp_next = CsrStage<CT>::rows_load(csr, w0, min(w0 + 32u, nn));
+                }
                 for (uint32_t u = (uint32_t)grp.unit0(); u < nunits_s; u += (uint32_t)grp.ustep()) {
                     uint32_t g0[RPT];
                     bool ok[RPT];
@@ -1901,11 +1923,18 @@ __device__ void plcg_body(const SolveArgs<T> &a, Smem<T> &s, Grp &grp)
                         ok[r] = g0[r] < nn;
                     }
                     bool stg = false;
-                    int64_t e0s = 0;
+                    int64_t e0s = 0, rs = 0, re = 0;
                     if constexpr (kStage) {   // this warp's 32 rows of the unit
                         const uint32_t w0 = u * usw + (uint32_t)(tid & ~31);
-                        if (a.stage)
-                            stg = stage.stage(csr, w0, min(w0 + 32u, nn), &e0s, a.poll_limit, &a.out->abort);
+                        if (a.stage && w0 < nn) {
+                            const typename CsrStage<CT>::Rows rp = rp_next;
+                            const uint32_t wn = w0 + (uint32_t)grp.ustep() * usw;
+                            if (u + (uint32_t)grp.ustep() < nunits_s && wn < nn)
+                                rp_next = CsrStage<CT>::rows_load(csr, wn, min(wn + 32u, nn));
+                            int64_t e0, e1;
+                            CsrStage<CT>::rows_bounds(rp, &e0, &e1, &rs, &re);
+                            stg = stage.stage_range(csr, e0, e1, &e0s, a.poll_limit, &a.out->abort);
+                        }
                     }
                     T bw[13];   // the tiled unit's backward coefficients (row g0[0])
                     if constexpr (kTile) {    // the copies NB - 1 units ahead; this unit's tile
@@ -1928,7 +1957,8 @@ __device__ void plcg_body(const SolveArgs<T> &a, Smem<T> &s, Grp &grp)
                         if constexpr (kStage) {   // K1 operands
                             if (stg) {
                                 c[r][0] = C.zl_cur[g0[r]];
-                                nb[r][0] = csr_row_staged<T, CT>(csr, stage.col, stage.val, e0s, Ld1<T>{C.zl_cur}, g0[r]);
+                                nb[r][0] = csr_row_k<T, CT>(stage.col, stage.val, (uint32_t)(rs - e0s),
+                                                            (uint32_t)(re - e0s), Ld1<T>{C.zl_cur});
                             } else {
                                 op_parts<T, CT, VEC, OP>(st, csr, Ld1<T>{C.zl_cur}, g0[r], c[r], nb[r]);
                             }
@@ -2384,29 +2414,42 @@ __device__ void cg_body(const SolveArgs<T> &a, Smem<T> &s, Grp &grp)
                     tb = (tb + 1) % Tile::NB;
                 }
             } else {
+                typename CsrStage<CT>::Rows rp_next{0, 0};   // the warp's next unit's row pointers
+                if constexpr (kStage) {
+                    const uint32_t w0 = (uint32_t)grp.unit0() * USWEEP + (uint32_t)(tid & ~31);
+                    if (a.stage && w0 < nn) rp_next = CsrStage<CT>::rows_load(csr, w0, min(w0 + 32u, nn));
+                }
                 for (uint32_t u = (uint32_t)grp.unit0(); u < (uint32_t)nunits_s; u += (uint32_t)grp.ustep()) {
                     T c[RPT][VEC], w[RPT][VEC], mi[RPT];
                     uint32_t g0[RPT];
                     bool stg = false;
-                    int64_t e0s = 0;
+                    int64_t e0s = 0, rs = 0, re = 0;
                     if constexpr (kStage) {   // this warp's 32 rows of the unit
                         const uint32_t w0 = u * USWEEP + (uint32_t)(tid & ~31);
-                        if (a.stage)
-                            stg = stage.stage(csr, w0, min(w0 + 32u, nn), &e0s, a.poll_limit, &a.out->abort);
+                        if (a.stage && w0 < nn) {
+                            const typename CsrStage<CT>::Rows rp = rp_next;
+                            const uint32_t wn = w0 + (uint32_t)grp.ustep() * USWEEP;
+                            if (u + (uint32_t)grp.ustep() < (uint32_t)nunits_s && wn < nn)
+                                rp_next = CsrStage<CT>::rows_load(csr, wn, min(wn + 32u, nn));
+                            int64_t e0, e1;
+                            CsrStage<CT>::rows_bounds(rp, &e0, &e1, &rs, &re);
+                            stg = stage.stage_range(csr, e0, e1, &e0s, a.poll_limit, &a.out->abort);
+                        }
                     }
 #pragma unroll
                     for (int r = 0; r < RPT; ++r) {
                         g0[r] = u * USWEEP + ((uint32_t)r * kBlock + tid) * VEC;
                         if (g0[r] >= nn) continue;
                         if (stg) {
+                            const uint32_t k0 = (uint32_t)(rs - e0s), k1 = (uint32_t)(re - e0s);
                             if (k == 0) {
                                 const LdFirst<T> ld{rc};
                                 c[r][0] = ld.one(g0[r]);
-                                w[r][0] = csr_row_staged<T, CT>(csr, stage.col, stage.val, e0s, ld, g0[r]);
+                                w[r][0] = csr_row_k<T, CT>(stage.col, stage.val, k0, k1, ld);
                             } else {
                                 const LdAxpy<T> ld{rc, po, (T)beta};
                                 c[r][0] = ld.one(g0[r]);
-                                w[r][0] = csr_row_staged<T, CT>(csr, stage.col, stage.val, e0s, ld, g0[r]);
+                                w[r][0] = csr_row_k<T, CT>(stage.col, stage.val, k0, k1, ld);
                             }
                         } else if (k == 0) {
                             op_apply<T, CT, VEC, OP>(st, csr, cC, cO, LdFirst<T>{rc}, g0[r], c[r], w[r]);
