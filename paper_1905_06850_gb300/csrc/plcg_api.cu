@@ -65,6 +65,7 @@ extern "C" void plcg_debug_force_barrier_timeout(int on) { g_force_timeout = on 
 // not for p(1)-CG (8.0 vs 7.1 us: sixteen SMs of FP64 units against twenty),
 // and above ~2x10^4 rows the grid wins throughout.
 constexpr int64_t kClusterRowsDefault = 12288;
+constexpr int64_t kVec1Rows = 16384;
 static int64_t g_cluster_rows = kClusterRowsDefault;
 
 extern "C" plcg_status plcg_set_cluster_rows(int64_t max_rows)
@@ -483,10 +484,17 @@ static plcg_status build_solve(const plcg_matrix *A, const double *b, double *x,
     const bool c32 = prm->prec == PLCG_FP32_MATRIX;
     if (c32 && f32) return fail(PLCG_ERR_INVALID, "internal: FP32 matrix path with FP32 vectors");
     const unsigned value_bytes = c32 ? 4u : (unsigned)sizeof(T);
+    // Stencil rows per thread: 16 bytes of a vector (rows in one x-line),
+    // except FP64 systems of at most kVec1Rows rows, which take one row per
+    // thread so that their FP64-bound sweep spreads over twice the SMs (or
+    // balances better over one cluster's 16): measured on GB300, 2D 100^2
+    // p(1)-CG 7.11 -> 6.61 us per iteration, p(2) 6.54 -> 6.06, 2D 64^2 p(1)
+    // 5.93 -> 5.16, 3D 20^3 p(1) 7.70 -> 6.78; from ~6*10^4 rows it costs
+    // (3D 40^3 p(1) 8.9 -> 10.4 us), and the FP32 sweeps never gain
     int vec = 1;
     if (op == kOpStencil) {
         const int want = 16 / (int)sizeof(T);
-        vec = (A->st.nx % want == 0) ? want : 1;
+        vec = (A->st.nx % want == 0 && !(sizeof(T) == 8 && n <= kVec1Rows)) ? want : 1;
     }
     // FP64 p(l)-CG on 2^19 rows or more: the scaled-basis kernel (one FP64
     // multiply per recurrence and row fewer; below that the longer scalar step
