@@ -4,9 +4,10 @@ forward offsets with their negatives and the centre cover {-1,0,1}^3 once,
 the zero halo around the coefficient arrays and ring vectors covers the
 largest offset plus a 16-byte-rounded copy, the tile header holds the
 mbarriers (and, where the backward coefficients come through L2, the 13
-backward-load pointers) with the slots 16-byte aligned after it, and two
-CTAs' tile buffers fit one SM's shared memory for every l, for the p(l)-CG
-and the classic CG tiles in the layout each uses."""
+backward-load pointers) with the slots 16-byte aligned after it, the
+buffers are followed by one 40-byte copy plan per slot, and two CTAs' tiles
+fit one SM's shared memory for every l, for the p(l)-CG and the classic CG
+tiles in the layout each uses."""
 import os
 import shutil
 import subprocess
