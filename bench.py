@@ -570,7 +570,8 @@ def other_configs(plcg, W, dev, hbm_peak, orc):
         d[name] = {"status": st, "converged": ok, "batch_time_s": round(best, 5),
                    "schedule": {"gang_size": sched[0], "large_work_factor": sched[1],
                                 "max_gang_fraction": sched[2]},
-                   "launch_shape": {"ctas_per_sm": shape[0], "rows_per_thread": shape[1]},
+                   "launch_shape": {"ctas_per_sm": shape[0], "rows_per_thread": shape[1],
+                                    "vector_width": shape[2]},
                    "system_completion_ms": {"p50": round(float(np.percentile(lat, 50)), 3),
                                             "p99": round(float(np.percentile(lat, 99)), 3),
                                             "max": round(float(lat.max()), 3)},

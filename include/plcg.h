@@ -208,8 +208,8 @@ plcg_status plcg_solve(plcg_matrix *A, const double *b, double *x,
 plcg_status plcg_solve_host(plcg_matrix *A, const double *b, double *x,
                             const plcg_params *prm, plcg_result *res);
 
-/* Solve count independent systems A[i] x[i] = b[i] (device pointers) in one
- * persistent launch; each system gets its own thread block(s), converged
+/* Solve count independent systems A[i] x[i] = b[i] (device pointers,
+ * 16-byte aligned, else PLCG_ERR_INVALID) in one persistent launch; each system gets its own thread block(s), converged
  * systems retire and their blocks take the next system.  prm applies to
  * every system except that shifts == NULL places Chebyshev shifts on each
  * system's own [lmin_i, lmax_i] given in lmin[], lmax[] (may be NULL: then
@@ -312,12 +312,15 @@ plcg_status plcg_measure_fp64_fma_rate(double *flops_per_s);
 
 /* Launch shape of plcg_solve_batched's FP32 solves (set by an autotuner;
  * process-wide): the kernel variant whose registers are sized for
- * ctas_per_sm (3 or 4) thread blocks per SM, and rows_per_thread (1, 2 or 4)
- * row groups per thread in the one-block-per-system path.  0, 0 restores
- * each method's default (4 blocks per SM; 4 row groups for p(1)-CG and
- * classic CG, 1 for l >= 2).  FP64 batched solves always use the defaults.
- * Errors: PLCG_ERR_INVALID. */
-plcg_status plcg_set_batched_launch(int ctas_per_sm, int rows_per_thread);
+ * ctas_per_sm (3 or 4) thread blocks per SM, with rows_per_thread (1, 2 or
+ * 4) row groups per thread in the one-block-per-system path
+ * (vector_width = 1); or (4, 1, 2): in that path each thread takes pairs of
+ * adjacent rows as 2-wide vectors in the systems whose nx is even, one row
+ * group in the others.  0, 0, 0 restores each method's default (4 blocks per
+ * SM; 2-wide rows for p(1)- and p(2)-CG, 1 row group for l >= 3, 4 for
+ * classic CG).  FP64 batched solves always use their defaults (4 row groups
+ * for p(1)-CG and classic CG, 1 for l >= 2).  Errors: PLCG_ERR_INVALID. */
+plcg_status plcg_set_batched_launch(int ctas_per_sm, int rows_per_thread, int vector_width);
 
 /* Small systems (stencil or CSR operators, M = I or a Jacobi-preconditioned
  * stencil, grid_ctas = 0) are solved by one thread-block cluster of up to 16

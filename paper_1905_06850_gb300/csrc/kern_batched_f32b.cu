@@ -9,12 +9,12 @@ namespace plcg {
 template <int RPT>
 static const void *batched_f32_shape3(int l, bool cg)
 {
-    if (cg) return reinterpret_cast<const void *>(&batched_kernel<float, 1, true, 3, RPT>);
+    if (cg) return reinterpret_cast<const void *>(&batched_kernel<float, 1, true, 3, RPT, 1>);
     switch (l) {
-    case 1: return reinterpret_cast<const void *>(&batched_kernel<float, 1, false, 3, RPT>);
-    case 2: return reinterpret_cast<const void *>(&batched_kernel<float, 2, false, 3, RPT>);
-    case 3: return reinterpret_cast<const void *>(&batched_kernel<float, 3, false, 3, RPT>);
-    case 4: return reinterpret_cast<const void *>(&batched_kernel<float, 4, false, 3, RPT>);
+    case 1: return reinterpret_cast<const void *>(&batched_kernel<float, 1, false, 3, RPT, 1>);
+    case 2: return reinterpret_cast<const void *>(&batched_kernel<float, 2, false, 3, RPT, 1>);
+    case 3: return reinterpret_cast<const void *>(&batched_kernel<float, 3, false, 3, RPT, 1>);
+    case 4: return reinterpret_cast<const void *>(&batched_kernel<float, 4, false, 3, RPT, 1>);
     default: return nullptr;
     }
 }

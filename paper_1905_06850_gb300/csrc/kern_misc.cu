@@ -28,10 +28,12 @@ const void *kernel_ptr(bool f32, int op, int vec, int l, bool cg, bool sc, bool 
     return vec == 4 ? kptr_f32_st4(l, cg) : kptr_f32_st1(l, cg);
 }
 
-const void *batched_kernel_ptr(bool f32, int l, bool cg, int ctas_per_sm, int rows_per_thread)
+const void *batched_kernel_ptr(bool f32, int l, bool cg, int ctas_per_sm, int rows_per_thread,
+                               int vector_width)
 {
-    if (f32) return batched_kernel_ptr_f32(l, cg, ctas_per_sm, rows_per_thread);
-    return (ctas_per_sm == 0 && rows_per_thread == 0) ? batched_kernel_ptr_f64(l, cg) : nullptr;
+    if (f32) return batched_kernel_ptr_f32(l, cg, ctas_per_sm, rows_per_thread, vector_width);
+    return (ctas_per_sm == 0 && rows_per_thread == 0 && vector_width == 0) ? batched_kernel_ptr_f64(l, cg)
+                                                                          : nullptr;
 }
 
 // v[i] uniform in [-1, 1): SplitMix64 (Steele, Lea, Flood, "Fast splittable

@@ -994,22 +994,26 @@ BatchCtx g_batch[64];
 static int g_batch_G = 8;
 static double g_batch_beta = 1.0;
 static double g_batch_gang_frac = 0.5;
-// Launch shape of FP32 batched solves (0, 0: each method's default).
+// Launch shape of FP32 batched solves (0, 0, 0: each method's default).
 static int g_batch_ctas_per_sm = 0;
 static int g_batch_rows_per_thread = 0;
+static int g_batch_vector_width = 0;
 
-extern "C" plcg_status plcg_set_batched_launch(int ctas_per_sm, int rows_per_thread)
+extern "C" plcg_status plcg_set_batched_launch(int ctas_per_sm, int rows_per_thread, int vector_width)
 {
-    if (ctas_per_sm == 0 && rows_per_thread == 0) {
-        g_batch_ctas_per_sm = g_batch_rows_per_thread = 0;
+    if (ctas_per_sm == 0 && rows_per_thread == 0 && vector_width == 0) {
+        g_batch_ctas_per_sm = g_batch_rows_per_thread = g_batch_vector_width = 0;
         return PLCG_OK;
     }
-    if ((ctas_per_sm != 3 && ctas_per_sm != 4) ||
-        (rows_per_thread != 1 && rows_per_thread != 2 && rows_per_thread != 4))
-        return fail(PLCG_ERR_INVALID, "batched launch shape: need 3 or 4 CTAs per SM and 1, 2 or 4 "
-                                      "row groups per thread (or 0, 0)");
+    const bool rows = (ctas_per_sm == 3 || ctas_per_sm == 4) && vector_width == 1 &&
+                      (rows_per_thread == 1 || rows_per_thread == 2 || rows_per_thread == 4);
+    const bool pairs = ctas_per_sm == 4 && rows_per_thread == 1 && vector_width == 2;
+    if (!rows && !pairs)
+        return fail(PLCG_ERR_INVALID, "batched launch shape: need 3 or 4 CTAs per SM, 1, 2 or 4 row groups "
+                                      "per thread and vector width 1, or (4, 1, 2), or (0, 0, 0)");
     g_batch_ctas_per_sm = ctas_per_sm;
     g_batch_rows_per_thread = rows_per_thread;
+    g_batch_vector_width = vector_width;
     return PLCG_OK;
 }
 
@@ -1053,7 +1057,8 @@ static plcg_status run_batched(int count, plcg_matrix *const *A, const double *c
     const bool cg = prm->method == PLCG_METHOD_CG;
     const int l = cg ? 1 : prm->l;
     // the tuned launch shape applies to FP32 solves; FP64 uses the defaults
-    const void *func = f32 ? batched_kernel_ptr(f32, l, cg, g_batch_ctas_per_sm, g_batch_rows_per_thread)
+    const void *func = f32 ? batched_kernel_ptr(f32, l, cg, g_batch_ctas_per_sm, g_batch_rows_per_thread,
+                                                g_batch_vector_width)
                            : batched_kernel_ptr(f32, l, cg);
     if (!func) return fail(PLCG_ERR_UNIMPL, "plcg_solve_batched: l must be 1..4");
     cudaStream_t stream = A[0]->stream;
@@ -1246,6 +1251,8 @@ extern "C" plcg_status plcg_solve_batched(int count, plcg_matrix *const *A, cons
     if (!A || !b || !x || !prm) return fail(PLCG_ERR_INVALID, "plcg_solve_batched: NULL argument");
     for (int i = 0; i < count; ++i) {
         if (!A[i] || !b[i] || !x[i]) return fail(PLCG_ERR_INVALID, "system %d: NULL argument", i);
+        if ((reinterpret_cast<uintptr_t>(b[i]) | reinterpret_cast<uintptr_t>(x[i])) & 15)
+            return fail(PLCG_ERR_INVALID, "system %d: b and x must be 16-byte aligned", i);
         if (A[i]->kind != kOpStencil)
             return fail(PLCG_ERR_UNIMPL, "plcg_solve_batched: system %d is not a stencil operator", i);
         if (A[i]->device != A[0]->device)

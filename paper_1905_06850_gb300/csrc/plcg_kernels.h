@@ -17,11 +17,14 @@ const void *kernel_ptr(bool f32, int op, int vec, int l, bool cg, bool sc = fals
 
 // Address of the batched kernel for p(l)-CG (l = 1..4) or classic CG in a
 // launch shape (CTAs per SM the registers are sized for, row groups per
-// thread; 0, 0 = the method's default; other shapes exist for FP32 only:
-// 3 or 4 CTAs per SM with 1, 2 or 4 row groups); nullptr when absent.
-const void *batched_kernel_ptr(bool f32, int l, bool cg, int ctas_per_sm = 0, int rows_per_thread = 0);
-const void *batched_kernel_ptr_f32(int l, bool cg, int ctas_per_sm, int rows_per_thread);
+// thread, vector width; 0, 0, 0 = the method's default; other shapes exist
+// for FP32 only: 3 or 4 CTAs per SM with 1, 2 or 4 row groups and width 1,
+// or 4 CTAs per SM, 1 row group and width 2); nullptr when absent.
+const void *batched_kernel_ptr(bool f32, int l, bool cg, int ctas_per_sm = 0, int rows_per_thread = 0,
+                               int vector_width = 0);
+const void *batched_kernel_ptr_f32(int l, bool cg, int ctas_per_sm, int rows_per_thread, int vector_width);
 const void *batched_kernel_ptr_f32_3(int l, bool cg, int rows_per_thread);
+const void *batched_kernel_ptr_f32_v(int l, bool cg);
 const void *batched_kernel_ptr_f64(int l, bool cg);
 
 // Per-translation-unit getters used by kernel_ptr.

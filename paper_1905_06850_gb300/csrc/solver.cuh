@@ -2614,16 +2614,22 @@ __global__ void __launch_bounds__(kBlock, 1) plcg_cluster_kernel(SolveArgs<T> a)
 // their CTA or gang for the next system.
 // ------------------------------------------------------------------------
 // Launch shape of the batched kernel, per method: CTAs per SM (the
-// register budget) and row groups per thread in the one-CTA path, where a
-// CTA streams a whole system and latency is hidden by warps and by loads in
-// flight per thread.  Chosen by timing the 4096-system workload on GB300
-// over 2-6 CTAs per SM and 1, 2 or 4 row groups: 4 CTAs per SM for every
-// method; 4 row groups for classic CG and p(1)-CG, 1 for p(l >= 2)-CG.
+// register budget), row groups per thread and vector width VW in the
+// one-CTA path, where a CTA streams a whole system and latency is hidden by
+// warps and by loads in flight per thread.  VW = 2: each thread takes pairs
+// of adjacent rows as 2-wide vectors in systems whose nx is even (the
+// others take the row-group path).  Chosen by timing the 4096-system
+// workload on GB300 over 2-6 CTAs per SM, 1, 2 or 4 row groups and vector
+// widths 1 and 2: 4 CTAs per SM for every method; 4 row groups for classic
+// CG and p(1)-CG, 1 for p(l >= 2)-CG (FP64); in FP32, 2-wide rows for p(1)-
+// and p(2)-CG (44.8 and 59.4 ms against 47.0 and 60.8 ms with one row per
+// thread), 2-wide rows being slower for p(3)-CG (77.4 ms against 74.6) and
+// classic CG (58.9 against 56.9), and 4-wide rows spilling registers.
 template <int L, bool CG> constexpr int kBatchMinBlocks = 4;
 template <int L, bool CG> constexpr int kBatchRPT = (CG || L == 1) ? 4 : 1;
 // Other launch shapes (CTAs per SM the registers are sized for, row groups
-// per thread) are instantiated for the FP32 path; the batched autotuner
-// picks among them (plcg_set_batched_launch).
+// per thread, vector width) are instantiated for the FP32 path; the batched
+// autotuner picks among them (plcg_set_batched_launch).
 
 template <typename T>
 __device__ __forceinline__ void batch_args(const BatchArgs<T> &ba, const BatchSys &sy, T *ws,
@@ -2656,7 +2662,7 @@ __device__ __forceinline__ void batch_args(const BatchArgs<T> &ba, const BatchSy
                                      ((((size_t)(nvec + 2) * nv * sizeof(T)) + 255) / 256) * 256);
 }
 
-template <typename T, int L, bool CG, int MINB = kBatchMinBlocks<L, CG>, int RPT = kBatchRPT<L, CG>>
+template <typename T, int L, bool CG, int MINB = kBatchMinBlocks<L, CG>, int RPT = kBatchRPT<L, CG>, int VW = 1>
 __global__ void __launch_bounds__(kBlock, MINB) batched_kernel(BatchArgs<T> ba)
 {
     __shared__ Smem<T> s;
@@ -2708,8 +2714,16 @@ __global__ void __launch_bounds__(kBlock, MINB) batched_kernel(BatchArgs<T> ba)
         if (threadIdx.x == 0) batch_args(ba, ba.sys[ba.order_small[k]], ws, sa);
         __syncthreads();
         BlockGroup<T> grp;
-        if constexpr (CG) cg_body<T, 1, kOpStencil, BlockGroup<T>, RPT>(sa, s, grp);
-        else plcg_body<T, L, 1, kOpStencil, BlockGroup<T>, RPT, false, T, true>(sa, s, grp);
+        // VW rows per thread need nx % VW == 0 (a vector never straddles two
+        // grid lines); the ring vectors (n = nx * ny * nz apart), b and x
+        // (16-byte aligned) are then aligned for the vector loads
+        if (VW > 1 && sa.st.nx % VW == 0) {
+            if constexpr (CG) cg_body<T, VW, kOpStencil, BlockGroup<T>, 1>(sa, s, grp);
+            else plcg_body<T, L, VW, kOpStencil, BlockGroup<T>, 1, false, T, true>(sa, s, grp);
+        } else {
+            if constexpr (CG) cg_body<T, 1, kOpStencil, BlockGroup<T>, RPT>(sa, s, grp);
+            else plcg_body<T, L, 1, kOpStencil, BlockGroup<T>, RPT, false, T, true>(sa, s, grp);
+        }
     }
 }
 

@@ -94,7 +94,7 @@ SIGNATURES = {
     "plcg_wait": (C.c_int, [_VP, C.c_uint64, C.POINTER(plcg_result)]),
     "plcg_server_destroy": (None, [_VP]),
     "plcg_set_batched_schedule": (C.c_int, [C.c_int, C.c_double, C.c_double]),
-    "plcg_set_batched_launch": (C.c_int, [C.c_int, C.c_int]),
+    "plcg_set_batched_launch": (C.c_int, [C.c_int, C.c_int, C.c_int]),
     "plcg_set_cluster_rows": (C.c_int, [C.c_int64]),
     "plcg_last_error": (C.c_char_p, []),
     "plcg_version": (C.c_char_p, []),

@@ -156,12 +156,13 @@ def test_batched_gang_schedules(P, schedule):
         autotune.set_schedule(0)
 
 
-@pytest.mark.parametrize("shape", [(4, 1), (4, 2), (3, 4)])
+@pytest.mark.parametrize("shape", [(4, 1, 1), (4, 2, 1), (3, 4, 1), (4, 1, 2)])
 def test_batched_launch_shapes(P, shape):
     """Every FP32 launch shape the autotuner chooses among (blocks per SM,
-    row groups per thread) solves the batch like the oracle, and the tuner
-    installs one of the timed candidates; each system's completion time is
-    inside the batch's."""
+    row groups per thread, vector width; the batch mixes odd and even nx, so
+    the 2-wide shape runs both of its paths) solves the batch like the
+    oracle, and the tuner installs one of the timed candidates; each
+    system's completion time is inside the batch's."""
     from paper_1905_06850_gb300 import autotune
     systems = make_batch(count=24, seed=23)
     try:
@@ -190,3 +191,20 @@ def test_batched_launch_shapes(P, shape):
     assert ("shape", shp) in times and ("schedule", sched) in times
     assert times[("shape", shp)] == min(t for k, t in times.items() if k[0] == "shape")
 
+
+
+def test_batched_rejects_unaligned_vectors(P):
+    """b and x are read as 16-byte vectors: a system whose b or x is not
+    16-byte aligned is rejected before anything runs."""
+    import torch
+    op = W.stencil2d(16, 16, shift=0.5)
+    A = P.Matrix(op)
+    buf = torch.zeros(W.op_size(op) + 1, dtype=torch.float64, device="cuda")
+    good = torch.ones(W.op_size(op), dtype=torch.float64, device="cuda")
+    try:
+        for b, x in ((buf[1:], torch.zeros_like(good)), (good, buf[1:])):
+            st, _ = P.solve_batched([A], [b], [x], lmins=[0.5], lmaxs=[8.5], check=False, l=1,
+                                    prec="fp32")
+            assert st == P.PLCG_ERR_INVALID and "16-byte" in P.last_error()
+    finally:
+        A.close()
