@@ -163,6 +163,13 @@ def dp_flops_per_point(l: int) -> int:
     return 8 + 6 * l + 10
 
 
+# Flops per row and iteration that the FP64 p(1)-CG stencil sweep (scaled
+# bases, two rows per thread) issues on the FP64 pipe: 8 FMAs -- K4's two
+# recurrences, K6 and the two K5 dots; the six-neighbour sum runs on the
+# integer units and the SpMV's multiplies are folded into the recurrences.
+DP_PIPE_FLOPS_L1 = 16
+
+
 # ---------------------------------------------------------------- oracle errors
 class OracleErrors:
     """FP64 oracle solves run on the host cores while the GPU legs run (a
@@ -302,6 +309,10 @@ def run_ours(args):
                 "unit": "TFLOP/s", "frac": round(dp_frac, 4), "peak_source": dp_src,
                 "flops_per_row_iter": dp_flops_per_point(args.l),
                 "ncu_fp64_pipe_pct": None if rec is None else rec.get("fp64_pipe_pct")}
+    if (args.prec, args.l) == ("fp64", 1):
+        # the part of the algorithmic flops the FP64 pipe executes
+        alu_part["fp64_pipe_flops_per_row_iter"] = DP_PIPE_FLOPS_L1
+        alu_part["fp64_pipe_frac"] = round(dp_frac * DP_PIPE_FLOPS_L1 / dp_flops_per_point(1), 4)
     if dp_frac >= hbm_frac:
         roofline = dict(alu_part, traffic=traffic, hbm=hbm_part)
     else:

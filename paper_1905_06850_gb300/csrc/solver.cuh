@@ -21,6 +21,7 @@
 
 #include <type_traits>
 
+#include "fxsum.h"
 #include "plcg_internal.h"
 
 namespace plcg {
@@ -401,6 +402,37 @@ __device__ __forceinline__ void stencil_parts(const StencilDesc &st, const Ld &l
     ld.template vec<VEC>(g0, c);
     const V left = (x0 > 0) ? ld.one(g0 - 1) : V(0);
     const V right = (x0 + VEC < nx) ? ld.one(g0 + VEC) : V(0);
+    if constexpr (std::is_same<V, double>::value && VEC >= 2) {
+        // FP64, two rows per thread (systems of more than 16384 rows, bound
+        // by the FP64 pipe): the neighbour sum on the integer units
+        // (fxsum.h), the out-of-grid neighbours as zeros.  One row per
+        // thread (small systems, bound by latency) keeps the FP64
+        // additions, whose dependent chain is shorter.
+        V ym[VEC], yp[VEC], zm[VEC], zp[VEC];
+#pragma unroll
+        for (int v = 0; v < VEC; ++v) ym[v] = yp[v] = zm[v] = zp[v] = V(0);
+        if (y > 0) ld.template vec<VEC>(g0 - nx, ym);
+        if (y + 1 < ny) ld.template vec<VEC>(g0 + nx, yp);
+        if (st.dim == 3) {
+            const uint32_t nxy = nx * ny;
+            if (zc > 0) ld.template vec<VEC>(g0 - nxy, zm);
+            if (zc + 1 < (uint32_t)st.nz) ld.template vec<VEC>(g0 + nxy, zp);
+#pragma unroll
+            for (int v = 0; v < VEC; ++v) {
+                const double x[6] = {(v > 0) ? c[v - 1] : left, (v < VEC - 1) ? c[v + 1] : right,
+                                     ym[v], yp[v], zm[v], zp[v]};
+                nb[v] = fx_sum(x);
+            }
+        } else {
+#pragma unroll
+            for (int v = 0; v < VEC; ++v) {
+                const double x[4] = {(v > 0) ? c[v - 1] : left, (v < VEC - 1) ? c[v + 1] : right,
+                                     ym[v], yp[v]};
+                nb[v] = fx_sum(x);
+            }
+        }
+        return;
+    }
 #pragma unroll
     for (int v = 0; v < VEC; ++v)
         nb[v] = ((v > 0) ? c[v - 1] : left) + ((v < VEC - 1) ? c[v + 1] : right);
