@@ -56,6 +56,28 @@ PLCG_HD inline int fx_clz64(uint64_t u)   // u != 0
 #endif
 }
 
+#ifdef __CUDACC__
+#define PLCG_FX_NOINLINE __noinline__
+#else
+#define PLCG_FX_NOINLINE __attribute__((noinline))
+#endif
+
+// The plain FP64 additions of the out-of-range case, out of line: kept off
+// the common path (not evaluated alongside it).
+template <int K>
+struct FxOperands {
+    double v[K];
+};
+
+template <int K>
+PLCG_HD PLCG_FX_NOINLINE double fx_plain_sum(FxOperands<K> x)
+{
+    double s = x.v[0];
+#pragma unroll
+    for (int k = 1; k < K; ++k) s += x.v[k];
+    return s;
+}
+
 constexpr int kFxShift = 6;                        // significand headroom: 2^58 <= m < 2^59
 constexpr int kFxUnitBias = 1075 + kFxShift;       // unit of the sum: 2^(emax - kFxUnitBias)
 constexpr int kFxEmaxLo = kFxUnitBias - 1022;      // (double)acc >= 1: result exponent >= 1
@@ -74,11 +96,11 @@ PLCG_HD inline double fx_sum(const double (&x)[K])
         const int e = (int)((b[k] >> 52) & 0x7ff);
         emax = e > emax ? e : emax;
     }
-    if (emax < kFxEmaxLo || emax > kFxEmaxHi) {
-        double s = x[0];
+    if (__builtin_expect(emax < kFxEmaxLo || emax > kFxEmaxHi, 0)) {
+        FxOperands<K> o;
 #pragma unroll
-        for (int k = 1; k < K; ++k) s += x[k];
-        return s;
+        for (int k = 0; k < K; ++k) o.v[k] = x[k];
+        return fx_plain_sum<K>(o);
     }
     int64_t acc = 0;
 #pragma unroll
