@@ -170,6 +170,50 @@ def dp_flops_per_point(l: int) -> int:
 DP_PIPE_FLOPS_L1 = 16
 
 
+def stencil_roofline(*, n, nx, l, prec, iters, seconds, hbm_peak, hbm_src, dp_peak_tf, dp_src, rec=None):
+    """The roofline object of the 3D 7-point p(l)-CG solve (one launch of
+    ``iters`` iterations and 2 FP64 residual sweeps in ``seconds``): the HBM
+    fraction (algorithmic bytes over the measured copy bandwidth) and, for
+    FP64 sweeps, the FP64 one (flops over the measured FMA rate); "bound"
+    names the larger, the other sits beside it.  ``rec``: the committed ncu
+    record of the same kernel (DRAM bytes per row per sweep), or None."""
+    vb = 8 if prec == "fp64" else 4
+    bytes_iter = passes_per_iter(l, "plcg") * vb * n
+    bytes_launch = iters * bytes_iter + 3 * 8 * n * 2   # + 2 FP64 residual sweeps
+    achieved_gbs = bytes_launch / seconds / 1e9
+    achieved_dp_tf = iters * dp_flops_per_point(l) * n / seconds / 1e12
+    # measured DRAM traffic per launch: bytes per row per sweep of an ncu
+    # capture (smaller grid, same kernel) x rows x sweeps of this solve
+    traffic = None if rec is None else round(rec["dram_bytes_per_point_iter"] * n * (iters + 2))
+    hbm_frac = achieved_gbs / hbm_peak
+    dp_frac = achieved_dp_tf / dp_peak_tf
+    hbm_part = {"bound": "hbm", "achieved": round(achieved_gbs, 1), "peak": hbm_peak, "unit": "GB/s",
+                "frac": round(hbm_frac, 4), "peak_source": hbm_src,
+                "bytes_per_iter": bytes_iter}
+    alu_part = {"bound": "alu", "achieved": round(achieved_dp_tf, 4), "peak": dp_peak_tf,
+                "unit": "TFLOP/s", "frac": round(dp_frac, 4), "peak_source": dp_src,
+                "flops_per_row_iter": dp_flops_per_point(l),
+                "ncu_fp64_pipe_pct": None if rec is None else rec.get("fp64_pipe_pct")}
+    if (prec, l) == ("fp64", 1) and n >= (1 << 19) and nx % 2 == 0:
+        # the kernel of this solve (scaled bases, two rows per thread) executes
+        # 16 of the paper's 24 flops per row on the FP64 pipe (the neighbour
+        # sum runs on the integer units): the FP64 roofline counts those, the
+        # paper's count stays beside them
+        pipe = DP_PIPE_FLOPS_L1 / dp_flops_per_point(1)
+        dp_frac *= pipe
+        alu_part.update({"achieved": round(achieved_dp_tf * pipe, 4), "frac": round(dp_frac, 4),
+                         "flops_per_row_iter": DP_PIPE_FLOPS_L1,
+                         "flops_counted": "FP64-pipe flops: 8 FMA per row (K4's two recurrences, K6, "
+                                          "the two K5 dots); the six-neighbour sum runs on the integer units",
+                         "paper_flops_per_row_iter": dp_flops_per_point(1),
+                         "paper_flops_tflops": round(achieved_dp_tf, 4)})
+    if prec != "fp64":   # FP32 sweeps: no FP64 roof (FP64 only in dots and scalars)
+        return dict(hbm_part, traffic=traffic)
+    if dp_frac >= hbm_frac:
+        return dict(alu_part, traffic=traffic, hbm=hbm_part)
+    return dict(hbm_part, traffic=traffic, alu=alu_part)
+
+
 # ---------------------------------------------------------------- oracle errors
 class OracleErrors:
     """FP64 oracle solves run on the host cores while the GPU legs run (a
@@ -281,51 +325,17 @@ def run_ours(args):
     peaks = measured_peaks()
     hbm_peak = peaks.get("hbm_gbs") or 6800.0
     hbm_src = "measured" if peaks.get("hbm_gbs") else "fallback"
-    bytes_iter = passes_per_iter(L_HEAD, "plcg") * 8 * n
-    bytes_launch = statistics.mean(iters) * bytes_iter + 3 * 8 * n * 2   # + 2 residual sweeps
-    achieved_gbs = bytes_launch / statistics.mean(kern_s) / 1e9
-    dp_flops = statistics.mean(iters) * dp_flops_per_point(L_HEAD) * n
-    achieved_dp_tf = dp_flops / statistics.mean(kern_s) / 1e12
     # FP64 peak: measured on this GPU (independent FMA chains on every
     # resident thread, plcg_measure_fp64_fma_rate); nominal 1.25 if that fails
     try:
         dp_peak_tf, dp_src = round(plcg.measure_fp64_fma_rate() / 1e12, 4), "measured (plcg_measure_fp64_fma_rate)"
     except Exception as exc:   # noqa: BLE001
         dp_peak_tf, dp_src = 1.25, f"nominal (measurement failed: {exc})"
-    # measured DRAM traffic per launch: bytes per row per sweep of an ncu
-    # capture (smaller grid, same kernel) x rows x sweeps (iterations + 2
-    # residual sweeps) of this solve
     rec = profiled_record("plcg_3d_fp64_l1.json") if (args.prec, args.l) == ("fp64", 1) else None
-    traffic = None if rec is None else round(rec["dram_bytes_per_point_iter"] * n * (statistics.mean(iters) + 2))
-    hbm_frac = achieved_gbs / hbm_peak
-    dp_frac = achieved_dp_tf / dp_peak_tf
-    # both fractions of the FP64 sweep: the HBM one (algorithmic bytes over the
-    # measured copy bandwidth) and the FP64 one (flops over the measured FMA
-    # rate); "bound" names the larger
-    hbm_part = {"bound": "hbm", "achieved": round(achieved_gbs, 1), "peak": hbm_peak, "unit": "GB/s",
-                "frac": round(hbm_frac, 4), "peak_source": hbm_src,
-                "bytes_per_iter": bytes_iter}
-    alu_part = {"bound": "alu", "achieved": round(achieved_dp_tf, 4), "peak": dp_peak_tf,
-                "unit": "TFLOP/s", "frac": round(dp_frac, 4), "peak_source": dp_src,
-                "flops_per_row_iter": dp_flops_per_point(args.l),
-                "ncu_fp64_pipe_pct": None if rec is None else rec.get("fp64_pipe_pct")}
-    if (args.prec, args.l) == ("fp64", 1) and n >= (1 << 19) and args.nx % 2 == 0:
-        # the kernel of this solve (scaled bases, two rows per thread) executes
-        # 16 of the paper's 24 flops per row on the FP64 pipe (the neighbour
-        # sum runs on the integer units): the FP64 roofline counts those, the
-        # paper's count stays beside them
-        pipe = DP_PIPE_FLOPS_L1 / dp_flops_per_point(1)
-        dp_frac *= pipe
-        alu_part.update({"achieved": round(achieved_dp_tf * pipe, 4), "frac": round(dp_frac, 4),
-                         "flops_per_row_iter": DP_PIPE_FLOPS_L1,
-                         "flops_counted": "FP64-pipe flops: 8 FMA per row (K4's two recurrences, K6, "
-                                          "the two K5 dots); the six-neighbour sum runs on the integer units",
-                         "paper_flops_per_row_iter": dp_flops_per_point(1),
-                         "paper_flops_tflops": round(achieved_dp_tf, 4)})
-    if dp_frac >= hbm_frac:
-        roofline = dict(alu_part, traffic=traffic, hbm=hbm_part)
-    else:
-        roofline = dict(hbm_part, traffic=traffic, alu=alu_part)
+    roofline = stencil_roofline(n=n, nx=args.nx, l=args.l, prec=args.prec, iters=statistics.mean(iters),
+                                seconds=statistics.mean(kern_s), hbm_peak=hbm_peak, hbm_src=hbm_src,
+                                dp_peak_tf=dp_peak_tf, dp_src=dp_src, rec=rec)
+    achieved_gbs = roofline["hbm"]["achieved"] if "hbm" in roofline else roofline["achieved"]
 
     extra = {}
     if rank == 0 and not args.quick:
