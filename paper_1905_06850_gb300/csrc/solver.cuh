@@ -2597,16 +2597,22 @@ finish:
 // Single-system kernels: the whole grid solves one system (cooperative
 // launch, so that every CTA is resident and the grid barrier can complete).
 // ------------------------------------------------------------------------
-// CTAs per SM the register budget is sized for: three for FP32 with l <= 2,
-// two otherwise; the 27-point tiles' buffers (about 47 KB each) leave room
+// CTAs per SM the register budget is sized for: three for FP32 with l <= 2
+// and for the FP64 p(1)-CG stencil sweep with scaled bases and two rows per
+// thread (latency-bound once its neighbour sum runs on the integer units:
+// 3D 256^3 161.7 -> 138.5 ms at 85 registers with 72 bytes of spills,
+// against 128 registers at two CTAs per SM), two otherwise; the 27-point tiles' buffers (about 47 KB each) leave room
 // for one CTA per SM with four of them (two with two).
-template <typename T, int L, int OP>
-constexpr int kPlcgMinBlocks = (sizeof(T) == 4 && op_is_var27(OP)) ? 2 : (sizeof(T) == 4 && L <= 2) ? 3 : 2;
+template <typename T, int L, int OP, bool SC = false, int VEC = 1>
+constexpr int kPlcgMinBlocks = (sizeof(T) == 4 && op_is_var27(OP)) ? 2
+                               : (sizeof(T) == 4 && L <= 2)       ? 3
+                               : (SC && L == 1 && OP == kOpStencil && VEC == 2) ? 3
+                                                                                : 2;
 
 // CT: the stored type of the matrix values (T, or float under FP64 vectors:
 // the FP32-matrix path).
 template <typename T, int L, int VEC, int OP, bool SC = false, typename CT = T>
-__global__ void __launch_bounds__(kBlock, (kPlcgMinBlocks<T, L, OP>))
+__global__ void __launch_bounds__(kBlock, (kPlcgMinBlocks<T, L, OP, SC, VEC>))
 plcg_kernel(SolveArgs<T> a)
 {
     __shared__ Smem<T> s;
