@@ -9,13 +9,13 @@
 // exponent (bits below its unit 2^(emax - 1081) are dropped, toward zero),
 // the signed 64-bit integers are added exactly, and the total is rounded
 // to FP64 once (to nearest even, in integer operations) with the exponent
-// of its unit (a normal number in the range checked).  Error: below K units of 2^(emax - 1081) from the
-// dropped bits (subnormal operands lie below the unit) plus half an ulp of
-// the result, i.e. at most
-// K * 2^-58 * max|x_k| + 2^-53 |sum| -- tighter than the (K - 1) * 2^-53 *
-// sum|x_k| bound of K - 1 rounded FP64 additions.  Operands whose largest
-// binade is outside [2^-964, 2^1019] (all zero, tiny, huge, Inf, NaN) take
-// the plain FP64 additions.
+// of its unit (a normal number in the range checked).  Error: below K units
+// of 2^(emax - 1081) from the dropped bits (subnormal operands lie below the
+// unit) plus half an ulp of the result, i.e. at most K * 2^-58 * max|x_k| +
+// 2^-53 |sum| -- tighter than the (K - 1) * 2^-53 * sum|x_k| bound of K - 1
+// rounded FP64 additions.  Operands whose largest binade is outside
+// [2^-964, 2^1019] (all zero, tiny, huge, Inf, NaN) take the plain FP64
+// additions, out of line.
 #pragma once
 
 #include <stdint.h>
@@ -80,8 +80,8 @@ PLCG_HD PLCG_FX_NOINLINE double fx_plain_sum(FxOperands<K> x)
 
 constexpr int kFxShift = 6;                        // significand headroom: 2^58 <= m < 2^59
 constexpr int kFxUnitBias = 1075 + kFxShift;       // unit of the sum: 2^(emax - kFxUnitBias)
-constexpr int kFxEmaxLo = kFxUnitBias - 1022;      // (double)acc >= 1: result exponent >= 1
-constexpr int kFxEmaxHi = 2046 + kFxUnitBias - 1085;   // |acc| < 2^62 (rounds to <= 2^62)
+constexpr int kFxEmaxLo = kFxUnitBias - 1022;      // |acc| >= 1: result exponent >= 1
+constexpr int kFxEmaxHi = 2046 + kFxUnitBias - 1085;   // |acc| < 2^62, rounded up to 2^62 at most
 
 // Sum of the K <= 8 values x[0..K-1] (see above).
 template <int K>
